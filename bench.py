@@ -1,0 +1,364 @@
+"""Benchmark: batched uneven grids, FP32, one graph-captured launch per sweep.
+
+Workload (one bench "step" = one aniso_step_batched call): 512 independent
+periodic random-field grids, nx and ny drawn from the multiples of 32 in
+[64, 1024], chi_par log-uniform in [1e-3, 1e-1], dt log-uniform in
+[10, 1000] x the explicit limit, 200 steps each, FP32 state and FP32 face
+coefficients.  Metric: Gcell-steps/s = sum(nx*ny*steps) / wall time / 1e9.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Prints one JSON line on rank 0.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gcell-steps/s, FP32 batched vs plain FP64 on one GB300 at L∞ err<=1e-4; % HBM peak"
+UNIT = "Gcell-steps/s"
+N_INST = 512
+STEPS_PER_CALL = 200
+BYTES_PER_CELL_SWEEP = 16  # FP32: read T (4) + two face coefficients (8) + write T (4)
+WORKLOAD = ("batched 512 uneven periodic random-field grids (nx, ny multiples of 32 in "
+            "[64,1024]), FP32, 200 steps per call, one launch per sweep in a captured CUDA graph")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--instances", type=int, default=N_INST)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "of measured"
+    except Exception:
+        return 6800.0, "of fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("sweep_kernels.cuh", "aniso_internal.h", "util_kernels.cu"):
+        h.update(open(os.path.join(ROOT, "paper_1008_0861_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel):
+    """dram bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        d = json.load(open(p))
+        ent = d[kernel]
+        if ent.get("source_hash") != kernel_source_hash():
+            return None
+        return ent["dram_bytes_per_launch"]
+    except Exception:
+        return None
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + q, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                rows.append((float(parts[0]), float(parts[1]), parts[3:7]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for _, _, r in rows for k in range(4) if r[k].lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def make_instances(count, rank):
+    import workloads as W
+    return W.batch_instances(count, nsteps=STEPS_PER_CALL, first=rank * count)
+
+
+def cpu_baseline(insts, budget_s=12.0):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload:
+    whole instances for their full 200 steps until the time budget is used."""
+    import numpy as np
+    import oracle as O
+    cells = 0
+    t0 = time.perf_counter()
+    used = []
+    for inst in insts:
+        w = lambda a: a.astype(np.float32).astype(np.float64)  # noqa: E731
+        co = O.face_coeffs(w(inst.bx), w(inst.by), inst.bc, inst.chi_par)
+        O.step(w(inst.T0), co, inst.bc, inst.dt, inst.dx, inst.dy, inst.chi_par, nsteps=inst.nsteps)
+        cells += inst.cells * inst.nsteps
+        used.append(inst.name)
+        if time.perf_counter() - t0 > budget_s:
+            break
+    el = time.perf_counter() - t0
+    return {"value": cells / el / 1e9, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+            "sample": "%d of %d instances (%s..%s), full %d steps each, FP64, %.1f s" % (
+                len(used), len(insts), used[0], used[-1], STEPS_PER_CALL, el)}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    insts = make_instances(args.instances, 0)
+    # each reference step: a bounded sample of the workload (whole instances, full steps)
+    per_step_budget = max(2.0, 150.0 / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        cpu_baseline(insts[:2], budget_s=0.1)
+    vals, samples = [], []
+    t_all = 0.0
+    for k in range(args.steps):
+        start = (k * 3) % len(insts)
+        b = cpu_baseline(insts[start:] + insts[:start], budget_s=per_step_budget)
+        vals.append(b["value"])
+        samples.append(b["sample"])
+        t_all += 1.0
+    v = statistics.median(vals)
+    import oracle as O
+    total_cells = sum(i.cells for i in insts) * STEPS_PER_CALL
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total_cells / (v * 1e9) * 1e3 if v else None,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "instances": len(insts)},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+                             "sample": samples[0]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def fp64_plain_compare(P, torch):
+    """Plain FP64 single instance on the GPU: the 50x50 ring workload, 250
+    steps, for the FP32-batched vs plain-FP64 comparison."""
+    import numpy as np
+    import oracle as O
+    import workloads as W
+    inst = W.ring_instance(50)
+    h = P.aniso_create(inst.nx, inst.ny, inst.dx, inst.dy, inst.chi_par, 0.0, inst.bc)
+    try:
+        bx = torch.tensor(inst.bx, dtype=torch.float64, device="cuda")
+        by = torch.tensor(inst.by, dtype=torch.float64, device="cuda")
+        P.aniso_set_field(h, bx, by)
+        T = torch.tensor(inst.T0, dtype=torch.float64, device="cuda")
+        P.aniso_step(h, T, inst.dt, inst.nsteps)
+        P.aniso_sync(h)
+        got = T.cpu().numpy()
+        ref = O.step(inst.T0, O.face_coeffs(inst.bx, inst.by, 0, inst.chi_par), 0, inst.dt, inst.dx,
+                     inst.dy, inst.chi_par, nsteps=inst.nsteps)
+        err = float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
+        reps = 20
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            P.aniso_step(h, T, inst.dt, inst.nsteps)
+        P.aniso_sync(h)
+        el = time.perf_counter() - t0
+        return {"value": inst.cells * inst.nsteps * reps / el / 1e9, "unit": UNIT,
+                "workload": "ring 50x50 FP64 single instance, 250 steps (graph replay)",
+                "rel_linf_vs_oracle": err}
+    finally:
+        P.aniso_destroy(h)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import numpy as np
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_1008_0861_gb300 as P
+    import oracle as O
+
+    P.load()
+    insts = make_instances(args.instances, rank)
+    handles, Ts, bufs = [], [], []
+    for inst in insts:
+        h = P.aniso_create(inst.nx, inst.ny, inst.dx, inst.dy, inst.chi_par, 0.0, inst.bc)
+        P.aniso_set_option(h, P.ANISO_OPT_PRECISION, P.ANISO_PREC_FP32)
+        bx = torch.tensor(inst.bx, dtype=torch.float32, device="cuda")
+        by = torch.tensor(inst.by, dtype=torch.float32, device="cuda")
+        P.aniso_set_field(h, bx, by)
+        Ts.append(torch.tensor(inst.T0, dtype=torch.float32, device="cuda"))
+        handles.append(h)
+        bufs.append((bx, by))
+    P.aniso_set_option(handles[0], P.ANISO_OPT_PROFILE, 1)
+    batch = P.aniso_batch_create(handles)
+    P.aniso_set_option(handles[0], P.ANISO_OPT_PROFILE, 0)
+    dts = [i.dt for i in insts]
+    nsteps = [STEPS_PER_CALL] * len(insts)
+    cells = sum(i.cells for i in insts)
+    cell_steps = cells * STEPS_PER_CALL
+    torch.cuda.synchronize()
+    del bufs
+
+    # parity sample of this very workload: instance 0 after one call, vs the oracle
+    T0_saved = [t.clone() for t in Ts[:2]]
+
+    def sync_all():
+        torch.cuda.synchronize()
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        P.aniso_step_batched(batch, Ts, dts, nsteps)
+    sync_all()
+    P.aniso_kernel_times(batch=batch, kind=0, reset=True)
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        sync_all()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            P.aniso_step_batched(batch, Ts, dts, nsteps)
+        ev1.record(stream)
+        sync_all()
+    ms = ev0.elapsed_time(ev1)
+    kt = {k: P.aniso_kernel_times(batch=batch, kind=k) for k in (0, 1)}
+    ms_step = ms / args.steps
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms_step], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    value = cell_steps * world / (ms_step * 1e-3) / 1e9
+
+    # end to end: host (pinned) T in, one call, host T out, every step
+    host = [torch.empty(t.shape, dtype=torch.float32, pin_memory=True) for t in Ts]
+    for hsrc, t in zip(host, Ts):
+        hsrc.copy_(t)
+    e2e_steps = max(1, min(3, args.steps))
+    sync_all()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        for hsrc, t in zip(host, Ts):
+            t.copy_(hsrc, non_blocking=True)
+        P.aniso_step_batched(batch, Ts, dts, nsteps)
+        for hsrc, t in zip(host, Ts):
+            hsrc.copy_(t, non_blocking=True)
+    e1.record(stream)
+    sync_all()
+    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+    io_bytes = cells * 4
+
+    # roofline of the dominant kernel (live CUDA-event durations over the timed region)
+    names = {0: "xsweep", 1: "ysweep"}
+    dom = max(kt, key=lambda k: kt[k][0])
+    dom_ms, dom_n = kt[dom]
+    achieved = BYTES_PER_CELL_SWEEP * cells / (dom_ms / dom_n * 1e-3) / 1e9 if dom_n else None
+    peak, peak_note = measured_peak()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "instances_per_gpu": len(insts), "cells_per_gpu": cells,
+                   "steps_per_call": STEPS_PER_CALL,
+                   "l2": "inputs larger than L2: %.2f GB resident per GPU (T, T*, 4 coefficient arrays)"
+                         % (cells * 4 * 6 / 1e9),
+                   "parallelism": "independent instances per GPU (no collective)"},
+        "roofline": {"bound": "hbm", "kernel": names[dom], "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak if achieved else None,
+                     "peak_source": peak_note, "traffic": ncu_traffic(names[dom]),
+                     "algorithmic_bytes_per_launch": BYTES_PER_CELL_SWEEP * cells,
+                     "avg_launch_ms": dom_ms / dom_n if dom_n else None,
+                     "per_kernel_ms": {names[k]: kt[k][0] / max(1, kt[k][1]) for k in kt}},
+        "e2e": {"value": cell_steps / (e2e_ms * 1e-3) / 1e9, "unit": UNIT,
+                "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes},
+        "clocks": clk.summary(),
+        "gpu_launches": 2 * STEPS_PER_CALL * args.steps,
+    }
+    if rank == 0:
+        # accuracy of this workload (FP32) against the FP64 oracle on a sample
+        import workloads as W  # noqa: F401
+        errs = []
+        for k in range(2):
+            inst = insts[k]
+            hT = T0_saved[k]
+            t = hT.clone()
+            P.aniso_step(handles[k], t, inst.dt, STEPS_PER_CALL)
+            P.aniso_sync(handles[k])
+            w = lambda a: a.astype(np.float32).astype(np.float64)  # noqa: E731
+            co = O.face_coeffs(w(inst.bx), w(inst.by), inst.bc, inst.chi_par)
+            ref = O.step(hT.double().cpu().numpy(), co, inst.bc, inst.dt, inst.dx, inst.dy,
+                         inst.chi_par, nsteps=STEPS_PER_CALL)
+            got = t.double().cpu().numpy()
+            errs.append(float(np.max(np.abs(got - ref)) / np.max(np.abs(ref))))
+        line["accuracy"] = {"rel_linf_vs_fp64_oracle": max(errs),
+                            "sample": "instances 0-1, one 200-step call"}
+        line["fp64_plain"] = fp64_plain_compare(P, torch)
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(insts)
+        print(json.dumps(line), flush=True)
+    P.aniso_batch_destroy(batch)
+    for h in handles:
+        P.aniso_destroy(h)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,197 @@
+/*
+ * aniso.h -- C ABI of libaniso.so, a GB300 (sm_103a) implementation of the
+ * directionally split semi-implicit step for anisotropic diffusion of
+ * Sharma & Hammett, "A Fast Semi-implicit Method for Anisotropic Diffusion"
+ * (arXiv:1008.0861), Section 2.
+ *
+ * The equation (Section 2, Eqs. aniso_cond and heat_flux):
+ *     dT/dt = -div q,   q = -chi_par b (b . grad T)  [+ chi_perp grad T part]
+ * on a uniform 2-D Cartesian grid of nx * ny cells (x fastest in memory:
+ * T[j*nx + i] is cell (i, j)).  One step is the composition of Eq. op_2step:
+ *     T^{n+1} = (1 + dt D_yy)^-1 (1 - dt D_yx) (1 + dt D_xx)^-1 (1 - dt D_xy) T^n,
+ * i.e. an x-update (Eq. xup) and then a y-update (Eq. yup).  Each update is
+ * implicit in the face-normal flux (one tridiagonal system per grid line,
+ * cyclic when the boundary is periodic) and explicit in the transverse flux,
+ * whose face differences are limited with van Leer's limiter
+ * (Eq. vanLeer, L(a,b,c,d) = L(L(a,b), L(c,d))).  The face value of b is the
+ * plain average of the two adjacent cell centres (Section 2).
+ *
+ * Conventions shared by every call:
+ *  - All status codes are `int` (ANISO_OK = 0).  No call aborts, traps or
+ *    prints; the message of the last failure on the calling host thread is
+ *    returned by aniso_last_error().
+ *  - Pointers named "device" must point to device memory of the current
+ *    CUDA device; "host" pointers to ordinary host memory.  The caller owns
+ *    every buffer it passes; the library owns the buffers inside a handle.
+ *  - Element type of T, bx, by follows the handle's precision:
+ *    ANISO_PREC_FP64 -> double, ANISO_PREC_FP32 -> float.
+ *  - Work is enqueued asynchronously on the handle's stream (the legacy
+ *    default stream unless ANISO_OPT_STREAM sets another); only calls that
+ *    return host values (aniso_total, aniso_sync, aniso_get_state with a
+ *    host copy) synchronise it.
+ *  - Units: dx, dy are cell sizes; chi_par, chi_perp diffusivities; dt the
+ *    timestep.  Coefficients used per update: lamx = chi_par dt / dx^2,
+ *    lamy = chi_par dt / dy^2, mu = chi_par dt / (dx dy).
+ */
+#ifndef ANISO_H
+#define ANISO_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct aniso_ctx *aniso_t;         /* one grid (opaque, library-owned) */
+typedef struct aniso_batch *aniso_batch_t; /* a set of grids stepped together */
+
+/* Status codes. */
+enum {
+    ANISO_OK = 0,
+    ANISO_ERR_ARG = 1,         /* invalid argument (size, spacing, null pointer, range) */
+    ANISO_ERR_STATE = 2,       /* call out of order, e.g. aniso_step before aniso_set_field */
+    ANISO_ERR_CUDA = 3,        /* a CUDA runtime call failed; message has the CUDA error */
+    ANISO_ERR_NONFINITE = 4,   /* a step produced a NaN or infinite temperature */
+    ANISO_ERR_TIMEOUT = 5,     /* reserved for bounded device-side waits */
+    ANISO_ERR_OOM = 6,         /* device allocation failed */
+    ANISO_ERR_UNSUPPORTED = 7  /* valid request outside what this build handles */
+};
+
+/* Boundary conditions (both directions). */
+enum {
+    ANISO_BC_ZEROFLUX = 0, /* reflective (Section 3.1): no flux through boundary faces */
+    ANISO_BC_PERIODIC = 1  /* wrap-around; line systems become cyclic */
+};
+
+/* Option keys for aniso_set_option and their values. */
+enum {
+    ANISO_OPT_PRECISION = 0,  /* ANISO_PREC_FP64 (default) or ANISO_PREC_FP32 */
+    ANISO_OPT_FIELD_FP16 = 1, /* 1: store face coefficients as FP16 (FP32 precision only) */
+    ANISO_OPT_KAHAN = 2,      /* 1: compensated FP32 state, T + lo (FP32 precision only) */
+    ANISO_OPT_LIMITER = 3,    /* ANISO_LIM_* */
+    ANISO_OPT_ORDER = 4,      /* ANISO_ORDER_* */
+    ANISO_OPT_STREAM = 5,     /* cudaStream_t cast to integer; 0 = legacy default stream */
+    ANISO_OPT_GRAPH = 6,      /* 1 (default): replay aniso_step loops from a captured CUDA graph */
+    ANISO_OPT_PROFILE = 7     /* 1: time every sweep launch with CUDA events (aniso_kernel_times) */
+};
+enum { ANISO_PREC_FP64 = 0, ANISO_PREC_FP32 = 1 };
+enum {
+    ANISO_LIM_VANLEER = 0, /* Eq. vanLeer (default) */
+    ANISO_LIM_ARITH = 1,   /* arithmetic mean of the four differences: the linear
+                              reading used for Eqs. amp1/amp2 (testing only) */
+    ANISO_LIM_MINMOD = 2,  /* minmod, named in Section 2 */
+    ANISO_LIM_MC = 3       /* monotonized central, named in Section 2 */
+};
+enum {
+    ANISO_ORDER_XY = 0,       /* Eq. op_2step: x-update then y-update every step (default) */
+    ANISO_ORDER_YX = 1,       /* the reversed order the paper mentions after Eq. op_2step */
+    ANISO_ORDER_ALTERNATE = 2 /* x,y on even step counters, y,x on odd ones */
+};
+/* Directions for aniso_sweep. */
+enum { ANISO_DIR_X = 0, ANISO_DIR_Y = 1 };
+/* Kernel kinds for aniso_kernel_times. */
+enum { ANISO_KERNEL_XSWEEP = 0, ANISO_KERNEL_YSWEEP = 1, ANISO_KERNEL_TRANSPOSE = 2 };
+
+/* Create a handle for one nx * ny grid.
+ *   nx, ny   : cells per direction, each >= 3.
+ *   dx, dy   : cell sizes, > 0.
+ *   chi_par  : parallel diffusivity, > 0 (Eq. heat_flux).
+ *   chi_perp : perpendicular diffusivity, 0 <= chi_perp <= chi_par.  It adds
+ *              chi_perp * I to the diffusion tensor (Section 2.1's general
+ *              symmetric tensor); the paper's tests use 0.
+ *   bc       : ANISO_BC_*.
+ *   out      : receives the handle.
+ * Allocates nothing on the device yet (buffers are sized on
+ * aniso_set_field).  Errors: ANISO_ERR_ARG. */
+int aniso_create(int nx, int ny, double dx, double dy, double chi_par, double chi_perp, int bc,
+                 aniso_t *out);
+
+/* Set an option (ANISO_OPT_*).  PRECISION, FIELD_FP16 and KAHAN must be set
+ * before aniso_set_field; the others any time.  Errors: ANISO_ERR_ARG (key
+ * or value), ANISO_ERR_STATE (precision change after the field is set). */
+int aniso_set_option(aniso_t h, int key, long long value);
+
+/* Set the unit field b (Section 2): bx, by are device arrays of nx*ny cell-
+ * centred components in the handle's precision.  The library averages b to
+ * faces (Section 2, "simple averaging") in FP64 and stores the face
+ * coefficients it needs, in units of chi_par (kappa = chi_perp/chi_par):
+ *     x faces: kappa + (1-kappa) bx^2,  (1-kappa) bx by
+ *     y faces: kappa + (1-kappa) by^2,  (1-kappa) by bx
+ * rounded once to the storage type (FP64, FP32 or FP16).  Under zero-flux
+ * boundaries the boundary-face coefficients are zero.  b is not required to
+ * be unit length; the paper's b is.  The caller may free bx, by after the
+ * call returns and the stream has passed it.  Errors: ANISO_ERR_ARG (null),
+ * ANISO_ERR_OOM, ANISO_ERR_CUDA. */
+int aniso_set_field(aniso_t h, const void *bx, const void *by);
+
+/* Advance T by nsteps steps of size dt (Eq. op_2step), in place.
+ *   T      : device array nx*ny in the handle's precision.
+ *   dt     : > 0.  nsteps >= 0.
+ * The update order of each step follows ANISO_OPT_ORDER; the handle's step
+ * counter (used by ANISO_ORDER_ALTERNATE) advances by nsteps.  With
+ * ANISO_OPT_KAHAN the handle keeps the low parts of T between calls.
+ * Asynchronous.  Errors: ANISO_ERR_ARG, ANISO_ERR_STATE (no field),
+ * ANISO_ERR_CUDA, ANISO_ERR_UNSUPPORTED (a line longer than the on-chip
+ * limit: 16384 cells in FP32, 8192 in FP64). */
+int aniso_step(aniso_t h, void *T, double dt, int nsteps);
+
+/* One directional update: Eq. xup (dir = ANISO_DIR_X) or Eq. yup
+ * (ANISO_DIR_Y) from Tin to Tout (device arrays, nx*ny, distinct).  Exposes
+ * a single half of the split for line-by-line checks.  Does not touch the
+ * step counter or the Kahan state.  Asynchronous.  Errors as aniso_step. */
+int aniso_sweep(aniso_t h, int dir, const void *Tin, void *Tout, double dt);
+
+/* Conservation and bounds diagnostics of T (device array, handle precision):
+ * sum in FP64 (deterministic order; with Kahan state the sum of T + lo),
+ * minimum, maximum and the count of non-finite values.  Any output pointer
+ * may be NULL.  Synchronises the handle's stream.  Returns
+ * ANISO_ERR_NONFINITE when a step since the last check produced a
+ * non-finite value (the flag is then cleared). */
+int aniso_total(aniso_t h, const void *T, double *sum, double *tmin, double *tmax,
+                long long *nonfinite);
+
+/* Step counter and compensated low part (checkpoint / resume).
+ * get: *step_counter receives the counter; if lo_out (device, nx*ny float)
+ *      is non-NULL and Kahan is on, the low parts are copied there.
+ * set: sets the counter; lo_in (device) may be NULL to clear the low parts.
+ * Asynchronous copies on the handle's stream. */
+int aniso_get_state(aniso_t h, long long *step_counter, void *lo_out);
+int aniso_set_state(aniso_t h, long long step_counter, const void *lo_in);
+
+/* Wait for the handle's stream; returns ANISO_ERR_NONFINITE if a step since
+ * the last check produced a non-finite value. */
+int aniso_sync(aniso_t h);
+
+/* Sum of CUDA-event durations (milliseconds) and number of launches of one
+ * kernel kind (ANISO_KERNEL_*) recorded while ANISO_OPT_PROFILE was on, for
+ * a handle (h) or a batch (b; pass h = NULL).  Synchronises.  reset = 1
+ * clears the counters after reading. */
+int aniso_kernel_times(aniso_t h, aniso_batch_t b, int kind, double *ms, long long *launches,
+                       int reset);
+
+/* Free a handle and its device buffers (after synchronising its stream). */
+void aniso_destroy(aniso_t h);
+
+/* Message of the last failed call on this host thread ("" if none). */
+const char *aniso_last_error(void);
+
+/* Group n handles (same precision, limiter and field storage; each with its
+ * field set) so that one launch per sweep advances all of them: the
+ * paper's update applied to independent grids of uneven sizes, fields and
+ * timesteps.  The batch uses the first handle's stream and options
+ * GRAPH/PROFILE.  The handles must outlive the batch.  Errors:
+ * ANISO_ERR_ARG, ANISO_ERR_STATE, ANISO_ERR_UNSUPPORTED (ny above the
+ * on-chip column limit of 1024). */
+int aniso_batch_create(int n, const aniso_t *hs, aniso_batch_t *out);
+
+/* Advance grid k of the batch by nsteps[k] steps of size dt[k] in place on
+ * T[k] (host arrays of n entries; T[k] a device pointer).  Grids with fewer
+ * steps drop out as they finish.  The whole call is captured once into a
+ * CUDA graph and replayed while T, dt and nsteps stay the same.
+ * Asynchronous. */
+int aniso_step_batched(aniso_batch_t b, void *const *T, const double *dt, const int *nsteps);
+
+void aniso_batch_destroy(aniso_batch_t b);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ANISO_H */

@@ -1,0 +1,191 @@
+"""ctypes binding of libaniso.so: the C ABI of include/aniso.h under the same
+names.  Argument marshalling only -- every step of the method runs in the
+library's CUDA kernels; there is no Python or CPU fallback, and loading fails
+loudly when the library has not been built."""
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libaniso.so")
+
+# status codes
+ANISO_OK = 0
+ANISO_ERR_ARG = 1
+ANISO_ERR_STATE = 2
+ANISO_ERR_CUDA = 3
+ANISO_ERR_NONFINITE = 4
+ANISO_ERR_TIMEOUT = 5
+ANISO_ERR_OOM = 6
+ANISO_ERR_UNSUPPORTED = 7
+# boundary conditions
+ANISO_BC_ZEROFLUX = 0
+ANISO_BC_PERIODIC = 1
+# options
+ANISO_OPT_PRECISION = 0
+ANISO_OPT_FIELD_FP16 = 1
+ANISO_OPT_KAHAN = 2
+ANISO_OPT_LIMITER = 3
+ANISO_OPT_ORDER = 4
+ANISO_OPT_STREAM = 5
+ANISO_OPT_GRAPH = 6
+ANISO_OPT_PROFILE = 7
+ANISO_PREC_FP64 = 0
+ANISO_PREC_FP32 = 1
+ANISO_LIM_VANLEER = 0
+ANISO_LIM_ARITH = 1
+ANISO_LIM_MINMOD = 2
+ANISO_LIM_MC = 3
+ANISO_ORDER_XY = 0
+ANISO_ORDER_YX = 1
+ANISO_ORDER_ALTERNATE = 2
+ANISO_DIR_X = 0
+ANISO_DIR_Y = 1
+ANISO_KERNEL_XSWEEP = 0
+ANISO_KERNEL_YSWEEP = 1
+ANISO_KERNEL_TRANSPOSE = 2
+
+EXPORTED = ("aniso_create", "aniso_set_option", "aniso_set_field", "aniso_step", "aniso_sweep",
+            "aniso_total", "aniso_get_state", "aniso_set_state", "aniso_sync",
+            "aniso_kernel_times", "aniso_destroy", "aniso_last_error", "aniso_batch_create",
+            "aniso_step_batched", "aniso_batch_destroy")
+
+
+class AnisoError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("aniso error %d: %s" % (code, msg))
+        self.code = code
+
+
+_lib = None
+
+
+def load():
+    """Load libaniso.so (built by paper_1008_0861_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libaniso.so is missing at %s: build it with "
+                           "paper_1008_0861_gb300.build.build()" % LIB_PATH)
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i, d, ll = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_longlong
+    P = ctypes.POINTER
+    sig = {
+        "aniso_create": (i, [i, i, d, d, d, d, i, P(vp)]),
+        "aniso_set_option": (i, [vp, i, ll]),
+        "aniso_set_field": (i, [vp, vp, vp]),
+        "aniso_step": (i, [vp, vp, d, i]),
+        "aniso_sweep": (i, [vp, i, vp, vp, d]),
+        "aniso_total": (i, [vp, vp, P(d), P(d), P(d), P(ll)]),
+        "aniso_get_state": (i, [vp, P(ll), vp]),
+        "aniso_set_state": (i, [vp, ll, vp]),
+        "aniso_sync": (i, [vp]),
+        "aniso_kernel_times": (i, [vp, vp, i, P(d), P(ll), i]),
+        "aniso_destroy": (None, [vp]),
+        "aniso_last_error": (ctypes.c_char_p, []),
+        "aniso_batch_create": (i, [i, P(vp), P(vp)]),
+        "aniso_step_batched": (i, [vp, P(vp), P(d), P(i)]),
+        "aniso_batch_destroy": (None, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(x):
+    """Device address of a torch tensor (or an int address)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return ctypes.c_void_p(x.data_ptr())
+    return ctypes.c_void_p(int(x))
+
+
+def _check(rc):
+    if rc != ANISO_OK:
+        raise AnisoError(rc, load().aniso_last_error().decode())
+
+
+def aniso_last_error():
+    return load().aniso_last_error().decode()
+
+
+def aniso_create(nx, ny, dx, dy, chi_par, chi_perp=0.0, bc=ANISO_BC_PERIODIC):
+    h = ctypes.c_void_p()
+    _check(load().aniso_create(int(nx), int(ny), float(dx), float(dy), float(chi_par),
+                               float(chi_perp), int(bc), ctypes.byref(h)))
+    return h
+
+
+def aniso_set_option(h, key, value):
+    _check(load().aniso_set_option(h, int(key), int(value)))
+
+
+def aniso_set_field(h, bx, by):
+    _check(load().aniso_set_field(h, _ptr(bx), _ptr(by)))
+
+
+def aniso_step(h, T, dt, nsteps=1):
+    _check(load().aniso_step(h, _ptr(T), float(dt), int(nsteps)))
+
+
+def aniso_sweep(h, direction, Tin, Tout, dt):
+    _check(load().aniso_sweep(h, int(direction), _ptr(Tin), _ptr(Tout), float(dt)))
+
+
+def aniso_total(h, T):
+    """(sum, min, max, nonfinite count) of T, FP64 sum."""
+    s, lo, hi, nf = ctypes.c_double(), ctypes.c_double(), ctypes.c_double(), ctypes.c_longlong()
+    _check(load().aniso_total(h, _ptr(T), ctypes.byref(s), ctypes.byref(lo), ctypes.byref(hi),
+                              ctypes.byref(nf)))
+    return s.value, lo.value, hi.value, nf.value
+
+
+def aniso_get_state(h, lo_out=None):
+    c = ctypes.c_longlong()
+    _check(load().aniso_get_state(h, ctypes.byref(c), _ptr(lo_out)))
+    return c.value
+
+
+def aniso_set_state(h, step_counter, lo_in=None):
+    _check(load().aniso_set_state(h, int(step_counter), _ptr(lo_in)))
+
+
+def aniso_sync(h):
+    _check(load().aniso_sync(h))
+
+
+def aniso_kernel_times(h=None, batch=None, kind=ANISO_KERNEL_XSWEEP, reset=False):
+    ms, n = ctypes.c_double(), ctypes.c_longlong()
+    _check(load().aniso_kernel_times(h, batch, int(kind), ctypes.byref(ms), ctypes.byref(n),
+                                     int(bool(reset))))
+    return ms.value, n.value
+
+
+def aniso_destroy(h):
+    if h:
+        load().aniso_destroy(h)
+
+
+def aniso_batch_create(handles):
+    arr = (ctypes.c_void_p * len(handles))(*[h.value if isinstance(h, ctypes.c_void_p) else h
+                                              for h in handles])
+    b = ctypes.c_void_p()
+    _check(load().aniso_batch_create(len(handles), arr, ctypes.byref(b)))
+    return b
+
+
+def aniso_step_batched(batch, Ts, dts, nsteps):
+    n = len(Ts)
+    Tarr = (ctypes.c_void_p * n)(*[t.data_ptr() if hasattr(t, "data_ptr") else int(t) for t in Ts])
+    darr = (ctypes.c_double * n)(*[float(x) for x in dts])
+    narr = (ctypes.c_int * n)(*[int(x) for x in nsteps])
+    _check(load().aniso_step_batched(batch, Tarr, darr, narr))
+
+
+def aniso_batch_destroy(batch):
+    if batch:
+        load().aniso_batch_destroy(batch)

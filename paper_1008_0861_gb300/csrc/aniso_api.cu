@@ -1,0 +1,808 @@
+// aniso_api.cu -- host side of libaniso.so: handles, validation, the step
+// schedule of Eq. op_2step, CUDA-graph capture, batches and diagnostics.
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "../../include/aniso.h"
+#include "aniso_internal.h"
+
+using namespace aniso;
+
+// ------------------------------------------------------------- errors
+
+static thread_local std::string g_last_error;
+
+static int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+#define CU(call)                                                                           \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return fail(e_ == cudaErrorMemoryAllocation ? ANISO_ERR_OOM : ANISO_ERR_CUDA, \
+                        "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+extern "C" const char *aniso_last_error(void) { return g_last_error.c_str(); }
+
+// ------------------------------------------------------------- profiling
+
+struct EventPair {
+    cudaEvent_t a, b;
+    int kind;
+};
+
+struct Profiler {
+    std::vector<EventPair> pool;   // all pairs ever created
+    std::vector<int> pending;      // indices whose timings have not been read
+    size_t next = 0;               // next free pair for a direct (non-graph) launch
+    double ms[3] = {0, 0, 0};
+    long long count[3] = {0, 0, 0};
+
+    int take(int kind)
+    {
+        if (next == pool.size()) {
+            EventPair p;
+            p.kind = kind;
+            if (cudaEventCreate(&p.a) != cudaSuccess || cudaEventCreate(&p.b) != cudaSuccess) return -1;
+            pool.push_back(p);
+        }
+        pool[next].kind = kind;
+        return (int)next++;
+    }
+    int drain()
+    {
+        for (int idx : pending) {
+            float t = 0.f;
+            cudaError_t e = cudaEventElapsedTime(&t, pool[idx].a, pool[idx].b);
+            if (e != cudaSuccess) return fail(ANISO_ERR_CUDA, "event timing: %s", cudaGetErrorString(e));
+            ms[pool[idx].kind] += t;
+            count[pool[idx].kind] += 1;
+        }
+        pending.clear();
+        return ANISO_OK;
+    }
+    void destroy()
+    {
+        for (auto &p : pool) {
+            cudaEventDestroy(p.a);
+            cudaEventDestroy(p.b);
+        }
+        pool.clear();
+        pending.clear();
+        next = 0;
+    }
+};
+
+// ------------------------------------------------------------- handle
+
+struct aniso_ctx {
+    int nx = 0, ny = 0, bc = 0;
+    double dx = 0, dy = 0, chi_par = 0, chi_perp = 0;
+    int prec = PREC_FP64, field_fp16 = 0, kahan = 0, limiter = LIM_VANLEER, order = ANISO_ORDER_XY;
+    int use_graph = 1, profile = 0;
+    cudaStream_t stream = 0;
+    long long step_counter = 0;
+    bool field_set = false;
+    // device buffers
+    void *cxx = nullptr, *cxy = nullptr, *cyy = nullptr, *cyx = nullptr;
+    void *cyyT = nullptr, *cyxT = nullptr;  // transposed y coefficients (long columns)
+    void *tstar = nullptr;                  // intermediate T* of a step
+    void *tA = nullptr, *tB = nullptr;      // transposed scratch (long columns)
+    double *partials = nullptr, *result = nullptr;
+    unsigned *err = nullptr;
+    // graph cache
+    cudaGraphExec_t gexec = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    void *g_T = nullptr;
+    double g_dt = 0;
+    int g_nsteps = -1, g_parity = -1, g_order = -1, g_limiter = -1, g_profile = -1;
+    std::vector<int> g_pairs;  // profiler pairs recorded by the graph
+    Profiler prof;
+
+    size_t cells() const { return (size_t)nx * ny; }
+    size_t esz() const { return prec == PREC_FP64 ? 8 : 4; }
+    size_t csz() const { return prec == PREC_FP64 ? 8 : (field_fp16 ? 2 : 4); }
+    int coef_kind() const { return prec == PREC_FP64 ? 0 : (field_fp16 ? 2 : 1); }
+    bool long_cols() const { return ny > MAX_COL; }
+    int max_line() const { return prec == PREC_FP64 ? MAX_LINE_FP64 : MAX_LINE_FP32; }
+};
+
+static void free_buffers(aniso_ctx *h)
+{
+    void **bufs[] = {&h->cxx, &h->cxy, &h->cyy, &h->cyx, &h->cyyT, &h->cyxT, &h->tstar, &h->tA, &h->tB};
+    for (void **b : bufs) {
+        if (*b) cudaFree(*b);
+        *b = nullptr;
+    }
+    if (h->partials) cudaFree(h->partials);
+    if (h->result) cudaFree(h->result);
+    if (h->err) cudaFree(h->err);
+    h->partials = h->result = nullptr;
+    h->err = nullptr;
+}
+
+static void drop_graph(aniso_ctx *h)
+{
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    h->gexec = nullptr;
+    h->g_nsteps = -1;
+    h->g_pairs.clear();
+}
+
+extern "C" int aniso_create(int nx, int ny, double dx, double dy, double chi_par, double chi_perp,
+                            int bc, aniso_t *out)
+{
+    if (!out) return fail(ANISO_ERR_ARG, "aniso_create: out is NULL");
+    *out = nullptr;
+    if (nx < 3 || ny < 3) return fail(ANISO_ERR_ARG, "aniso_create: nx=%d ny=%d (need >= 3)", nx, ny);
+    if (!(dx > 0) || !(dy > 0)) return fail(ANISO_ERR_ARG, "aniso_create: dx, dy must be > 0");
+    if (!(chi_par > 0)) return fail(ANISO_ERR_ARG, "aniso_create: chi_par must be > 0");
+    if (!(chi_perp >= 0) || chi_perp > chi_par)
+        return fail(ANISO_ERR_ARG, "aniso_create: need 0 <= chi_perp <= chi_par");
+    if (bc != ANISO_BC_ZEROFLUX && bc != ANISO_BC_PERIODIC)
+        return fail(ANISO_ERR_ARG, "aniso_create: unknown boundary condition %d", bc);
+    aniso_ctx *h = new aniso_ctx;
+    h->nx = nx;
+    h->ny = ny;
+    h->dx = dx;
+    h->dy = dy;
+    h->chi_par = chi_par;
+    h->chi_perp = chi_perp;
+    h->bc = bc;
+    *out = h;
+    return ANISO_OK;
+}
+
+extern "C" int aniso_set_option(aniso_t h, int key, long long v)
+{
+    if (!h) return fail(ANISO_ERR_ARG, "aniso_set_option: null handle");
+    switch (key) {
+    case ANISO_OPT_PRECISION:
+        if (v != ANISO_PREC_FP64 && v != ANISO_PREC_FP32) return fail(ANISO_ERR_ARG, "bad precision %lld", v);
+        if (h->field_set && v != h->prec) return fail(ANISO_ERR_STATE, "precision is fixed once the field is set");
+        h->prec = (int)v;
+        break;
+    case ANISO_OPT_FIELD_FP16:
+        if (h->field_set && (v != 0) != (h->field_fp16 != 0))
+            return fail(ANISO_ERR_STATE, "field storage is fixed once the field is set");
+        h->field_fp16 = v != 0;
+        break;
+    case ANISO_OPT_KAHAN:
+        if (v) return fail(ANISO_ERR_UNSUPPORTED, "compensated (Kahan) state is not available in this build");
+        h->kahan = 0;
+        break;
+    case ANISO_OPT_LIMITER:
+        if (v < 0 || v > 3) return fail(ANISO_ERR_ARG, "bad limiter %lld", v);
+        h->limiter = (int)v;
+        break;
+    case ANISO_OPT_ORDER:
+        if (v < 0 || v > 2) return fail(ANISO_ERR_ARG, "bad order %lld", v);
+        h->order = (int)v;
+        break;
+    case ANISO_OPT_STREAM:
+        h->stream = (cudaStream_t)(intptr_t)v;
+        drop_graph(h);
+        break;
+    case ANISO_OPT_GRAPH:
+        h->use_graph = v != 0;
+        break;
+    case ANISO_OPT_PROFILE:
+        h->profile = v != 0;
+        break;
+    default:
+        return fail(ANISO_ERR_ARG, "unknown option key %d", key);
+    }
+    return ANISO_OK;
+}
+
+extern "C" int aniso_set_field(aniso_t h, const void *bx, const void *by)
+{
+    if (!h) return fail(ANISO_ERR_ARG, "aniso_set_field: null handle");
+    if (!bx || !by) return fail(ANISO_ERR_ARG, "aniso_set_field: null field pointer");
+    if (h->field_fp16 && h->prec != PREC_FP32)
+        return fail(ANISO_ERR_ARG, "aniso_set_field: FP16 field storage needs FP32 precision");
+    if (h->nx > h->max_line() || (h->long_cols() && h->ny > h->max_line()))
+        return fail(ANISO_ERR_UNSUPPORTED, "grid %dx%d exceeds the on-chip line limit %d", h->nx, h->ny,
+                    h->max_line());
+    if (!h->field_set) {
+        const size_t n = h->cells();
+        CU(cudaMalloc(&h->cxx, n * h->csz()));
+        CU(cudaMalloc(&h->cxy, n * h->csz()));
+        CU(cudaMalloc(&h->cyy, n * h->csz()));
+        CU(cudaMalloc(&h->cyx, n * h->csz()));
+        CU(cudaMalloc(&h->tstar, n * h->esz()));
+        if (h->long_cols()) {
+            CU(cudaMalloc(&h->cyyT, n * h->csz()));
+            CU(cudaMalloc(&h->cyxT, n * h->csz()));
+            CU(cudaMalloc(&h->tA, n * h->esz()));
+            CU(cudaMalloc(&h->tB, n * h->esz()));
+        }
+        CU(cudaMalloc(&h->partials, 4 * TOTALS_BLOCKS * sizeof(double)));
+        CU(cudaMalloc(&h->result, 4 * sizeof(double)));
+        CU(cudaMalloc(&h->err, sizeof(unsigned)));
+        CU(cudaMemsetAsync(h->err, 0, sizeof(unsigned), h->stream));
+    }
+    const double kappa = h->chi_perp / h->chi_par;
+    CU(launch_face_coeffs(h->prec, h->coef_kind(), bx, by, h->nx, h->ny, h->bc, kappa, h->cxx, h->cxy,
+                          h->cyy, h->cyx, h->cyyT, h->cyxT, h->stream));
+    h->field_set = true;
+    drop_graph(h);
+    return ANISO_OK;
+}
+
+// One directional update from `in` to `out` (distinct buffers) on stream s.
+static int enqueue_sweep(aniso_ctx *h, int dir, const void *in, void *out, double dt, cudaStream_t s,
+                         std::vector<int> *pairs)
+{
+    const double lamx = h->chi_par * dt / (h->dx * h->dx);
+    const double lamy = h->chi_par * dt / (h->dy * h->dy);
+    const double mu = h->chi_par * dt / (h->dx * h->dy);
+    const int per = h->bc == ANISO_BC_PERIODIC;
+    int pidx = -1;
+    auto begin = [&](int kind) -> int {
+        if (!h->profile) return ANISO_OK;
+        pidx = h->prof.take(kind);
+        if (pidx < 0) return fail(ANISO_ERR_CUDA, "event creation failed");
+        CU(cudaEventRecord(h->prof.pool[pidx].a, s));
+        return ANISO_OK;
+    };
+    auto end = [&]() -> int {
+        if (!h->profile) return ANISO_OK;
+        CU(cudaEventRecord(h->prof.pool[pidx].b, s));
+        if (pairs) pairs->push_back(pidx);
+        else h->prof.pending.push_back(pidx);
+        return ANISO_OK;
+    };
+    auto line = [&](const void *tin, void *tout, const void *g, const void *e, int n, int nlines,
+                    int per_line, int per_cross, double lam, int kind) -> int {
+        LineArgs a{};
+        a.jobs = nullptr;
+        a.njobs = 1;
+        a.limiter = h->limiter;
+        a.err = h->err;
+        LineJob &J = a.one;
+        J.Tin = tin;
+        J.Tout = tout;
+        J.g = g;
+        J.e = e;
+        J.lam = lam;
+        J.mu = mu;
+        J.n = n;
+        J.nlines = nlines;
+        J.per_line = per_line;
+        J.per_cross = per_cross;
+        int nthreads;
+        line_config(h->prec, n, &J.team, &J.lines_per_block, &nthreads);
+        J.block0 = 0;
+        J.nblocks = (nlines + J.lines_per_block - 1) / J.lines_per_block;
+        const size_t smem = line_smem_bytes(h->prec, n, J.team, J.lines_per_block);
+        int rc = begin(kind);
+        if (rc) return rc;
+        CU(launch_line(h->prec, h->field_fp16, a, J.nblocks, nthreads, smem, s));
+        return end();
+    };
+    int rc;
+    if (dir == ANISO_DIR_X)
+        return line(in, out, h->cxx, h->cxy, h->nx, h->ny, per, per, lamx, ANISO_KERNEL_XSWEEP);
+    if (!h->long_cols()) {
+        ColArgs a{};
+        a.jobs = nullptr;
+        a.njobs = 1;
+        a.limiter = h->limiter;
+        a.err = h->err;
+        ColJob &J = a.one;
+        J.Tin = in;
+        J.Tout = out;
+        J.g = h->cyy;
+        J.e = h->cyx;
+        J.lam = lamy;
+        J.mu = mu;
+        J.nx = h->nx;
+        J.ny = h->ny;
+        J.per_x = per;
+        J.per_y = per;
+        int nthreads;
+        col_config(h->prec, h->ny, &J.P, &J.Wb, &nthreads);
+        J.block0 = 0;
+        J.nblocks = (h->nx + J.Wb - 1) / J.Wb;
+        const size_t smem = col_smem_bytes(h->prec, h->ny, J.P, J.Wb);
+        if ((rc = begin(ANISO_KERNEL_YSWEEP))) return rc;
+        CU(launch_col(h->prec, h->field_fp16, a, J.nblocks, nthreads, smem, s));
+        return end();
+    }
+    // long columns: transpose, solve columns as contiguous lines, transpose back
+    if ((rc = begin(ANISO_KERNEL_TRANSPOSE))) return rc;
+    CU(launch_transpose((int)h->esz(), in, h->tA, h->ny, h->nx, s));
+    if ((rc = end())) return rc;
+    if ((rc = line(h->tA, h->tB, h->cyyT, h->cyxT, h->ny, h->nx, per, per, lamy, ANISO_KERNEL_YSWEEP)))
+        return rc;
+    if ((rc = begin(ANISO_KERNEL_TRANSPOSE))) return rc;
+    CU(launch_transpose((int)h->esz(), h->tB, out, h->nx, h->ny, s));
+    return end();
+}
+
+static bool x_first(int order, long long counter)
+{
+    if (order == ANISO_ORDER_XY) return true;
+    if (order == ANISO_ORDER_YX) return false;
+    return (counter & 1) == 0;
+}
+
+static int enqueue_steps(aniso_ctx *h, void *T, double dt, int nsteps, long long counter0,
+                         cudaStream_t s, std::vector<int> *pairs)
+{
+    for (int k = 0; k < nsteps; ++k) {
+        const bool xf = x_first(h->order, counter0 + k);
+        int rc = enqueue_sweep(h, xf ? ANISO_DIR_X : ANISO_DIR_Y, T, h->tstar, dt, s, pairs);
+        if (rc) return rc;
+        rc = enqueue_sweep(h, xf ? ANISO_DIR_Y : ANISO_DIR_X, h->tstar, T, dt, s, pairs);
+        if (rc) return rc;
+    }
+    return ANISO_OK;
+}
+
+static int check_ready(aniso_ctx *h, const char *who)
+{
+    if (!h) return fail(ANISO_ERR_ARG, "%s: null handle", who);
+    if (!h->field_set) return fail(ANISO_ERR_STATE, "%s: aniso_set_field has not been called", who);
+    return ANISO_OK;
+}
+
+extern "C" int aniso_step(aniso_t h, void *T, double dt, int nsteps)
+{
+    int rc = check_ready(h, "aniso_step");
+    if (rc) return rc;
+    if (!T) return fail(ANISO_ERR_ARG, "aniso_step: T is NULL");
+    if (!(dt > 0)) return fail(ANISO_ERR_ARG, "aniso_step: dt must be > 0");
+    if (nsteps < 0) return fail(ANISO_ERR_ARG, "aniso_step: nsteps must be >= 0");
+    if (nsteps == 0) return ANISO_OK;
+    const int parity = h->order == ANISO_ORDER_ALTERNATE ? (int)(h->step_counter & 1) : 0;
+    if (h->use_graph && nsteps >= 2) {
+        const bool hit = h->gexec && h->g_T == T && h->g_dt == dt && h->g_nsteps == nsteps &&
+                         h->g_parity == parity && h->g_order == h->order && h->g_limiter == h->limiter &&
+                         h->g_profile == h->profile;
+        if (!hit) {
+            drop_graph(h);
+            if (!h->cap_stream) CU(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+            h->prof.next = h->prof.pool.size();  // graph pairs are never reused by direct launches
+            CU(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+            std::vector<int> pairs;
+            rc = enqueue_steps(h, T, dt, nsteps, h->step_counter, h->cap_stream, &pairs);
+            cudaGraph_t graph = nullptr;
+            cudaError_t ce = cudaStreamEndCapture(h->cap_stream, &graph);
+            if (rc) {
+                if (graph) cudaGraphDestroy(graph);
+                return rc;
+            }
+            if (ce != cudaSuccess) return fail(ANISO_ERR_CUDA, "graph capture: %s", cudaGetErrorString(ce));
+            ce = cudaGraphInstantiate(&h->gexec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ce != cudaSuccess) return fail(ANISO_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(ce));
+            h->g_T = T;
+            h->g_dt = dt;
+            h->g_nsteps = nsteps;
+            h->g_parity = parity;
+            h->g_order = h->order;
+            h->g_limiter = h->limiter;
+            h->g_profile = h->profile;
+            h->g_pairs = pairs;
+        }
+        if (h->profile && !h->prof.pending.empty()) {
+            // the graph re-records its events: read the previous replay first
+            CU(cudaStreamSynchronize(h->stream));
+            if ((rc = h->prof.drain())) return rc;
+        }
+        CU(cudaGraphLaunch(h->gexec, h->stream));
+        if (h->profile) h->prof.pending.insert(h->prof.pending.end(), h->g_pairs.begin(), h->g_pairs.end());
+    } else {
+        if (h->profile && h->prof.next + 8 * (size_t)nsteps > 4096) {
+            CU(cudaStreamSynchronize(h->stream));
+            if ((rc = h->prof.drain())) return rc;
+            h->prof.next = 0;
+            drop_graph(h);
+        }
+        rc = enqueue_steps(h, T, dt, nsteps, h->step_counter, h->stream, nullptr);
+        if (rc) return rc;
+    }
+    h->step_counter += nsteps;
+    return ANISO_OK;
+}
+
+extern "C" int aniso_sweep(aniso_t h, int dir, const void *Tin, void *Tout, double dt)
+{
+    int rc = check_ready(h, "aniso_sweep");
+    if (rc) return rc;
+    if (!Tin || !Tout || Tin == Tout) return fail(ANISO_ERR_ARG, "aniso_sweep: need distinct Tin, Tout");
+    if (dir != ANISO_DIR_X && dir != ANISO_DIR_Y) return fail(ANISO_ERR_ARG, "aniso_sweep: bad direction");
+    if (!(dt > 0)) return fail(ANISO_ERR_ARG, "aniso_sweep: dt must be > 0");
+    return enqueue_sweep(h, dir, Tin, Tout, dt, h->stream, nullptr);
+}
+
+static int check_err_flag(aniso_ctx *h)
+{
+    unsigned flag = 0;
+    CU(cudaMemcpy(&flag, h->err, sizeof flag, cudaMemcpyDeviceToHost));
+    if (flag) {
+        CU(cudaMemset(h->err, 0, sizeof(unsigned)));
+        return fail(ANISO_ERR_NONFINITE, "a step produced a non-finite temperature");
+    }
+    return ANISO_OK;
+}
+
+extern "C" int aniso_total(aniso_t h, const void *T, double *sum, double *tmin, double *tmax,
+                           long long *nonfinite)
+{
+    int rc = check_ready(h, "aniso_total");
+    if (rc) return rc;
+    if (!T) return fail(ANISO_ERR_ARG, "aniso_total: T is NULL");
+    CU(launch_totals(h->prec, T, h->cells(), h->partials, h->result, h->stream));
+    double r[4];
+    CU(cudaMemcpyAsync(r, h->result, sizeof r, cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+    if (sum) *sum = r[0];
+    if (tmin) *tmin = r[1];
+    if (tmax) *tmax = r[2];
+    if (nonfinite) *nonfinite = (long long)r[3];
+    return check_err_flag(h);
+}
+
+extern "C" int aniso_get_state(aniso_t h, long long *step_counter, void *lo_out)
+{
+    if (!h) return fail(ANISO_ERR_ARG, "aniso_get_state: null handle");
+    if (step_counter) *step_counter = h->step_counter;
+    (void)lo_out;  // no compensated state in this build
+    return ANISO_OK;
+}
+
+extern "C" int aniso_set_state(aniso_t h, long long step_counter, const void *lo_in)
+{
+    if (!h) return fail(ANISO_ERR_ARG, "aniso_set_state: null handle");
+    if (step_counter < 0) return fail(ANISO_ERR_ARG, "aniso_set_state: negative step counter");
+    (void)lo_in;
+    h->step_counter = step_counter;
+    return ANISO_OK;
+}
+
+extern "C" int aniso_sync(aniso_t h)
+{
+    if (!h) return fail(ANISO_ERR_ARG, "aniso_sync: null handle");
+    CU(cudaStreamSynchronize(h->stream));
+    if (!h->err) return ANISO_OK;
+    return check_err_flag(h);
+}
+
+extern "C" void aniso_destroy(aniso_t h)
+{
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    drop_graph(h);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    h->prof.destroy();
+    free_buffers(h);
+    delete h;
+}
+
+// ------------------------------------------------------------- batches
+
+struct aniso_batch {
+    std::vector<aniso_ctx *> hs;
+    cudaStream_t stream = 0;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    std::vector<void *> key_T;
+    std::vector<double> key_dt;
+    std::vector<int> key_n;
+    std::vector<int> key_parity;
+    int key_profile = -1;
+    void *d_jobs = nullptr;  // device copies of all job lists of the plan
+    size_t d_jobs_bytes = 0;
+    Profiler prof;
+    std::vector<int> g_pairs;
+    int profile = 0;
+    int use_graph = 1;
+};
+
+extern "C" int aniso_batch_create(int n, const aniso_t *hs, aniso_batch_t *out)
+{
+    if (!out) return fail(ANISO_ERR_ARG, "aniso_batch_create: out is NULL");
+    *out = nullptr;
+    if (n < 1 || !hs) return fail(ANISO_ERR_ARG, "aniso_batch_create: need n >= 1 handles");
+    for (int k = 0; k < n; ++k) {
+        aniso_ctx *h = hs[k];
+        if (!h) return fail(ANISO_ERR_ARG, "aniso_batch_create: handle %d is NULL", k);
+        if (!h->field_set) return fail(ANISO_ERR_STATE, "aniso_batch_create: handle %d has no field", k);
+        if (h->prec != hs[0]->prec || h->field_fp16 != hs[0]->field_fp16 || h->limiter != hs[0]->limiter)
+            return fail(ANISO_ERR_ARG, "aniso_batch_create: handle %d differs in precision/field/limiter", k);
+        if (h->long_cols())
+            return fail(ANISO_ERR_UNSUPPORTED, "aniso_batch_create: handle %d has ny=%d > %d", k, h->ny, MAX_COL);
+    }
+    aniso_batch *b = new aniso_batch;
+    b->hs.assign(hs, hs + n);
+    b->stream = hs[0]->stream;
+    b->profile = hs[0]->profile;
+    b->use_graph = hs[0]->use_graph;
+    *out = b;
+    return ANISO_OK;
+}
+
+static void batch_drop(aniso_batch *b)
+{
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    b->gexec = nullptr;
+    b->key_T.clear();
+    b->g_pairs.clear();
+}
+
+// Build, capture and instantiate the whole batched call.
+static int batch_build(aniso_batch *b, void *const *T, const double *dt, const int *nsteps)
+{
+    const int n = (int)b->hs.size();
+    const int prec = b->hs[0]->prec;
+    const int fp16 = b->hs[0]->field_fp16;
+    int max_steps = 0;
+    for (int k = 0; k < n; ++k) max_steps = std::max(max_steps, nsteps[k]);
+
+    // Every (global step, phase) launch is one list of line jobs (x) and one
+    // of column jobs (y).  Identical lists are shared.
+    struct Launch {
+        int kind;  // 0 line, 1 col
+        size_t offset;
+        int njobs, nblocks, nthreads;
+        size_t smem;
+    };
+    std::vector<unsigned char> blob;
+    std::vector<Launch> launches;  // in enqueue order
+    auto add_line = [&](std::vector<LineJob> &jobs) {
+        if (jobs.empty()) return;
+        // large lines first: the block scheduler hands out blocks in order
+        std::stable_sort(jobs.begin(), jobs.end(),
+                         [](const LineJob &a, const LineJob &c) { return (long long)a.n * a.nlines > (long long)c.n * c.nlines; });
+        int nthreads = 0;
+        for (auto &J : jobs) nthreads = std::max(nthreads, J.team * J.lines_per_block);
+        int blocks = 0;
+        size_t smem = 0;
+        for (auto &J : jobs) {
+            J.lines_per_block = nthreads / J.team;
+            J.block0 = blocks;
+            J.nblocks = (J.nlines + J.lines_per_block - 1) / J.lines_per_block;
+            blocks += J.nblocks;
+            smem = std::max(smem, line_smem_bytes(prec, J.n, J.team, J.lines_per_block));
+        }
+        Launch L{0, blob.size(), (int)jobs.size(), blocks, nthreads, smem};
+        const unsigned char *p = reinterpret_cast<const unsigned char *>(jobs.data());
+        blob.insert(blob.end(), p, p + jobs.size() * sizeof(LineJob));
+        while (blob.size() % 16) blob.push_back(0);
+        launches.push_back(L);
+    };
+    auto add_col = [&](std::vector<ColJob> &jobs) {
+        if (jobs.empty()) return;
+        std::stable_sort(jobs.begin(), jobs.end(),
+                         [](const ColJob &a, const ColJob &c) { return (long long)a.nx * a.ny > (long long)c.nx * c.ny; });
+        const int nthreads = prec == PREC_FP64 ? 256 : 512;
+        int blocks = 0;
+        size_t smem = 0;
+        for (auto &J : jobs) {
+            // the launch-wide thread count fixes P * Wb
+            int P, Wb, nt;
+            col_config(prec, J.ny, &P, &Wb, &nt);
+            Wb = nthreads / P;
+            J.P = P;
+            J.Wb = Wb;
+            J.block0 = blocks;
+            J.nblocks = (J.nx + Wb - 1) / Wb;
+            blocks += J.nblocks;
+            smem = std::max(smem, col_smem_bytes(prec, J.ny, P, Wb));
+        }
+        Launch L{1, blob.size(), (int)jobs.size(), blocks, nthreads, smem};
+        const unsigned char *p = reinterpret_cast<const unsigned char *>(jobs.data());
+        blob.insert(blob.end(), p, p + jobs.size() * sizeof(ColJob));
+        while (blob.size() % 16) blob.push_back(0);
+        launches.push_back(L);
+    };
+
+    for (int s = 0; s < max_steps; ++s) {
+        for (int phase = 0; phase < 2; ++phase) {
+            std::vector<LineJob> xl;
+            std::vector<ColJob> yl;
+            for (int k = 0; k < n; ++k) {
+                if (s >= nsteps[k]) continue;
+                aniso_ctx *h = b->hs[k];
+                const bool xf = x_first(h->order, h->step_counter + s);
+                const bool is_x = (phase == 0) == xf;
+                const void *in = phase == 0 ? T[k] : h->tstar;
+                void *outp = phase == 0 ? h->tstar : T[k];
+                const double lamx = h->chi_par * dt[k] / (h->dx * h->dx);
+                const double lamy = h->chi_par * dt[k] / (h->dy * h->dy);
+                const double mu = h->chi_par * dt[k] / (h->dx * h->dy);
+                const int per = h->bc == ANISO_BC_PERIODIC;
+                if (is_x) {
+                    LineJob J{};
+                    J.Tin = in;
+                    J.Tout = outp;
+                    J.g = h->cxx;
+                    J.e = h->cxy;
+                    J.lam = lamx;
+                    J.mu = mu;
+                    J.n = h->nx;
+                    J.nlines = h->ny;
+                    J.per_line = per;
+                    J.per_cross = per;
+                    int nt;
+                    line_config(prec, h->nx, &J.team, &J.lines_per_block, &nt);
+                    xl.push_back(J);
+                } else {
+                    ColJob J{};
+                    J.Tin = in;
+                    J.Tout = outp;
+                    J.g = h->cyy;
+                    J.e = h->cyx;
+                    J.lam = lamy;
+                    J.mu = mu;
+                    J.nx = h->nx;
+                    J.ny = h->ny;
+                    J.per_x = per;
+                    J.per_y = per;
+                    yl.push_back(J);
+                }
+            }
+            add_line(xl);
+            add_col(yl);
+        }
+    }
+    // device copy of the job lists
+    if (b->d_jobs && b->d_jobs_bytes < blob.size()) {
+        cudaFree(b->d_jobs);
+        b->d_jobs = nullptr;
+    }
+    if (!b->d_jobs) {
+        CU(cudaMalloc(&b->d_jobs, std::max<size_t>(blob.size(), 16)));
+        b->d_jobs_bytes = std::max<size_t>(blob.size(), 16);
+    }
+    CU(cudaMemcpy(b->d_jobs, blob.data(), blob.size(), cudaMemcpyHostToDevice));
+
+    // capture
+    if (!b->cap_stream) CU(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
+    b->prof.next = b->prof.pool.size();
+    b->g_pairs.clear();
+    CU(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+    int rc = ANISO_OK;
+    unsigned *err = b->hs[0]->err;
+    for (const Launch &L : launches) {
+        int pidx = -1;
+        if (b->profile) {
+            pidx = b->prof.take(L.kind == 0 ? ANISO_KERNEL_XSWEEP : ANISO_KERNEL_YSWEEP);
+            if (pidx < 0 || cudaEventRecord(b->prof.pool[pidx].a, b->cap_stream) != cudaSuccess) {
+                rc = fail(ANISO_ERR_CUDA, "profiling event failed");
+                break;
+            }
+        }
+        cudaError_t ce;
+        if (L.kind == 0) {
+            LineArgs a{};
+            a.jobs = reinterpret_cast<const LineJob *>(static_cast<unsigned char *>(b->d_jobs) + L.offset);
+            a.njobs = L.njobs;
+            a.limiter = b->hs[0]->limiter;
+            a.err = err;
+            ce = launch_line(prec, fp16, a, L.nblocks, L.nthreads, L.smem, b->cap_stream);
+        } else {
+            ColArgs a{};
+            a.jobs = reinterpret_cast<const ColJob *>(static_cast<unsigned char *>(b->d_jobs) + L.offset);
+            a.njobs = L.njobs;
+            a.limiter = b->hs[0]->limiter;
+            a.err = err;
+            ce = launch_col(prec, fp16, a, L.nblocks, L.nthreads, L.smem, b->cap_stream);
+        }
+        if (ce != cudaSuccess) {
+            rc = fail(ANISO_ERR_CUDA, "batched launch: %s", cudaGetErrorString(ce));
+            break;
+        }
+        if (b->profile) {
+            if (cudaEventRecord(b->prof.pool[pidx].b, b->cap_stream) != cudaSuccess) {
+                rc = fail(ANISO_ERR_CUDA, "profiling event failed");
+                break;
+            }
+            b->g_pairs.push_back(pidx);
+        }
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(b->cap_stream, &graph);
+    if (rc) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (ce != cudaSuccess) return fail(ANISO_ERR_CUDA, "batch capture: %s", cudaGetErrorString(ce));
+    ce = cudaGraphInstantiate(&b->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) return fail(ANISO_ERR_CUDA, "batch instantiate: %s", cudaGetErrorString(ce));
+    return ANISO_OK;
+}
+
+extern "C" int aniso_step_batched(aniso_batch_t b, void *const *T, const double *dt, const int *nsteps)
+{
+    if (!b) return fail(ANISO_ERR_ARG, "aniso_step_batched: null batch");
+    if (!T || !dt || !nsteps) return fail(ANISO_ERR_ARG, "aniso_step_batched: null array");
+    const int n = (int)b->hs.size();
+    for (int k = 0; k < n; ++k) {
+        if (!T[k]) return fail(ANISO_ERR_ARG, "aniso_step_batched: T[%d] is NULL", k);
+        if (!(dt[k] > 0)) return fail(ANISO_ERR_ARG, "aniso_step_batched: dt[%d] must be > 0", k);
+        if (nsteps[k] < 0) return fail(ANISO_ERR_ARG, "aniso_step_batched: nsteps[%d] < 0", k);
+    }
+    std::vector<int> parity(n);
+    for (int k = 0; k < n; ++k)
+        parity[k] = b->hs[k]->order == ANISO_ORDER_ALTERNATE ? (int)(b->hs[k]->step_counter & 1) : -b->hs[k]->order;
+    const bool hit = b->gexec && b->key_profile == b->profile &&
+                     b->key_T == std::vector<void *>(T, T + n) &&
+                     b->key_dt == std::vector<double>(dt, dt + n) &&
+                     b->key_n == std::vector<int>(nsteps, nsteps + n) && b->key_parity == parity;
+    if (!hit) {
+        CU(cudaStreamSynchronize(b->stream));
+        if (b->profile) {
+            int rc = b->prof.drain();
+            if (rc) return rc;
+        }
+        batch_drop(b);
+        int rc = batch_build(b, T, dt, nsteps);
+        if (rc) return rc;
+        b->key_T.assign(T, T + n);
+        b->key_dt.assign(dt, dt + n);
+        b->key_n.assign(nsteps, nsteps + n);
+        b->key_parity = parity;
+        b->key_profile = b->profile;
+    }
+    if (b->profile && !b->prof.pending.empty()) {
+        CU(cudaStreamSynchronize(b->stream));
+        int rc = b->prof.drain();
+        if (rc) return rc;
+    }
+    CU(cudaGraphLaunch(b->gexec, b->stream));
+    if (b->profile) b->prof.pending.insert(b->prof.pending.end(), b->g_pairs.begin(), b->g_pairs.end());
+    for (int k = 0; k < n; ++k) b->hs[k]->step_counter += nsteps[k];
+    return ANISO_OK;
+}
+
+extern "C" void aniso_batch_destroy(aniso_batch_t b)
+{
+    if (!b) return;
+    cudaStreamSynchronize(b->stream);
+    batch_drop(b);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    if (b->d_jobs) cudaFree(b->d_jobs);
+    b->prof.destroy();
+    delete b;
+}
+
+extern "C" int aniso_kernel_times(aniso_t h, aniso_batch_t b, int kind, double *ms, long long *launches,
+                                  int reset)
+{
+    if ((!h) == (!b)) return fail(ANISO_ERR_ARG, "aniso_kernel_times: pass exactly one of h, b");
+    if (kind < 0 || kind > 2) return fail(ANISO_ERR_ARG, "aniso_kernel_times: bad kind %d", kind);
+    Profiler &p = h ? h->prof : b->prof;
+    CU(cudaStreamSynchronize(h ? h->stream : b->stream));
+    int rc = p.drain();
+    if (rc) return rc;
+    if (ms) *ms = p.ms[kind];
+    if (launches) *launches = p.count[kind];
+    if (reset) {
+        for (int k = 0; k < 3; ++k) {
+            p.ms[k] = 0;
+            p.count[k] = 0;
+        }
+    }
+    return ANISO_OK;
+}

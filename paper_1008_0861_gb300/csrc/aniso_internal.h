@@ -1,0 +1,93 @@
+// aniso_internal.h -- job descriptors and launch entry points shared by the
+// library's translation units (not part of the public ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+namespace aniso {
+
+enum { LIM_VANLEER = 0, LIM_ARITH = 1, LIM_MINMOD = 2, LIM_MC = 3 };
+enum { PREC_FP64 = 0, PREC_FP32 = 1 };
+
+// Longest line a block can hold on chip, per precision (three buffers of the
+// line's length in shared memory).
+constexpr int MAX_LINE_FP32 = 16384;
+constexpr int MAX_LINE_FP64 = 8192;
+// Longest column the column kernel holds on chip (3 x (ny + P) x 64 bytes).
+constexpr int MAX_COL = 1024;
+constexpr size_t SMEM_LIMIT = 227 * 1024;
+
+// One contiguous-line update (Eq. xup on rows, or Eq. yup on a transposed
+// grid): `nlines` lines of `n` cells, line-major.  Lines are solved by teams
+// of `team` threads, `lines_per_block` teams per block.
+struct LineJob {
+    const void *Tin;
+    void *Tout;
+    const void *g;   // normal (implicit) face coefficient, face p+1/2 of each line at index p
+    const void *e;   // transverse face coefficient, same layout
+    double lam, mu;  // chi dt / h_line^2, chi dt / (dx dy)
+    int n, nlines;
+    int per_line, per_cross;  // periodic along the line / across lines
+    int team, lines_per_block;
+    int block0, nblocks;      // this job's block range in the launch
+};
+
+// One column update (Eq. yup) in the natural row-major layout: blocks own
+// strips of `Wb` columns and all ny rows; each column is cut into `P`
+// segments, one thread per (column, segment).
+struct ColJob {
+    const void *Tin;
+    void *Tout;
+    const void *g;   // cyy, face j+1/2 of column i at [j][i]
+    const void *e;   // cyx
+    double lam, mu;  // chi dt / dy^2, chi dt / (dx dy)
+    int nx, ny;
+    int per_x, per_y;
+    int P, Wb;
+    int block0, nblocks;
+};
+
+// Kernel arguments: either a device array of jobs (batched launches) or one
+// job passed by value (jobs == nullptr).
+struct LineArgs {
+    const LineJob *jobs;
+    int njobs;
+    int limiter;
+    unsigned *err;
+    LineJob one;
+};
+struct ColArgs {
+    const ColJob *jobs;
+    int njobs;
+    int limiter;
+    unsigned *err;
+    ColJob one;
+};
+
+// Launch configuration helpers (host).
+void line_config(int prec, int n, int *team, int *lines_per_block, int *nthreads);
+size_t line_smem_bytes(int prec, int n, int team, int lines_per_block);
+void col_config(int prec, int ny, int *P, int *Wb, int *nthreads);
+size_t col_smem_bytes(int prec, int ny, int P, int Wb);
+
+// Launch wrappers (defined per precision in kernels_f32.cu / kernels_f64.cu).
+// coef_fp16 selects half-precision coefficient storage (FP32 only).
+cudaError_t launch_line(int prec, int coef_fp16, const LineArgs &a, int nblocks, int nthreads,
+                        size_t smem, cudaStream_t s);
+cudaError_t launch_col(int prec, int coef_fp16, const ColArgs &a, int nblocks, int nthreads,
+                       size_t smem, cudaStream_t s);
+// Face coefficients from cell-centred b (FP64 arithmetic, one rounding to the
+// storage type).  bprec: element type of bx, by.  coef: 0 fp64, 1 fp32, 2 fp16.
+// cyyT/cyxT (optional) receive transposed copies [nx][ny].
+cudaError_t launch_face_coeffs(int bprec, int coef, const void *bx, const void *by, int nx, int ny,
+                               int bc, double kappa, void *cxx, void *cxy, void *cyy, void *cyx,
+                               void *cyyT, void *cyxT, cudaStream_t s);
+// out[c][r] = in[r][c] for an rows x cols array of 4- or 8-byte elements.
+cudaError_t launch_transpose(int elem_bytes, const void *in, void *out, int rows, int cols,
+                             cudaStream_t s);
+// FP64 sum / min / max / non-finite count; partial buffers of TOTALS_BLOCKS.
+constexpr int TOTALS_BLOCKS = 608;
+cudaError_t launch_totals(int prec, const void *T, size_t n, double *partials, double *result,
+                          cudaStream_t s);
+
+}  // namespace aniso

@@ -1,0 +1,141 @@
+// Launch configuration, face coefficients, transposes and FP64 totals.
+#include "sweep_kernels.cuh"
+
+namespace aniso {
+
+cudaError_t launch_line_f32(int coef_fp16, const LineArgs &a, int nblocks, int nthreads, size_t smem,
+                            cudaStream_t s);
+cudaError_t launch_col_f32(int coef_fp16, const ColArgs &a, int nblocks, int nthreads, size_t smem,
+                           cudaStream_t s);
+cudaError_t launch_line_f64(const LineArgs &a, int nblocks, int nthreads, size_t smem, cudaStream_t s);
+cudaError_t launch_col_f64(const ColArgs &a, int nblocks, int nthreads, size_t smem, cudaStream_t s);
+
+static int pow2floor(int v)
+{
+    int p = 1;
+    while (p * 2 <= v) p *= 2;
+    return p;
+}
+static int pow2ceil(int v)
+{
+    int p = 1;
+    while (p < v) p *= 2;
+    return p;
+}
+static size_t esize(int prec) { return prec == PREC_FP64 ? 8 : 4; }
+
+// Target: about 32 cells per thread, one warp per line up to 1024 cells,
+// at most 512 threads per line; ~110 KB of shared memory per block so that
+// two blocks fit on an SM when the line allows it.
+void line_config(int prec, int n, int *team, int *lines_per_block, int *nthreads)
+{
+    int P;
+    if (n < 32) P = pow2floor(n);
+    else {
+        P = pow2ceil((n + 31) / 32);
+        if (P < 32) P = 32;
+        if (P > 512) P = 512;
+    }
+    int lpb = P >= 256 ? 1 : 256 / P;
+    const size_t per_line = line_smem_bytes(prec, n, P, 1);
+    while (lpb > 1 && per_line * lpb > 110 * 1024) lpb /= 2;
+    *team = P;
+    *lines_per_block = lpb;
+    *nthreads = P * lpb;
+}
+
+size_t line_smem_bytes(int prec, int n, int team, int lines_per_block)
+{
+    const size_t np = (size_t)n + (n >> 5) + 1;
+    return (size_t)lines_per_block * (3 * np + 8 * (size_t)team) * esize(prec);
+}
+
+void col_config(int prec, int ny, int *P_out, int *Wb_out, int *nthreads)
+{
+    const int wmin = prec == PREC_FP64 ? 8 : 16;  // 64-byte row segments at least
+    int NT = prec == PREC_FP64 ? 256 : 512;
+    int P = 1, Wb = NT;
+    for (;;) {
+        P = pow2floor(ny / 16 > 0 ? ny / 16 : 1);
+        if (P > NT / wmin) P = NT / wmin;
+        if (P > ny) P = pow2floor(ny);
+        Wb = NT / P;
+        if (col_smem_bytes(prec, ny, P, Wb) <= 113 * 1024 || Wb <= wmin || NT <= 128) break;
+        NT /= 2;
+    }
+    *P_out = P;
+    *Wb_out = Wb;
+    *nthreads = NT;
+}
+
+size_t col_smem_bytes(int prec, int ny, int P, int Wb)
+{
+    return (3 * ((size_t)ny + P) * Wb + 8 * (size_t)P * Wb) * esize(prec);
+}
+
+cudaError_t launch_line(int prec, int coef_fp16, const LineArgs &a, int nblocks, int nthreads,
+                        size_t smem, cudaStream_t s)
+{
+    if (prec == PREC_FP64) return launch_line_f64(a, nblocks, nthreads, smem, s);
+    return launch_line_f32(coef_fp16, a, nblocks, nthreads, smem, s);
+}
+
+cudaError_t launch_col(int prec, int coef_fp16, const ColArgs &a, int nblocks, int nthreads,
+                       size_t smem, cudaStream_t s)
+{
+    if (prec == PREC_FP64) return launch_col_f64(a, nblocks, nthreads, smem, s);
+    return launch_col_f32(coef_fp16, a, nblocks, nthreads, smem, s);
+}
+
+template <typename B, typename C>
+static void face_launch(const void *bx, const void *by, int nx, int ny, int bc, double kappa, void *cxx,
+                        void *cxy, void *cyy, void *cyx, void *cyyT, void *cyxT, cudaStream_t s)
+{
+    dim3 block(256), grid((nx + 255) / 256, ny);
+    face_coeffs_kernel<B, C><<<grid, block, 0, s>>>(
+        static_cast<const B *>(bx), static_cast<const B *>(by), nx, ny, bc, kappa, static_cast<C *>(cxx),
+        static_cast<C *>(cxy), static_cast<C *>(cyy), static_cast<C *>(cyx), static_cast<C *>(cyyT),
+        static_cast<C *>(cyxT));
+}
+
+cudaError_t launch_face_coeffs(int bprec, int coef, const void *bx, const void *by, int nx, int ny,
+                               int bc, double kappa, void *cxx, void *cxy, void *cyy, void *cyx,
+                               void *cyyT, void *cyxT, cudaStream_t s)
+{
+    if (bprec == PREC_FP64) {
+        if (coef == 0) face_launch<double, double>(bx, by, nx, ny, bc, kappa, cxx, cxy, cyy, cyx, cyyT, cyxT, s);
+        else if (coef == 1) face_launch<double, float>(bx, by, nx, ny, bc, kappa, cxx, cxy, cyy, cyx, cyyT, cyxT, s);
+        else face_launch<double, __half>(bx, by, nx, ny, bc, kappa, cxx, cxy, cyy, cyx, cyyT, cyxT, s);
+    } else {
+        if (coef == 0) face_launch<float, double>(bx, by, nx, ny, bc, kappa, cxx, cxy, cyy, cyx, cyyT, cyxT, s);
+        else if (coef == 1) face_launch<float, float>(bx, by, nx, ny, bc, kappa, cxx, cxy, cyy, cyx, cyyT, cyxT, s);
+        else face_launch<float, __half>(bx, by, nx, ny, bc, kappa, cxx, cxy, cyy, cyx, cyyT, cyxT, s);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_transpose(int elem_bytes, const void *in, void *out, int rows, int cols,
+                             cudaStream_t s)
+{
+    dim3 block(32, 8), grid((cols + 31) / 32, (rows + 31) / 32);
+    if (elem_bytes == 8)
+        transpose_kernel<double><<<grid, block, 0, s>>>(static_cast<const double *>(in),
+                                                        static_cast<double *>(out), rows, cols);
+    else
+        transpose_kernel<float><<<grid, block, 0, s>>>(static_cast<const float *>(in),
+                                                       static_cast<float *>(out), rows, cols);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_totals(int prec, const void *T, size_t n, double *partials, double *result,
+                          cudaStream_t s)
+{
+    if (prec == PREC_FP64)
+        totals_partial_kernel<double><<<TOTALS_BLOCKS, 256, 0, s>>>(static_cast<const double *>(T), n, partials);
+    else
+        totals_partial_kernel<float><<<TOTALS_BLOCKS, 256, 0, s>>>(static_cast<const float *>(T), n, partials);
+    totals_final_kernel<<<1, 32, 0, s>>>(partials, TOTALS_BLOCKS, result);
+    return cudaGetLastError();
+}
+
+}  // namespace aniso

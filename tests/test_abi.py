@@ -1,0 +1,68 @@
+"""The C-ABI library loads and exports every entry point include/aniso.h
+declares; argument validation that needs no GPU behaves as documented."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "aniso.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(aniso_[a-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def built():
+    from paper_1008_0861_gb300 import build
+    return build.build()
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for must in ("aniso_create", "aniso_set_field", "aniso_step", "aniso_step_batched"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(built):
+    lib = ctypes.CDLL(built)
+    for name in _declared():
+        assert hasattr(lib, name), name
+    import paper_1008_0861_gb300 as P
+    assert set(_declared()) == set(P.EXPORTED)
+
+
+def test_create_validates_arguments(built):
+    import paper_1008_0861_gb300 as P
+    bad = [dict(nx=2, ny=8), dict(nx=8, ny=2), dict(dx=0.0), dict(dy=-1.0), dict(chi_par=0.0),
+           dict(chi_perp=-0.1), dict(chi_perp=2.0), dict(bc=7)]
+    for kw in bad:
+        args = dict(nx=8, ny=8, dx=1.0, dy=1.0, chi_par=1.0, chi_perp=0.0, bc=1)
+        args.update(kw)
+        with pytest.raises(P.AnisoError) as ei:
+            P.aniso_create(**args)
+        assert ei.value.code == P.ANISO_ERR_ARG, kw
+    h = P.aniso_create(8, 8, 1.0, 1.0, 1.0)
+    try:
+        with pytest.raises(P.AnisoError) as ei:
+            P.aniso_step(h, 0x1000, 1.0, 1)
+        assert ei.value.code == P.ANISO_ERR_STATE
+        with pytest.raises(P.AnisoError) as ei:
+            P.aniso_set_option(h, P.ANISO_OPT_ORDER, 9)
+        assert ei.value.code == P.ANISO_ERR_ARG
+        with pytest.raises(P.AnisoError) as ei:
+            P.aniso_set_option(h, 99, 0)
+        assert ei.value.code == P.ANISO_ERR_ARG
+        P.aniso_set_option(h, P.ANISO_OPT_ORDER, P.ANISO_ORDER_ALTERNATE)
+        P.aniso_set_state(h, 5)
+        assert P.aniso_get_state(h) == 5
+    finally:
+        P.aniso_destroy(h)
+
+
+def test_library_does_not_reference_the_oracle(built):
+    data = open(built, "rb").read()
+    assert b"or_xsweep" not in data and b"liboracle" not in data
