@@ -70,7 +70,9 @@ enum {
     ANISO_OPT_ORDER = 4,      /* ANISO_ORDER_* */
     ANISO_OPT_STREAM = 5,     /* cudaStream_t cast to integer; 0 = legacy default stream */
     ANISO_OPT_GRAPH = 6,      /* 1 (default): replay aniso_step loops from a captured CUDA graph */
-    ANISO_OPT_PROFILE = 7     /* 1: time every sweep launch with CUDA events (aniso_kernel_times) */
+    ANISO_OPT_PROFILE = 7,    /* 1: time every sweep launch with CUDA events (aniso_kernel_times) */
+    ANISO_OPT_FAST_PATH = 8   /* 1 (default): vectorised line kernel with transposed intermediate
+                                 for the x-then-y order; 0: the general kernels only */
 };
 enum { ANISO_PREC_FP64 = 0, ANISO_PREC_FP32 = 1 };
 enum {

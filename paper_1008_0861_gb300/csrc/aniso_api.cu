@@ -95,7 +95,7 @@ struct aniso_ctx {
     int nx = 0, ny = 0, bc = 0;
     double dx = 0, dy = 0, chi_par = 0, chi_perp = 0;
     int prec = PREC_FP64, field_fp16 = 0, kahan = 0, limiter = LIM_VANLEER, order = ANISO_ORDER_XY;
-    int use_graph = 1, profile = 0;
+    int use_graph = 1, profile = 0, fast = 1;
     cudaStream_t stream = 0;
     long long step_counter = 0;
     bool field_set = false;
@@ -120,6 +120,15 @@ struct aniso_ctx {
     size_t csz() const { return prec == PREC_FP64 ? 8 : (field_fp16 ? 2 : 4); }
     int coef_kind() const { return prec == PREC_FP64 ? 0 : (field_fp16 ? 2 : 1); }
     bool long_cols() const { return ny > MAX_COL; }
+    int vec() const { return prec == PREC_FP64 ? 2 : 4; }
+    // Grid shapes the vectorised x-then-y path handles: both line lengths a
+    // multiple of the 16-byte vector and short enough for transposed output.
+    bool fast_shape() const
+    {
+        int a, b, c;
+        size_t d;
+        return line2_config(prec, nx, true, &a, &b, &c, &d) && line2_config(prec, ny, true, &a, &b, &c, &d);
+    }
     int max_line() const { return prec == PREC_FP64 ? MAX_LINE_FP64 : MAX_LINE_FP32; }
 };
 
@@ -205,6 +214,10 @@ extern "C" int aniso_set_option(aniso_t h, int key, long long v)
     case ANISO_OPT_PROFILE:
         h->profile = v != 0;
         break;
+    case ANISO_OPT_FAST_PATH:
+        h->fast = v != 0;
+        drop_graph(h);
+        break;
     default:
         return fail(ANISO_ERR_ARG, "unknown option key %d", key);
     }
@@ -227,9 +240,11 @@ extern "C" int aniso_set_field(aniso_t h, const void *bx, const void *by)
         CU(cudaMalloc(&h->cyy, n * h->csz()));
         CU(cudaMalloc(&h->cyx, n * h->csz()));
         CU(cudaMalloc(&h->tstar, n * h->esz()));
-        if (h->long_cols()) {
+        if (h->long_cols() || h->fast_shape()) {
             CU(cudaMalloc(&h->cyyT, n * h->csz()));
             CU(cudaMalloc(&h->cyxT, n * h->csz()));
+        }
+        if (h->long_cols()) {
             CU(cudaMalloc(&h->tA, n * h->esz()));
             CU(cudaMalloc(&h->tB, n * h->esz()));
         }
@@ -246,6 +261,74 @@ extern "C" int aniso_set_field(aniso_t h, const void *bx, const void *by)
     return ANISO_OK;
 }
 
+static bool aligned16(const void *p) { return ((uintptr_t)p & 15) == 0; }
+
+// One vectorised line update (line2_kernel) of `nlines` lines of n cells.
+static int enqueue_line2(aniso_ctx *h, const void *in, void *out, const void *g, const void *e, int n,
+                         int nlines, int per_line, int per_cross, double lam, double mu, bool transposed,
+                         int kind, cudaStream_t s, std::vector<int> *pairs)
+{
+    Line2Args a{};
+    a.jobs = nullptr;
+    a.njobs = 1;
+    a.limiter = h->limiter;
+    a.err = h->err;
+    Line2Job &J = a.one;
+    J.Tin = in;
+    J.Tout = out;
+    J.g = g;
+    J.e = e;
+    J.lam = lam;
+    J.mu = mu;
+    J.n = n;
+    J.nlines = nlines;
+    J.per_line = per_line;
+    J.per_cross = per_cross;
+    J.transpose_out = transposed ? 1 : 0;
+    int nthreads;
+    size_t smem;
+    if (!line2_config(h->prec, n, transposed, &J.team, &J.lines_per_block, &nthreads, &smem))
+        return fail(ANISO_ERR_UNSUPPORTED, "vectorised line kernel cannot take n=%d", n);
+    J.block0 = 0;
+    J.nblocks = (nlines + J.lines_per_block - 1) / J.lines_per_block;
+    int pidx = -1;
+    const unsigned rec_flags = pairs ? cudaEventRecordExternal : cudaEventRecordDefault;
+    if (h->profile) {
+        pidx = h->prof.take(kind);
+        if (pidx < 0) return fail(ANISO_ERR_CUDA, "event creation failed");
+        CU(cudaEventRecordWithFlags(h->prof.pool[pidx].a, s, rec_flags));
+    }
+    CU(launch_line2(h->prec, h->field_fp16, a, J.nblocks, nthreads, smem, s));
+    if (h->profile) {
+        CU(cudaEventRecordWithFlags(h->prof.pool[pidx].b, s, rec_flags));
+        if (pairs) pairs->push_back(pidx);
+        else h->prof.pending.push_back(pidx);
+    }
+    return ANISO_OK;
+}
+
+// Fast path of one x-then-y step: the x-update reads T row-major and writes T*
+// column-major; the y-update reads T*'s columns as contiguous lines (with the
+// transposed y coefficients) and writes T back row-major.
+static bool use_fast(const aniso_ctx *h, const void *T)
+{
+    return h->fast && h->order == ANISO_ORDER_XY && h->cyyT && aligned16(T) && aligned16(h->tstar) &&
+           h->fast_shape();
+}
+
+static int enqueue_fast_step(aniso_ctx *h, void *T, double dt, cudaStream_t s, std::vector<int> *pairs)
+{
+    const double lamx = h->chi_par * dt / (h->dx * h->dx);
+    const double lamy = h->chi_par * dt / (h->dy * h->dy);
+    const double mu = h->chi_par * dt / (h->dx * h->dy);
+    const int per = h->bc == ANISO_BC_PERIODIC;
+    int rc = enqueue_line2(h, T, h->tstar, h->cxx, h->cxy, h->nx, h->ny, per, per, lamx, mu, true,
+                           ANISO_KERNEL_XSWEEP, s, pairs);
+    if (rc) return rc;
+    return enqueue_line2(h, h->tstar, T, h->cyyT, h->cyxT, h->ny, h->nx, per, per, lamy, mu, true,
+                         ANISO_KERNEL_YSWEEP, s, pairs);
+}
+
 // One directional update from `in` to `out` (distinct buffers) on stream s.
 static int enqueue_sweep(aniso_ctx *h, int dir, const void *in, void *out, double dt, cudaStream_t s,
                          std::vector<int> *pairs)
@@ -255,16 +338,19 @@ static int enqueue_sweep(aniso_ctx *h, int dir, const void *in, void *out, doubl
     const double mu = h->chi_par * dt / (h->dx * h->dy);
     const int per = h->bc == ANISO_BC_PERIODIC;
     int pidx = -1;
+    // inside a stream capture only an "external" record becomes an event
+    // node that is recorded on every replay
+    const unsigned rec_flags = pairs ? cudaEventRecordExternal : cudaEventRecordDefault;
     auto begin = [&](int kind) -> int {
         if (!h->profile) return ANISO_OK;
         pidx = h->prof.take(kind);
         if (pidx < 0) return fail(ANISO_ERR_CUDA, "event creation failed");
-        CU(cudaEventRecord(h->prof.pool[pidx].a, s));
+        CU(cudaEventRecordWithFlags(h->prof.pool[pidx].a, s, rec_flags));
         return ANISO_OK;
     };
     auto end = [&]() -> int {
         if (!h->profile) return ANISO_OK;
-        CU(cudaEventRecord(h->prof.pool[pidx].b, s));
+        CU(cudaEventRecordWithFlags(h->prof.pool[pidx].b, s, rec_flags));
         if (pairs) pairs->push_back(pidx);
         else h->prof.pending.push_back(pidx);
         return ANISO_OK;
@@ -298,8 +384,14 @@ static int enqueue_sweep(aniso_ctx *h, int dir, const void *in, void *out, doubl
         return end();
     };
     int rc;
-    if (dir == ANISO_DIR_X)
+    if (dir == ANISO_DIR_X) {
+        int t1, t2, t3;
+        size_t t4;
+        if (h->fast && aligned16(in) && aligned16(out) && line2_config(h->prec, h->nx, false, &t1, &t2, &t3, &t4))
+            return enqueue_line2(h, in, out, h->cxx, h->cxy, h->nx, h->ny, per, per, lamx, mu, false,
+                                 ANISO_KERNEL_XSWEEP, s, pairs);
         return line(in, out, h->cxx, h->cxy, h->nx, h->ny, per, per, lamx, ANISO_KERNEL_XSWEEP);
+    }
     if (!h->long_cols()) {
         ColArgs a{};
         a.jobs = nullptr;
@@ -347,6 +439,13 @@ static bool x_first(int order, long long counter)
 static int enqueue_steps(aniso_ctx *h, void *T, double dt, int nsteps, long long counter0,
                          cudaStream_t s, std::vector<int> *pairs)
 {
+    if (use_fast(h, T)) {
+        for (int k = 0; k < nsteps; ++k) {
+            int rc = enqueue_fast_step(h, T, dt, s, pairs);
+            if (rc) return rc;
+        }
+        return ANISO_OK;
+    }
     for (int k = 0; k < nsteps; ++k) {
         const bool xf = x_first(h->order, counter0 + k);
         int rc = enqueue_sweep(h, xf ? ANISO_DIR_X : ANISO_DIR_Y, T, h->tstar, dt, s, pairs);
@@ -561,7 +660,7 @@ static int batch_build(aniso_batch *b, void *const *T, const double *dt, const i
     // Every (global step, phase) launch is one list of line jobs (x) and one
     // of column jobs (y).  Identical lists are shared.
     struct Launch {
-        int kind;  // 0 line, 1 col
+        int kind;  // 0 line, 1 col, 2 vectorised line (line2)
         size_t offset;
         int njobs, nblocks, nthreads;
         size_t smem;
@@ -616,13 +715,68 @@ static int batch_build(aniso_batch *b, void *const *T, const double *dt, const i
         launches.push_back(L);
     };
 
+    auto add_line2 = [&](std::vector<Line2Job> &jobs, int kind_xy) {
+        if (jobs.empty()) return;
+        std::stable_sort(jobs.begin(), jobs.end(),
+                         [](const Line2Job &a, const Line2Job &c) { return (long long)a.n * a.nlines > (long long)c.n * c.nlines; });
+        int nthreads = 0;
+        for (auto &J : jobs) nthreads = std::max(nthreads, J.team * J.lines_per_block);
+        int blocks = 0;
+        size_t smem = 0;
+        for (auto &J : jobs) {
+            J.lines_per_block = nthreads / J.team;
+            J.block0 = blocks;
+            J.nblocks = (J.nlines + J.lines_per_block - 1) / J.lines_per_block;
+            blocks += J.nblocks;
+            smem = std::max(smem, line2_smem_bytes(prec, J.n, J.team, J.lines_per_block));
+        }
+        Launch L{kind_xy == 0 ? 2 : 3, blob.size(), (int)jobs.size(), blocks, nthreads, smem};
+        const unsigned char *p = reinterpret_cast<const unsigned char *>(jobs.data());
+        blob.insert(blob.end(), p, p + jobs.size() * sizeof(Line2Job));
+        while (blob.size() % 16) blob.push_back(0);
+        launches.push_back(L);
+    };
+
     for (int s = 0; s < max_steps; ++s) {
         for (int phase = 0; phase < 2; ++phase) {
             std::vector<LineJob> xl;
             std::vector<ColJob> yl;
+            std::vector<Line2Job> fl;
             for (int k = 0; k < n; ++k) {
                 if (s >= nsteps[k]) continue;
                 aniso_ctx *h = b->hs[k];
+                if (use_fast(h, T[k])) {
+                    // x: T (rows) -> T* (column-major); y: T* (columns) -> T (rows)
+                    const int per = h->bc == ANISO_BC_PERIODIC;
+                    const double mu = h->chi_par * dt[k] / (h->dx * h->dy);
+                    Line2Job J{};
+                    int nt;
+                    size_t sm;
+                    if (phase == 0) {
+                        J.Tin = T[k];
+                        J.Tout = h->tstar;
+                        J.g = h->cxx;
+                        J.e = h->cxy;
+                        J.lam = h->chi_par * dt[k] / (h->dx * h->dx);
+                        J.n = h->nx;
+                        J.nlines = h->ny;
+                    } else {
+                        J.Tin = h->tstar;
+                        J.Tout = T[k];
+                        J.g = h->cyyT;
+                        J.e = h->cyxT;
+                        J.lam = h->chi_par * dt[k] / (h->dy * h->dy);
+                        J.n = h->ny;
+                        J.nlines = h->nx;
+                    }
+                    J.mu = mu;
+                    J.per_line = per;
+                    J.per_cross = per;
+                    J.transpose_out = 1;
+                    line2_config(prec, J.n, true, &J.team, &J.lines_per_block, &nt, &sm);
+                    fl.push_back(J);
+                    continue;
+                }
                 const bool xf = x_first(h->order, h->step_counter + s);
                 const bool is_x = (phase == 0) == xf;
                 const void *in = phase == 0 ? T[k] : h->tstar;
@@ -661,6 +815,7 @@ static int batch_build(aniso_batch *b, void *const *T, const double *dt, const i
                     yl.push_back(J);
                 }
             }
+            add_line2(fl, phase);
             add_line(xl);
             add_col(yl);
         }
@@ -686,14 +841,22 @@ static int batch_build(aniso_batch *b, void *const *T, const double *dt, const i
     for (const Launch &L : launches) {
         int pidx = -1;
         if (b->profile) {
-            pidx = b->prof.take(L.kind == 0 ? ANISO_KERNEL_XSWEEP : ANISO_KERNEL_YSWEEP);
-            if (pidx < 0 || cudaEventRecord(b->prof.pool[pidx].a, b->cap_stream) != cudaSuccess) {
+            pidx = b->prof.take((L.kind == 0 || L.kind == 2) ? ANISO_KERNEL_XSWEEP : ANISO_KERNEL_YSWEEP);
+            if (pidx < 0 || cudaEventRecordWithFlags(b->prof.pool[pidx].a, b->cap_stream,
+                                                     cudaEventRecordExternal) != cudaSuccess) {
                 rc = fail(ANISO_ERR_CUDA, "profiling event failed");
                 break;
             }
         }
         cudaError_t ce;
-        if (L.kind == 0) {
+        if (L.kind >= 2) {
+            Line2Args a{};
+            a.jobs = reinterpret_cast<const Line2Job *>(static_cast<unsigned char *>(b->d_jobs) + L.offset);
+            a.njobs = L.njobs;
+            a.limiter = b->hs[0]->limiter;
+            a.err = err;
+            ce = launch_line2(prec, fp16, a, L.nblocks, L.nthreads, L.smem, b->cap_stream);
+        } else if (L.kind == 0) {
             LineArgs a{};
             a.jobs = reinterpret_cast<const LineJob *>(static_cast<unsigned char *>(b->d_jobs) + L.offset);
             a.njobs = L.njobs;
@@ -713,7 +876,8 @@ static int batch_build(aniso_batch *b, void *const *T, const double *dt, const i
             break;
         }
         if (b->profile) {
-            if (cudaEventRecord(b->prof.pool[pidx].b, b->cap_stream) != cudaSuccess) {
+            if (cudaEventRecordWithFlags(b->prof.pool[pidx].b, b->cap_stream, cudaEventRecordExternal) !=
+                cudaSuccess) {
                 rc = fail(ANISO_ERR_CUDA, "profiling event failed");
                 break;
             }

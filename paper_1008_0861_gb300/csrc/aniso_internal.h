@@ -64,7 +64,35 @@ struct ColArgs {
     ColJob one;
 };
 
+// Vectorised contiguous-line update (line2_kernel): lines of n cells with n a
+// multiple of the 16-byte vector (4 FP32 / 2 FP64 cells); output line-major
+// or transposed (position-major, nlines wide).
+struct Line2Job {
+    const void *Tin;
+    void *Tout;
+    const void *g;
+    const void *e;
+    double lam, mu;
+    int n, nlines;
+    int per_line, per_cross;
+    int team, lines_per_block;
+    int transpose_out;
+    int block0, nblocks;
+};
+struct Line2Args {
+    const Line2Job *jobs;
+    int njobs;
+    int limiter;
+    unsigned *err;
+    Line2Job one;
+};
+constexpr int MAX_LINE2_TRANSPOSED = 2048;
+
 // Launch configuration helpers (host).
+// line2: returns false when the line cannot use the vectorised kernel.
+bool line2_config(int prec, int n, bool transposed, int *team, int *lines_per_block, int *nthreads,
+                  size_t *smem);
+size_t line2_smem_bytes(int prec, int n, int team, int lines_per_block);
 void line_config(int prec, int n, int *team, int *lines_per_block, int *nthreads);
 size_t line_smem_bytes(int prec, int n, int team, int lines_per_block);
 void col_config(int prec, int ny, int *P, int *Wb, int *nthreads);
@@ -76,6 +104,8 @@ cudaError_t launch_line(int prec, int coef_fp16, const LineArgs &a, int nblocks,
                         size_t smem, cudaStream_t s);
 cudaError_t launch_col(int prec, int coef_fp16, const ColArgs &a, int nblocks, int nthreads,
                        size_t smem, cudaStream_t s);
+cudaError_t launch_line2(int prec, int coef_fp16, const Line2Args &a, int nblocks, int nthreads,
+                         size_t smem, cudaStream_t s);
 // Face coefficients from cell-centred b (FP64 arithmetic, one rounding to the
 // storage type).  bprec: element type of bx, by.  coef: 0 fp64, 1 fp32, 2 fp16.
 // cyyT/cyxT (optional) receive transposed copies [nx][ny].

@@ -1,5 +1,5 @@
 // FP32 instantiations of the sweep kernels (FP32 or FP16 face coefficients).
-#include "sweep_kernels.cuh"
+#include "line2_kernel.cuh"
 
 namespace aniso {
 
@@ -40,6 +40,21 @@ cudaError_t launch_col_f32(int coef_fp16, const ColArgs &a, int nblocks, int nth
     } else {
         if ((err = prep(col_sweep_kernel<float, float>, smem)) != cudaSuccess) return err;
         col_sweep_kernel<float, float><<<nblocks, nthreads, smem, s>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+
+cudaError_t launch_line2_f32(int coef_fp16, const Line2Args &a, int nblocks, int nthreads, size_t smem,
+                             cudaStream_t s)
+{
+    cudaError_t err;
+    if (coef_fp16) {
+        if ((err = prep(line2_kernel<float, __half>, smem)) != cudaSuccess) return err;
+        line2_kernel<float, __half><<<nblocks, nthreads, smem, s>>>(a);
+    } else {
+        if ((err = prep(line2_kernel<float, float>, smem)) != cudaSuccess) return err;
+        line2_kernel<float, float><<<nblocks, nthreads, smem, s>>>(a);
     }
     return cudaGetLastError();
 }

@@ -1,5 +1,5 @@
 // FP64 instantiations of the sweep kernels.
-#include "sweep_kernels.cuh"
+#include "line2_kernel.cuh"
 
 namespace aniso {
 
@@ -29,6 +29,15 @@ cudaError_t launch_col_f64(const ColArgs &a, int nblocks, int nthreads, size_t s
     cudaError_t err = prep(col_sweep_kernel<double, double>, smem);
     if (err != cudaSuccess) return err;
     col_sweep_kernel<double, double><<<nblocks, nthreads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+
+cudaError_t launch_line2_f64(const Line2Args &a, int nblocks, int nthreads, size_t smem, cudaStream_t s)
+{
+    cudaError_t err = prep(line2_kernel<double, double>, smem);
+    if (err != cudaSuccess) return err;
+    line2_kernel<double, double><<<nblocks, nthreads, smem, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -215,13 +215,47 @@ __global__ void __launch_bounds__(512) line_sweep_kernel(LineArgs args)
     R *small = reinterpret_cast<R *>(smem_raw) + (size_t)J.lines_per_block * 3 * np +
                (size_t)tm * 8 * P;
 
-    // ---- A: fluxes through every face p+1/2 of the line
-    for (int p = t; p < n; p += P) {
-        int p1 = p + 1;
-        if (p1 == n) p1 = J.per_line ? 0 : n - 1;
-        R gv = ldcoef(G + p), ev = ldcoef(E + p);
-        sF[phys(p)] = face_flux<R>(lim, lam, mu, gv, ev, rd[p], rc[p], ru[p], rd[p1], rc[p1], ru[p1]);
-        sG[phys(p)] = gv;
+    // ---- A: fluxes through every face p+1/2 of the line.  Batches of UA
+    // cells per thread issue all their loads before any arithmetic so that
+    // many loads are in flight; the value at p+1 comes from the neighbouring
+    // lane (the last lane of each width-wide group loads it).
+    {
+        constexpr int UA = 4;
+        const int width = P < 32 ? P : 32;
+        const int lane_in = t & (width - 1);
+        const unsigned full = 0xffffffffu;
+        for (int p0 = t; p0 - t < n; p0 += UA * P) {
+            R vd[UA], vc[UA], vu[UA], vg[UA], ve[UA];
+#pragma unroll
+            for (int u = 0; u < UA; ++u) {
+                const int p = p0 + u * P;
+                const int pc = p < n ? p : n - 1;
+                vd[u] = rd[pc];
+                vc[u] = rc[pc];
+                vu[u] = ru[pc];
+                vg[u] = ldcoef(G + pc);
+                ve[u] = ldcoef(E + pc);
+            }
+#pragma unroll
+            for (int u = 0; u < UA; ++u) {
+                const int p = p0 + u * P;
+                R vd1 = __shfl_down_sync(full, vd[u], 1, width);
+                R vc1 = __shfl_down_sync(full, vc[u], 1, width);
+                R vu1 = __shfl_down_sync(full, vu[u], 1, width);
+                if (p < n) {
+                    int p1 = p + 1;
+                    if (lane_in == width - 1 || p1 >= n) {
+                        if (p1 == n) p1 = J.per_line ? 0 : n - 1;
+                        vd1 = rd[p1];
+                        vc1 = rc[p1];
+                        vu1 = ru[p1];
+                    }
+                    sF[phys(p)] = face_flux<R>(lim, lam, mu, vg[u], ve[u], vd[u], vc[u], vu[u], vd1,
+                                               vc1, vu1);
+                    sG[phys(p)] = vg[u];
+                }
+            }
+        }
     }
     __syncthreads();
 
@@ -233,11 +267,14 @@ __global__ void __launch_bounds__(512) line_sweep_kernel(LineArgs args)
     const R ae = -lam * gem, ce = -lam * ge, be = R(1) - ae - ce;
     R rho1 = R(0), alp1 = R(0), gam1 = R(-1);  // map of the virtual row e: delta_e = delta_e
     R qp = R(0), qq = R(1), qw = R(0);          // composite map, starts as the identity
+    R gk = gem, Fk = sF[phys(em1)];  // values at k = e-1, carried down the loop
     for (int k = e - 1; k >= s; --k) {
         const int km = k - 1 < 0 ? k - 1 + n : k - 1;
-        const R gk = sG[phys(k)], gkm = sG[phys(km)];
-        const R rk = sF[phys(k)] - sF[phys(km)];
+        const R gkm = sG[phys(km)], Fkm = sF[phys(km)];
+        const R rk = Fk - Fkm;
         const R a = -lam * gkm, c = -lam * gk, b = R(1) - a - c;
+        gk = gkm;
+        Fk = Fkm;
         const R inv = Num<R>::div(R(1), b - c * alp1);
         const R alp = a * inv, gam = -c * gam1 * inv, rho = (rk - c * rho1) * inv;
         sF[phys(k)] = rho;
@@ -290,13 +327,26 @@ __global__ void __launch_bounds__(512) line_sweep_kernel(LineArgs args)
     }
     __syncthreads();
 
-    // ---- C: T_new = T_old + delta
+    // ---- C: T_new = T_old + delta (batched loads of T_old, as in phase A)
     if (active) {
+        constexpr int UC = 8;
         R *out = static_cast<R *>(J.Tout) + (size_t)lc * n;
-        for (int p = t; p < n; p += P) {
-            const R v = rc[p] + sF[phys(p)];
-            out[p] = v;
-            flag_nonfinite(args.err, v);
+        for (int p0 = t; p0 < n; p0 += UC * P) {
+            R vo[UC];
+#pragma unroll
+            for (int u = 0; u < UC; ++u) {
+                const int p = p0 + u * P;
+                vo[u] = p < n ? rc[p] : R(0);
+            }
+#pragma unroll
+            for (int u = 0; u < UC; ++u) {
+                const int p = p0 + u * P;
+                if (p < n) {
+                    const R v = vo[u] + sF[phys(p)];
+                    out[p] = v;
+                    flag_nonfinite(args.err, v);
+                }
+            }
         }
     }
 }
@@ -382,31 +432,47 @@ __global__ void __launch_bounds__(512) col_sweep_kernel(ColArgs args)
     }
     R rho1 = R(0), alp1 = R(0), gam1 = R(-1);
     R qp = R(0), qq = R(1), qw = R(0);
-    for (int k = e - 1; k >= s; --k) {
-        const int km = k - 1, kf = km < 0 ? km + ny : km;
-        const R *row = Tin + (size_t)rowmap(km) * nx;
-        R lm = row[il], mm = row[ic], rm = row[ir];
-        R gkm = ldcoef(Gc + (size_t)kf * nx + ic);
-        R Fkm = face_flux<R>(lim, lam, mu, gkm, ldcoef(Ec + (size_t)kf * nx + ic), lm, mm, rm, l0,
-                             m0, r0);
-        const R rk = Fk - Fkm;
-        const R a = -lam * gkm, cc = -lam * gk, b = R(1) - a - cc;
-        const R inv = Num<R>::div(R(1), b - cc * alp1);
-        const R alp = a * inv, gam = -cc * gam1 * inv, rho = (rk - cc * rho1) * inv;
-        sRho[ph(k)] = rho;
-        sAlp[ph(k)] = alp;
-        sGam[ph(k)] = gam;
-        qp = qp + qq * rho;
-        qw = qw - qq * gam;
-        qq = -qq * alp;
-        rho1 = rho;
-        alp1 = alp;
-        gam1 = gam;
-        Fk = Fkm;
-        gk = gkm;
-        l0 = lm;
-        m0 = mm;
-        r0 = rm;
+    // Rows are fetched UB at a time (all loads of a batch issued before the
+    // elimination consumes them) so that each thread keeps many loads in flight.
+    constexpr int UB = sizeof(R) == 8 ? 4 : 8;
+    for (int k0 = e - 1; k0 >= s; k0 -= UB) {
+        R Lv[UB], Mv[UB], Rv[UB], Gv[UB], Ev[UB];
+#pragma unroll
+        for (int u = 0; u < UB; ++u) {
+            const int k = k0 - u >= s ? k0 - u : s;  // tail of the segment: repeat a valid row
+            const int km = k - 1, kf = km < 0 ? km + ny : km;
+            const R *row = Tin + (size_t)rowmap(km) * nx;
+            Lv[u] = row[il];
+            Mv[u] = row[ic];
+            Rv[u] = row[ir];
+            Gv[u] = ldcoef(Gc + (size_t)kf * nx + ic);
+            Ev[u] = ldcoef(Ec + (size_t)kf * nx + ic);
+        }
+#pragma unroll
+        for (int u = 0; u < UB; ++u) {
+            const int k = k0 - u;
+            if (k < s) break;
+            const R gkm = Gv[u];
+            const R Fkm = face_flux<R>(lim, lam, mu, gkm, Ev[u], Lv[u], Mv[u], Rv[u], l0, m0, r0);
+            const R rk = Fk - Fkm;
+            const R a = -lam * gkm, cc = -lam * gk, b = R(1) - a - cc;
+            const R inv = Num<R>::div(R(1), b - cc * alp1);
+            const R alp = a * inv, gam = -cc * gam1 * inv, rho = (rk - cc * rho1) * inv;
+            sRho[ph(k)] = rho;
+            sAlp[ph(k)] = alp;
+            sGam[ph(k)] = gam;
+            qp = qp + qq * rho;
+            qw = qw - qq * gam;
+            qq = -qq * alp;
+            rho1 = rho;
+            alp1 = alp;
+            gam1 = gam;
+            Fk = Fkm;
+            gk = gkm;
+            l0 = Lv[u];
+            m0 = Mv[u];
+            r0 = Rv[u];
+        }
     }
 
     // reduced system of column c across its P segments (threads t*Wb + c)
@@ -431,16 +497,24 @@ __global__ void __launch_bounds__(512) col_sweep_kernel(ColArgs args)
     if (active) {
         R *out = static_cast<R *>(J.Tout);
         R dprev = Xm;
-        for (int k = s; k < e; ++k) {
-            const R d = sRho[ph(k)] - sAlp[ph(k)] * dprev - sGam[ph(k)] * X;
-            dprev = d;
-            const R v = Tin[(size_t)k * nx + ic] + d;
-            out[(size_t)k * nx + ic] = v;
-            flag_nonfinite(args.err, v);
+        for (int k0 = s; k0 <= e; k0 += UB) {
+            R To[UB];
+#pragma unroll
+            for (int u = 0; u < UB; ++u) {
+                const int k = k0 + u <= e ? k0 + u : e;
+                To[u] = Tin[(size_t)k * nx + ic];
+            }
+#pragma unroll
+            for (int u = 0; u < UB; ++u) {
+                const int k = k0 + u;
+                if (k > e) break;
+                const R d = k < e ? sRho[ph(k)] - sAlp[ph(k)] * dprev - sGam[ph(k)] * X : X;
+                dprev = d;
+                const R v = To[u] + d;
+                out[(size_t)k * nx + ic] = v;
+                flag_nonfinite(args.err, v);
+            }
         }
-        const R v = Tin[(size_t)e * nx + ic] + X;
-        out[(size_t)e * nx + ic] = v;
-        flag_nonfinite(args.err, v);
     }
 }
 

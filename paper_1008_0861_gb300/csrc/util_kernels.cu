@@ -9,6 +9,9 @@ cudaError_t launch_col_f32(int coef_fp16, const ColArgs &a, int nblocks, int nth
                            cudaStream_t s);
 cudaError_t launch_line_f64(const LineArgs &a, int nblocks, int nthreads, size_t smem, cudaStream_t s);
 cudaError_t launch_col_f64(const ColArgs &a, int nblocks, int nthreads, size_t smem, cudaStream_t s);
+cudaError_t launch_line2_f32(int coef_fp16, const Line2Args &a, int nblocks, int nthreads, size_t smem,
+                             cudaStream_t s);
+cudaError_t launch_line2_f64(const Line2Args &a, int nblocks, int nthreads, size_t smem, cudaStream_t s);
 
 static int pow2floor(int v)
 {
@@ -85,6 +88,51 @@ cudaError_t launch_col(int prec, int coef_fp16, const ColArgs &a, int nblocks, i
 {
     if (prec == PREC_FP64) return launch_col_f64(a, nblocks, nthreads, smem, s);
     return launch_col_f32(coef_fp16, a, nblocks, nthreads, smem, s);
+}
+
+size_t line2_smem_bytes(int prec, int n, int team, int lines_per_block)
+{
+    const int N = prec == PREC_FP64 ? 2 : 4;
+    size_t words = (size_t)lines_per_block * (3 * (size_t)n + N);
+    if (team > 32) words += (size_t)lines_per_block * 8 * team;
+    return words * esize(prec);
+}
+
+// About 4 chunks (16 FP32 / 8 FP64 cells) per segment, so that a 256-thread
+// block needs ~49 KB of shared memory and four blocks share an SM; 256
+// threads per block unless a line needs more; the segment grows when shared
+// memory is short.
+bool line2_config(int prec, int n, bool transposed, int *team, int *lines_per_block, int *nthreads,
+                  size_t *smem)
+{
+    const int N = prec == PREC_FP64 ? 2 : 4;
+    if (n % N != 0 || n < 2 * N) return false;
+    if (transposed && n > MAX_LINE2_TRANSPOSED) return false;
+    const int m = n / N;
+    int P = pow2ceil((m + 3) / 4);
+    if (P > m) P = pow2floor(m);
+    if (P > 512) P = 512;
+    for (;;) {
+        const int NT = P > 256 ? P : 256;
+        const int lpb = NT / P;
+        const size_t sm = line2_smem_bytes(prec, n, P, lpb);
+        if (sm <= SMEM_LIMIT - 1024 && (!transposed || (lpb % N == 0))) {
+            *team = P;
+            *lines_per_block = lpb;
+            *nthreads = NT;
+            *smem = sm;
+            return true;
+        }
+        if (P == 1) return false;
+        P /= 2;
+    }
+}
+
+cudaError_t launch_line2(int prec, int coef_fp16, const Line2Args &a, int nblocks, int nthreads,
+                         size_t smem, cudaStream_t s)
+{
+    if (prec == PREC_FP64) return launch_line2_f64(a, nblocks, nthreads, smem, s);
+    return launch_line2_f32(coef_fp16, a, nblocks, nthreads, smem, s);
 }
 
 template <typename B, typename C>

@@ -33,11 +33,12 @@ def _inst(nx, ny, bc, seed=1):
 
 @pytest.mark.parametrize("nx,ny", SIZES)
 @pytest.mark.parametrize("bc", [0, 1])
-def test_single_sweeps_fp64(lib, nx, ny, bc):
+@pytest.mark.parametrize("fast", [True, False])
+def test_single_sweeps_fp64(lib, nx, ny, bc, fast):
     inst = _inst(nx, ny, bc, seed=nx * 7 + ny)
     T0, co = oracle_inputs(lib, inst, FP64)
     lamx, lamy, mu = O.lambdas(inst.dt, inst.dx, inst.dy, inst.chi_par)
-    g = GpuGrid(lib, inst, FP64)
+    g = GpuGrid(lib, inst, FP64, fast=fast)
     try:
         gx = g.sweep(lib.ANISO_DIR_X, T0)
         ox = O.xsweep(T0, co, bc, lamx, mu)
@@ -49,12 +50,15 @@ def test_single_sweeps_fp64(lib, nx, ny, bc):
         g.close()
 
 
-@pytest.mark.parametrize("nx,ny", [(50, 50), (64, 96), (33, 1030)])
+@pytest.mark.parametrize("nx,ny", [(50, 50), (64, 96), (33, 1030), (8, 6), (256, 2048), (2, 2)])
 @pytest.mark.parametrize("order", [0, 1, 2])
-def test_steps_fp64_all_orders(lib, nx, ny, order):
+@pytest.mark.parametrize("fast", [True, False])
+def test_steps_fp64_all_orders(lib, nx, ny, order, fast):
+    if (nx, ny) == (2, 2):
+        nx, ny = 12, 4
     inst = _inst(nx, ny, 1, seed=3)
     T0, co = oracle_inputs(lib, inst, FP64)
-    g = GpuGrid(lib, inst, FP64, order=order)
+    g = GpuGrid(lib, inst, FP64, order=order, fast=fast)
     try:
         nsteps = 7
         got = g.step(nsteps)
@@ -111,7 +115,7 @@ def test_chi_perp_and_unequal_spacing_fp64(lib):
         g.close()
 
 
-@pytest.mark.parametrize("nx,ny", [(256, 256), (96, 1024), (1024, 64), (100, 1200)])
+@pytest.mark.parametrize("nx,ny", [(256, 256), (96, 1024), (1024, 64), (100, 1200), (2048, 512)])
 def test_random_field_fp32(lib, nx, ny):
     """Random-field workload at reduced size, FP32, dt = 100x the explicit
     limit, 100 steps.  Tolerance: 1e-4, or 3x the FP32 noise floor of the
@@ -313,3 +317,50 @@ def test_large_grid_one_dimensional_mode_closed_form(lib):
         assert nf == 0 and abs(s / (n * n) - 2.0) < 1e-6
     finally:
         lib.aniso_destroy(h)
+
+
+@pytest.mark.parametrize("graph", [True, False])
+def test_kernel_timing_events(lib, graph):
+    """ANISO_OPT_PROFILE times every sweep launch, inside captured graphs too."""
+    inst = _inst(128, 96, 1, seed=6)
+    g = GpuGrid(lib, inst, FP32, graph=graph)
+    try:
+        lib.aniso_set_option(g.h, lib.ANISO_OPT_PROFILE, 1)
+        g.step(4)
+        g.step(4)
+        for kind in (lib.ANISO_KERNEL_XSWEEP, lib.ANISO_KERNEL_YSWEEP):
+            ms, n = lib.aniso_kernel_times(h=g.h, kind=kind)
+            assert n == 8 and ms > 0.0
+        lib.aniso_kernel_times(h=g.h, kind=0, reset=True)
+        assert lib.aniso_kernel_times(h=g.h, kind=1) == (0.0, 0)
+    finally:
+        g.close()
+
+
+@pytest.mark.parametrize("prec", [FP32, FP64])
+@pytest.mark.parametrize("nx,ny,bc", [(64, 96, 1), (128, 40, 0), (1024, 1024, 1), (36, 2048, 1)])
+def test_fast_path_matches_general_kernels(lib, prec, nx, ny, bc):
+    """The vectorised x-then-y path (transposed intermediate) and the general
+    kernels compute the same step: to 1e-12 per step in FP64, within FP32
+    rounding in FP32."""
+    inst = _inst(nx, ny, bc, seed=12)
+    a = GpuGrid(lib, inst, prec, fast=True)
+    b = GpuGrid(lib, inst, prec, fast=False)
+    try:
+        ga, gb = a.step(5), b.step(5)
+        tol = 5 * FP64_TOL_PER_STEP if prec == FP64 else 2e-5
+        assert rel_linf(ga, gb) < tol
+    finally:
+        a.close()
+        b.close()
+
+
+def test_fp16_field_fast_and_general_agree(lib):
+    inst = W.random_instance(256, 128, seed=31, chi_par=1.0, dt_factor=1000.0)
+    a = GpuGrid(lib, inst, FP32, fp16=True, fast=True)
+    b = GpuGrid(lib, inst, FP32, fp16=True, fast=False)
+    try:
+        assert rel_linf(a.step(3), b.step(3)) < 2e-5
+    finally:
+        a.close()
+        b.close()
