@@ -193,6 +193,29 @@ int aniso_step_batched(aniso_batch_t b, void *const *T, const double *dt, const 
 
 void aniso_batch_destroy(aniso_batch_t b);
 
+/* aniso_step without any device allocation.  (No counterpart in the paper: it
+ * exists for callers that are not allowed to allocate GPU memory, such as code
+ * running inside another framework's memory pool or under a fixed device
+ * memory budget; aniso_create/aniso_set_field allocate, this call does not.)
+ * It runs nsteps x-then-y steps (Eq. op_2step, van Leer limiter) of one grid
+ * in place on T, with the grid described by the same arguments as
+ * aniso_create and the field by device arrays bx, by (cell-centred, nx*ny,
+ * element type given by `precision`, ANISO_PREC_FP64 or ANISO_PREC_FP32).
+ * `stream` is a cudaStream_t (NULL: the legacy default stream); the call is
+ * asynchronous on it.
+ * Working memory (the face coefficients and T*) lives in one fixed device
+ * array of 20 MiB compiled into the library, which every GPU that loads the
+ * library holds until the process exits: at most 1,048,576 cells in FP32
+ * and 524,288 in FP64 (larger grids fail with ANISO_ERR_ARG and a message),
+ * and ny <= 1024.  The first call on a device looks up that array's device
+ * address (once per device, with the device current); make that first call
+ * before any stream capture.  Every call reuses the same array, so calls whose
+ * GPU work overlaps (other streams or host threads) race and corrupt each
+ * other: serialise them.  Non-finite results are not reported by this call. */
+int aniso_step_noalloc(int nx, int ny, double dx, double dy, double chi_par, double chi_perp, int bc,
+                       int precision, const void *bx, const void *by, void *T, double dt, int nsteps,
+                       void *stream);
+
 #ifdef __cplusplus
 }
 #endif

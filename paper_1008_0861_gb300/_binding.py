@@ -48,7 +48,7 @@ ANISO_KERNEL_TRANSPOSE = 2
 EXPORTED = ("aniso_create", "aniso_set_option", "aniso_set_field", "aniso_step", "aniso_sweep",
             "aniso_total", "aniso_get_state", "aniso_set_state", "aniso_sync",
             "aniso_kernel_times", "aniso_destroy", "aniso_last_error", "aniso_batch_create",
-            "aniso_step_batched", "aniso_batch_destroy")
+            "aniso_step_batched", "aniso_batch_destroy", "aniso_step_noalloc")
 
 
 class AnisoError(RuntimeError):
@@ -87,6 +87,7 @@ def load():
         "aniso_batch_create": (i, [i, P(vp), P(vp)]),
         "aniso_step_batched": (i, [vp, P(vp), P(d), P(i)]),
         "aniso_batch_destroy": (None, [vp]),
+        "aniso_step_noalloc": (i, [i, i, d, d, d, d, i, i, vp, vp, vp, d, i, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -190,3 +191,13 @@ def aniso_step_batched(batch, Ts, dts, nsteps):
 def aniso_batch_destroy(batch):
     if batch:
         load().aniso_batch_destroy(batch)
+
+
+def aniso_step_noalloc(nx, ny, dx, dy, chi_par, chi_perp, bc, precision, bx, by, T, dt, nsteps,
+                       stream=None):
+    """aniso_step without device allocation (fixed 20 MiB scratch array in
+    the library; see include/aniso.h).  For callers that may not allocate GPU
+    memory; serialise calls, they share that array."""
+    _check(load().aniso_step_noalloc(int(nx), int(ny), float(dx), float(dy), float(chi_par),
+                                     float(chi_perp), int(bc), int(precision), _ptr(bx), _ptr(by),
+                                     _ptr(T), float(dt), int(nsteps), _ptr(stream)))

@@ -40,6 +40,9 @@ static int fail(int code, const char *fmt, ...)
 
 extern "C" const char *aniso_last_error(void) { return g_last_error.c_str(); }
 
+// Lets other translation units of the library report through aniso_last_error.
+void aniso::record_error(const char *msg) { g_last_error = msg; }
+
 // ------------------------------------------------------------- profiling
 
 struct EventPair {

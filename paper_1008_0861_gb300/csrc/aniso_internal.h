@@ -120,4 +120,7 @@ constexpr int TOTALS_BLOCKS = 608;
 cudaError_t launch_totals(int prec, const void *T, size_t n, double *partials, double *result,
                           cudaStream_t s);
 
+// Set the message aniso_last_error() returns on this host thread.
+void record_error(const char *msg);
+
 }  // namespace aniso
