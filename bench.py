@@ -38,6 +38,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--instances", type=int, default=N_INST)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--segment", type=int, default=0,
+                    help="16-byte chunks per thread segment (0: library default)")
     return ap.parse_args()
 
 
@@ -59,7 +61,7 @@ def measured_peak():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("sweep_kernels.cuh", "aniso_internal.h", "util_kernels.cu"):
+    for f in ("sweep_kernels.cuh", "line2_kernel.cuh", "aniso_internal.h", "util_kernels.cu"):
         h.update(open(os.path.join(ROOT, "paper_1008_0861_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -236,6 +238,8 @@ def main():
     for inst in insts:
         h = P.aniso_create(inst.nx, inst.ny, inst.dx, inst.dy, inst.chi_par, 0.0, inst.bc)
         P.aniso_set_option(h, P.ANISO_OPT_PRECISION, P.ANISO_PREC_FP32)
+        if args.segment:
+            P.aniso_set_option(h, P.ANISO_OPT_SEGMENT, args.segment)
         bx = torch.tensor(inst.bx, dtype=torch.float32, device="cuda")
         by = torch.tensor(inst.by, dtype=torch.float32, device="cuda")
         P.aniso_set_field(h, bx, by)

@@ -71,8 +71,10 @@ enum {
     ANISO_OPT_STREAM = 5,     /* cudaStream_t cast to integer; 0 = legacy default stream */
     ANISO_OPT_GRAPH = 6,      /* 1 (default): replay aniso_step loops from a captured CUDA graph */
     ANISO_OPT_PROFILE = 7,    /* 1: time every sweep launch with CUDA events (aniso_kernel_times) */
-    ANISO_OPT_FAST_PATH = 8   /* 1 (default): vectorised line kernel with transposed intermediate
+    ANISO_OPT_FAST_PATH = 8,  /* 1 (default): vectorised line kernel with transposed intermediate
                                  for the x-then-y order; 0: the general kernels only */
+    ANISO_OPT_SEGMENT = 9     /* cells per thread segment of the vectorised kernel, in 16-byte
+                                 chunks (0 = default 4; larger: fewer threads per line) */
 };
 enum { ANISO_PREC_FP64 = 0, ANISO_PREC_FP32 = 1 };
 enum {

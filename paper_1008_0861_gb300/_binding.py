@@ -30,6 +30,7 @@ ANISO_OPT_STREAM = 5
 ANISO_OPT_GRAPH = 6
 ANISO_OPT_PROFILE = 7
 ANISO_OPT_FAST_PATH = 8
+ANISO_OPT_SEGMENT = 9
 ANISO_PREC_FP64 = 0
 ANISO_PREC_FP32 = 1
 ANISO_LIM_VANLEER = 0

@@ -98,7 +98,7 @@ struct aniso_ctx {
     int nx = 0, ny = 0, bc = 0;
     double dx = 0, dy = 0, chi_par = 0, chi_perp = 0;
     int prec = PREC_FP64, field_fp16 = 0, kahan = 0, limiter = LIM_VANLEER, order = ANISO_ORDER_XY;
-    int use_graph = 1, profile = 0, fast = 1;
+    int use_graph = 1, profile = 0, fast = 1, seg_chunks = 0;
     cudaStream_t stream = 0;
     long long step_counter = 0;
     bool field_set = false;
@@ -130,7 +130,8 @@ struct aniso_ctx {
     {
         int a, b, c;
         size_t d;
-        return line2_config(prec, nx, true, &a, &b, &c, &d) && line2_config(prec, ny, true, &a, &b, &c, &d);
+        return line2_config(prec, nx, true, &a, &b, &c, &d, seg_chunks) &&
+               line2_config(prec, ny, true, &a, &b, &c, &d, seg_chunks);
     }
     int max_line() const { return prec == PREC_FP64 ? MAX_LINE_FP64 : MAX_LINE_FP32; }
 };
@@ -221,6 +222,11 @@ extern "C" int aniso_set_option(aniso_t h, int key, long long v)
         h->fast = v != 0;
         drop_graph(h);
         break;
+    case ANISO_OPT_SEGMENT:
+        if (v < 0 || v > 64) return fail(ANISO_ERR_ARG, "bad segment length %lld", v);
+        h->seg_chunks = (int)v;
+        drop_graph(h);
+        break;
     default:
         return fail(ANISO_ERR_ARG, "unknown option key %d", key);
     }
@@ -290,7 +296,7 @@ static int enqueue_line2(aniso_ctx *h, const void *in, void *out, const void *g,
     J.transpose_out = transposed ? 1 : 0;
     int nthreads;
     size_t smem;
-    if (!line2_config(h->prec, n, transposed, &J.team, &J.lines_per_block, &nthreads, &smem))
+    if (!line2_config(h->prec, n, transposed, &J.team, &J.lines_per_block, &nthreads, &smem, h->seg_chunks))
         return fail(ANISO_ERR_UNSUPPORTED, "vectorised line kernel cannot take n=%d", n);
     J.block0 = 0;
     J.nblocks = (nlines + J.lines_per_block - 1) / J.lines_per_block;
@@ -390,7 +396,8 @@ static int enqueue_sweep(aniso_ctx *h, int dir, const void *in, void *out, doubl
     if (dir == ANISO_DIR_X) {
         int t1, t2, t3;
         size_t t4;
-        if (h->fast && aligned16(in) && aligned16(out) && line2_config(h->prec, h->nx, false, &t1, &t2, &t3, &t4))
+        if (h->fast && aligned16(in) && aligned16(out) &&
+            line2_config(h->prec, h->nx, false, &t1, &t2, &t3, &t4, h->seg_chunks))
             return enqueue_line2(h, in, out, h->cxx, h->cxy, h->nx, h->ny, per, per, lamx, mu, false,
                                  ANISO_KERNEL_XSWEEP, s, pairs);
         return line(in, out, h->cxx, h->cxy, h->nx, h->ny, per, per, lamx, ANISO_KERNEL_XSWEEP);
@@ -776,7 +783,7 @@ static int batch_build(aniso_batch *b, void *const *T, const double *dt, const i
                     J.per_line = per;
                     J.per_cross = per;
                     J.transpose_out = 1;
-                    line2_config(prec, J.n, true, &J.team, &J.lines_per_block, &nt, &sm);
+                    line2_config(prec, J.n, true, &J.team, &J.lines_per_block, &nt, &sm, h->seg_chunks);
                     fl.push_back(J);
                     continue;
                 }

@@ -90,8 +90,9 @@ constexpr int MAX_LINE2_TRANSPOSED = 2048;
 
 // Launch configuration helpers (host).
 // line2: returns false when the line cannot use the vectorised kernel.
+// seg_chunks: target 16-byte chunks per segment (0 = default of 4).
 bool line2_config(int prec, int n, bool transposed, int *team, int *lines_per_block, int *nthreads,
-                  size_t *smem);
+                  size_t *smem, int seg_chunks = 0);
 size_t line2_smem_bytes(int prec, int n, int team, int lines_per_block);
 void line_config(int prec, int n, int *team, int *lines_per_block, int *nthreads);
 size_t line_smem_bytes(int prec, int n, int team, int lines_per_block);

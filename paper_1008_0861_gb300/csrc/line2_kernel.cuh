@@ -70,15 +70,15 @@ __device__ __forceinline__ void ld_coef_chunk(const __half *p, float *o)
 __device__ __forceinline__ int swz_chunk(int c, int mfull) { return c < mfull ? c ^ ((c >> 3) & 7) : c; }
 
 // van Leer L(L(a,b),L(c,d)) in FP32 with one division: when all four share a
-// strict sign the nesting equals 4abcd / (ab(c+d) + cd(a+b)); a vanishing
-// denominator (differences below ~1e-15) gives 0, the limit of the nesting.
+// strict sign the nesting equals 4abcd / (ab(c+d) + cd(a+b)).
 __device__ __forceinline__ float vanleer4_fast(float a, float b, float c, float d)
 {
-    const float mn = fminf(fminf(a, b), fminf(c, d)), mx = fmaxf(fmaxf(a, b), fmaxf(c, d));
-    if (!(mn > 0.f || mx < 0.f)) return 0.f;
+    // same strict sign of all four <=> ab > 0, cd > 0, ac > 0.  Products below
+    // 1e-18 (differences below ~1e-9) give 0, the nesting's limit there; this
+    // also keeps the denominator a normal number.
     const float p = a * b, q = c * d;
+    if (!(p > 1e-18f && q > 1e-18f && a * c > 0.f)) return 0.f;
     const float den = fmaf(p, c + d, q * (a + b));
-    if (!(fabsf(den) > 1e-30f)) return 0.f;
     return __fdividef(4.f * p * q, den);
 }
 
@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(512, 2) line2_kernel(Line2Args args)
         R rho1 = R(0), alp1 = R(0), gam1 = R(-1);
         R qp = R(0), qq = R(1), qw = R(0);
         R ae, be, ce, re;
-        R f[N], gg[N], fp[N], gp[N];
+        R f[N] = {}, gg[N] = {}, fp[N] = {}, gp[N] = {};
         auto load_prev = [&](int cc) {
             if (cc > c_lo) {
                 V16<R>::unpack(vF[swz(cc - 1)], fp);
@@ -307,49 +307,66 @@ __global__ void __launch_bounds__(512, 2) line2_kernel(Line2Args args)
                 R to[N], d[N];
                 V16<R>::unpack(vo[c], to);
                 V16<R>::unpack(vF[swz(c)], d);
+                R sum = R(0);
 #pragma unroll
                 for (int v = 0; v < N; ++v) {
                     to[v] += d[v];
-                    bad |= !isfinite(to[v]);
+                    sum += to[v];
                 }
+                bad |= !(fabs(sum) < R(INFINITY));  // a NaN or infinity in the chunk
                 out[c] = V16<R>::pack(to);
             }
         }
     } else {
-        // out[p][line] (position-major, nl wide): each thread writes N lines of
-        // one position (a 16-byte store when the lines are aligned); thread
-        // (grp, p) with grp fastest, so consecutive threads cover consecutive
-        // line groups of a position.
+        // out[p][line] (position-major, nl wide).  Groups of N lanes take an
+        // N x N tile (N lines of the block x the N cells of one chunk): lane j
+        // reads chunk c of line j (16 bytes of T_old and of delta), the tile is
+        // transposed with N-1 rotating shuffles, and lane j writes cell
+        // c*N + j of the N lines as one 16-byte store.
         R *out = static_cast<R *>(J.Tout);
-        const int groups = LPB / N;  // a power of two: LPB is a multiple of N in this mode
-        const int logG = __ffs(groups) - 1;
-        const int grp = threadIdx.x & (groups - 1);
-        const int l0 = grp * N;
-        const bool vec_ok = (nl % N) == 0 && line0 + l0 + N <= nl;
-        const R *src[N];
-        const R *sl[N];
+        constexpr int logN = N == 4 ? 2 : 1;
+        const int quads = LPB / N;  // line groups; a power of two in this mode
+        const int logQ = __ffs(quads) - 1;
+        const int j = threadIdx.x & (N - 1);
+        const int grp = threadIdx.x >> logN, ngrp = blockDim.x >> logN;
+        const int total = quads * m;
+        for (int base = 0; base < total; base += ngrp) {
+            const int idx = base + grp;
+            const bool ok = idx < total;
+            const int q4 = ok ? (idx & (quads - 1)) : 0;
+            const int c = ok ? (idx >> logQ) : 0;
+            const int lrow = q4 * N + j;
+            const int ln = line0 + lrow < nl ? line0 + lrow : nl - 1;
+            R a[N], d[N];
+            V16<R>::unpack(reinterpret_cast<const VT *>(Tin + (size_t)ln * n)[c], a);
+            V16<R>::unpack(reinterpret_cast<const VT *>(reinterpret_cast<R *>(smem_raw) + lrow * LS)[swz(c)], d);
 #pragma unroll
-        for (int q = 0; q < N; ++q) {
-            const int ln = line0 + l0 + q < nl ? line0 + l0 + q : nl - 1;
-            src[q] = Tin + (size_t)ln * n;
-            sl[q] = reinterpret_cast<R *>(smem_raw) + (l0 + q) * LS;
-        }
-        const int pstride = blockDim.x >> logG;
-        for (int p = threadIdx.x >> logG; p < n; p += pstride) {
-            R v[N];
-            const int ap = at(p);
+            for (int v = 0; v < N; ++v) a[v] += d[v];
+            R o[N];
 #pragma unroll
-            for (int q = 0; q < N; ++q) {
-                v[q] = src[q][p] + sl[q][ap];
-                bad |= !isfinite(v[q]);
+            for (int r = 0; r < N; ++r) {
+                const int ks = (j - r) & (N - 1), kr = (j + r) & (N - 1);
+                R send = a[0];
+#pragma unroll
+                for (int v = 1; v < N; ++v) send = ks == v ? a[v] : send;
+                const R recv = __shfl_sync(full, send, kr, N);
+#pragma unroll
+                for (int v = 0; v < N; ++v) o[v] = kr == v ? recv : o[v];
             }
-            R *dst = out + (size_t)p * nl + line0 + l0;
-            if (vec_ok) {
-                *reinterpret_cast<VT *>(dst) = V16<R>::pack(v);
-            } else {
+            if (ok) {
+                R sum = R(0);
 #pragma unroll
-                for (int q = 0; q < N; ++q)
-                    if (line0 + l0 + q < nl) dst[q] = v[q];
+                for (int v = 0; v < N; ++v) sum += o[v];
+                bad |= !(fabs(sum) < R(INFINITY));
+                const int l0 = line0 + q4 * N;
+                R *dst = out + (size_t)(c * N + j) * nl + l0;
+                if ((nl & (N - 1)) == 0 && l0 + N <= nl) {
+                    *reinterpret_cast<VT *>(dst) = V16<R>::pack(o);
+                } else {
+#pragma unroll
+                    for (int v = 0; v < N; ++v)
+                        if (l0 + v < nl) dst[v] = o[v];
+                }
             }
         }
     }

@@ -103,13 +103,14 @@ size_t line2_smem_bytes(int prec, int n, int team, int lines_per_block)
 // threads per block unless a line needs more; the segment grows when shared
 // memory is short.
 bool line2_config(int prec, int n, bool transposed, int *team, int *lines_per_block, int *nthreads,
-                  size_t *smem)
+                  size_t *smem, int seg_chunks)
 {
+    const int sc = seg_chunks > 0 ? seg_chunks : 4;
     const int N = prec == PREC_FP64 ? 2 : 4;
     if (n % N != 0 || n < 2 * N) return false;
     if (transposed && n > MAX_LINE2_TRANSPOSED) return false;
     const int m = n / N;
-    int P = pow2ceil((m + 3) / 4);
+    int P = pow2ceil((m + sc - 1) / sc);
     if (P > m) P = pow2floor(m);
     if (P > 512) P = 512;
     for (;;) {
