@@ -40,6 +40,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--segment", type=int, default=0,
                     help="16-byte chunks per thread segment (0: library default)")
+    ap.add_argument("--fast", type=int, default=-1,
+                    help="ANISO_OPT_FAST_PATH value (-1: library default)")
     return ap.parse_args()
 
 
@@ -240,6 +242,8 @@ def main():
         P.aniso_set_option(h, P.ANISO_OPT_PRECISION, P.ANISO_PREC_FP32)
         if args.segment:
             P.aniso_set_option(h, P.ANISO_OPT_SEGMENT, args.segment)
+        if args.fast >= 0:
+            P.aniso_set_option(h, P.ANISO_OPT_FAST_PATH, args.fast)
         bx = torch.tensor(inst.bx, dtype=torch.float32, device="cuda")
         by = torch.tensor(inst.by, dtype=torch.float32, device="cuda")
         P.aniso_set_field(h, bx, by)

@@ -50,7 +50,7 @@ enum {
     ANISO_ERR_STATE = 2,       /* call out of order, e.g. aniso_step before aniso_set_field */
     ANISO_ERR_CUDA = 3,        /* a CUDA runtime call failed; message has the CUDA error */
     ANISO_ERR_NONFINITE = 4,   /* a step produced a NaN or infinite temperature */
-    ANISO_ERR_TIMEOUT = 5,     /* reserved for bounded device-side waits */
+    ANISO_ERR_TIMEOUT = 5,     /* a kernel's bounded wait for its staged input expired */
     ANISO_ERR_OOM = 6,         /* device allocation failed */
     ANISO_ERR_UNSUPPORTED = 7  /* valid request outside what this build handles */
 };
@@ -72,7 +72,8 @@ enum {
     ANISO_OPT_GRAPH = 6,      /* 1 (default): replay aniso_step loops from a captured CUDA graph */
     ANISO_OPT_PROFILE = 7,    /* 1: time every sweep launch with CUDA events (aniso_kernel_times) */
     ANISO_OPT_FAST_PATH = 8,  /* 1 (default): vectorised line kernel with transposed intermediate
-                                 for the x-then-y order; 0: the general kernels only */
+                                 for the x-then-y order; 2: the same with rows staged by bulk
+                                 asynchronous copies in persistent blocks; 0: general kernels only */
     ANISO_OPT_SEGMENT = 9     /* cells per thread segment of the vectorised kernel, in 16-byte
                                  chunks (0 = default 4; larger: fewer threads per line) */
 };

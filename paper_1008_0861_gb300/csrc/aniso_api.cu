@@ -126,13 +126,20 @@ struct aniso_ctx {
     int vec() const { return prec == PREC_FP64 ? 2 : 4; }
     // Grid shapes the vectorised x-then-y path handles: both line lengths a
     // multiple of the 16-byte vector and short enough for transposed output.
-    bool fast_shape() const
+    // 3: staged persistent kernel (line3, option value 2), 2: line2, 0: neither.
+    int fast_kind() const
     {
         int a, b, c;
         size_t d;
-        return line2_config(prec, nx, true, &a, &b, &c, &d, seg_chunks) &&
-               line2_config(prec, ny, true, &a, &b, &c, &d, seg_chunks);
+        if (fast == 2 && line3_config(prec, field_fp16, nx, true, seg_chunks, &a, &b, &c, &d) &&
+            line3_config(prec, field_fp16, ny, true, seg_chunks, &a, &b, &c, &d))
+            return 3;
+        if (line2_config(prec, nx, true, &a, &b, &c, &d, seg_chunks) &&
+            line2_config(prec, ny, true, &a, &b, &c, &d, seg_chunks))
+            return 2;
+        return 0;
     }
+    bool fast_shape() const { return fast_kind() != 0; }
     int max_line() const { return prec == PREC_FP64 ? MAX_LINE_FP64 : MAX_LINE_FP32; }
 };
 
@@ -219,7 +226,8 @@ extern "C" int aniso_set_option(aniso_t h, int key, long long v)
         h->profile = v != 0;
         break;
     case ANISO_OPT_FAST_PATH:
-        h->fast = v != 0;
+        if (v < 0 || v > 2) return fail(ANISO_ERR_ARG, "bad fast-path value %lld", v);
+        h->fast = (int)v;
         drop_graph(h);
         break;
     case ANISO_OPT_SEGMENT:
@@ -316,6 +324,53 @@ static int enqueue_line2(aniso_ctx *h, const void *in, void *out, const void *g,
     return ANISO_OK;
 }
 
+// One staged persistent line update (line3_kernel).
+static int enqueue_line3(aniso_ctx *h, const void *in, void *out, const void *g, const void *e, int n,
+                         int nlines, int per_line, int per_cross, double lam, double mu, bool transposed,
+                         int kind, cudaStream_t s, std::vector<int> *pairs)
+{
+    Line3Args a{};
+    a.jobs = nullptr;
+    a.njobs = 1;
+    a.limiter = h->limiter;
+    a.err = h->err;
+    Line3Job &J = a.one;
+    J.Tin = in;
+    J.Tout = out;
+    J.g = g;
+    J.e = e;
+    J.lam = lam;
+    J.mu = mu;
+    J.n = n;
+    J.nlines = nlines;
+    J.per_line = per_line;
+    J.per_cross = per_cross;
+    J.transpose_out = transposed ? 1 : 0;
+    int nthreads;
+    size_t smem;
+    if (!line3_config(h->prec, h->field_fp16, n, transposed, h->seg_chunks, &J.team, &J.lines_per_block,
+                      &nthreads, &smem))
+        return fail(ANISO_ERR_UNSUPPORTED, "staged line kernel cannot take n=%d", n);
+    J.group0 = 0;
+    J.ngroups = (nlines + J.lines_per_block - 1) / J.lines_per_block;
+    a.total_groups = J.ngroups;
+    a.work_off = (int)line3_stage_bytes(h->prec, h->field_fp16, n, J.team, J.lines_per_block);
+    int pidx = -1;
+    const unsigned rec_flags = pairs ? cudaEventRecordExternal : cudaEventRecordDefault;
+    if (h->profile) {
+        pidx = h->prof.take(kind);
+        if (pidx < 0) return fail(ANISO_ERR_CUDA, "event creation failed");
+        CU(cudaEventRecordWithFlags(h->prof.pool[pidx].a, s, rec_flags));
+    }
+    CU(launch_line3(h->prec, h->field_fp16, a, nthreads, smem, s));
+    if (h->profile) {
+        CU(cudaEventRecordWithFlags(h->prof.pool[pidx].b, s, rec_flags));
+        if (pairs) pairs->push_back(pidx);
+        else h->prof.pending.push_back(pidx);
+    }
+    return ANISO_OK;
+}
+
 // Fast path of one x-then-y step: the x-update reads T row-major and writes T*
 // column-major; the y-update reads T*'s columns as contiguous lines (with the
 // transposed y coefficients) and writes T back row-major.
@@ -331,11 +386,12 @@ static int enqueue_fast_step(aniso_ctx *h, void *T, double dt, cudaStream_t s, s
     const double lamy = h->chi_par * dt / (h->dy * h->dy);
     const double mu = h->chi_par * dt / (h->dx * h->dy);
     const int per = h->bc == ANISO_BC_PERIODIC;
-    int rc = enqueue_line2(h, T, h->tstar, h->cxx, h->cxy, h->nx, h->ny, per, per, lamx, mu, true,
-                           ANISO_KERNEL_XSWEEP, s, pairs);
+    auto launch = h->fast_kind() == 3 ? enqueue_line3 : enqueue_line2;
+    int rc = launch(h, T, h->tstar, h->cxx, h->cxy, h->nx, h->ny, per, per, lamx, mu, true,
+                    ANISO_KERNEL_XSWEEP, s, pairs);
     if (rc) return rc;
-    return enqueue_line2(h, h->tstar, T, h->cyyT, h->cyxT, h->ny, h->nx, per, per, lamy, mu, true,
-                         ANISO_KERNEL_YSWEEP, s, pairs);
+    return launch(h, h->tstar, T, h->cyyT, h->cyxT, h->ny, h->nx, per, per, lamy, mu, true,
+                  ANISO_KERNEL_YSWEEP, s, pairs);
 }
 
 // One directional update from `in` to `out` (distinct buffers) on stream s.
@@ -396,6 +452,10 @@ static int enqueue_sweep(aniso_ctx *h, int dir, const void *in, void *out, doubl
     if (dir == ANISO_DIR_X) {
         int t1, t2, t3;
         size_t t4;
+        if (h->fast == 2 && aligned16(in) && aligned16(out) &&
+            line3_config(h->prec, h->field_fp16, h->nx, false, h->seg_chunks, &t1, &t2, &t3, &t4))
+            return enqueue_line3(h, in, out, h->cxx, h->cxy, h->nx, h->ny, per, per, lamx, mu, false,
+                                 ANISO_KERNEL_XSWEEP, s, pairs);
         if (h->fast && aligned16(in) && aligned16(out) &&
             line2_config(h->prec, h->nx, false, &t1, &t2, &t3, &t4, h->seg_chunks))
             return enqueue_line2(h, in, out, h->cxx, h->cxy, h->nx, h->ny, per, per, lamx, mu, false,
@@ -549,6 +609,7 @@ static int check_err_flag(aniso_ctx *h)
     CU(cudaMemcpy(&flag, h->err, sizeof flag, cudaMemcpyDeviceToHost));
     if (flag) {
         CU(cudaMemset(h->err, 0, sizeof(unsigned)));
+        if (flag & 2u) return fail(ANISO_ERR_TIMEOUT, "a kernel gave up waiting for its staged rows");
         return fail(ANISO_ERR_NONFINITE, "a step produced a non-finite temperature");
     }
     return ANISO_OK;
@@ -670,10 +731,11 @@ static int batch_build(aniso_batch *b, void *const *T, const double *dt, const i
     // Every (global step, phase) launch is one list of line jobs (x) and one
     // of column jobs (y).  Identical lists are shared.
     struct Launch {
-        int kind;  // 0 line, 1 col, 2 vectorised line (line2)
+        int kind;  // 0 line, 1 col, 2/3 line2 (x/y), 4/5 line3 (x/y)
         size_t offset;
         int njobs, nblocks, nthreads;
         size_t smem;
+        int work_off = 0;
     };
     std::vector<unsigned char> blob;
     std::vector<Launch> launches;  // in enqueue order
@@ -747,14 +809,81 @@ static int batch_build(aniso_batch *b, void *const *T, const double *dt, const i
         launches.push_back(L);
     };
 
+    // line3 jobs: one launch per block size (normally a single launch)
+    auto add_line3 = [&](std::vector<Line3Job> &all, std::vector<int> &nts, int phase_xy) {
+        if (all.empty()) return;
+        std::vector<int> sizes(nts);
+        std::sort(sizes.begin(), sizes.end());
+        sizes.erase(std::unique(sizes.begin(), sizes.end()), sizes.end());
+        for (int NT : sizes) {
+            std::vector<Line3Job> jobs;
+            for (size_t k = 0; k < all.size(); ++k)
+                if (nts[k] == NT) jobs.push_back(all[k]);
+            std::stable_sort(jobs.begin(), jobs.end(), [](const Line3Job &a, const Line3Job &c) {
+                return (long long)a.n * a.nlines > (long long)c.n * c.nlines;
+            });
+            // one shared-memory layout for the whole launch: staging sized for the
+            // largest job, working arrays after it
+            int groups = 0;
+            size_t stage = 0, work = 0;
+            for (auto &J : jobs) {
+                J.group0 = groups;
+                J.ngroups = (J.nlines + J.lines_per_block - 1) / J.lines_per_block;
+                groups += J.ngroups;
+                const size_t st = line3_stage_bytes(prec, fp16, J.n, J.team, J.lines_per_block);
+                stage = std::max(stage, st);
+                work = std::max(work, line3_smem_bytes(prec, fp16, J.n, J.team, J.lines_per_block) - st);
+            }
+            Launch L{phase_xy == 0 ? 4 : 5, blob.size(), (int)jobs.size(), groups, NT, stage + work};
+            L.work_off = (int)stage;
+            const unsigned char *p = reinterpret_cast<const unsigned char *>(jobs.data());
+            blob.insert(blob.end(), p, p + jobs.size() * sizeof(Line3Job));
+            while (blob.size() % 16) blob.push_back(0);
+            launches.push_back(L);
+        }
+    };
+
     for (int s = 0; s < max_steps; ++s) {
         for (int phase = 0; phase < 2; ++phase) {
             std::vector<LineJob> xl;
             std::vector<ColJob> yl;
             std::vector<Line2Job> fl;
+            std::vector<Line3Job> tl;
+            std::vector<int> tl_nt;
             for (int k = 0; k < n; ++k) {
                 if (s >= nsteps[k]) continue;
                 aniso_ctx *h = b->hs[k];
+                if (use_fast(h, T[k]) && h->fast_kind() == 3) {
+                    const int per = h->bc == ANISO_BC_PERIODIC;
+                    Line3Job J{};
+                    int nt;
+                    size_t sm;
+                    if (phase == 0) {
+                        J.Tin = T[k];
+                        J.Tout = h->tstar;
+                        J.g = h->cxx;
+                        J.e = h->cxy;
+                        J.lam = h->chi_par * dt[k] / (h->dx * h->dx);
+                        J.n = h->nx;
+                        J.nlines = h->ny;
+                    } else {
+                        J.Tin = h->tstar;
+                        J.Tout = T[k];
+                        J.g = h->cyyT;
+                        J.e = h->cyxT;
+                        J.lam = h->chi_par * dt[k] / (h->dy * h->dy);
+                        J.n = h->ny;
+                        J.nlines = h->nx;
+                    }
+                    J.mu = h->chi_par * dt[k] / (h->dx * h->dy);
+                    J.per_line = per;
+                    J.per_cross = per;
+                    J.transpose_out = 1;
+                    line3_config(prec, fp16, J.n, true, h->seg_chunks, &J.team, &J.lines_per_block, &nt, &sm);
+                    tl.push_back(J);
+                    tl_nt.push_back(nt);
+                    continue;
+                }
                 if (use_fast(h, T[k])) {
                     // x: T (rows) -> T* (column-major); y: T* (columns) -> T (rows)
                     const int per = h->bc == ANISO_BC_PERIODIC;
@@ -825,6 +954,7 @@ static int batch_build(aniso_batch *b, void *const *T, const double *dt, const i
                     yl.push_back(J);
                 }
             }
+            add_line3(tl, tl_nt, phase);
             add_line2(fl, phase);
             add_line(xl);
             add_col(yl);
@@ -851,7 +981,8 @@ static int batch_build(aniso_batch *b, void *const *T, const double *dt, const i
     for (const Launch &L : launches) {
         int pidx = -1;
         if (b->profile) {
-            pidx = b->prof.take((L.kind == 0 || L.kind == 2) ? ANISO_KERNEL_XSWEEP : ANISO_KERNEL_YSWEEP);
+            pidx = b->prof.take((L.kind == 0 || L.kind == 2 || L.kind == 4) ? ANISO_KERNEL_XSWEEP
+                                                                            : ANISO_KERNEL_YSWEEP);
             if (pidx < 0 || cudaEventRecordWithFlags(b->prof.pool[pidx].a, b->cap_stream,
                                                      cudaEventRecordExternal) != cudaSuccess) {
                 rc = fail(ANISO_ERR_CUDA, "profiling event failed");
@@ -859,7 +990,16 @@ static int batch_build(aniso_batch *b, void *const *T, const double *dt, const i
             }
         }
         cudaError_t ce;
-        if (L.kind >= 2) {
+        if (L.kind >= 4) {
+            Line3Args a{};
+            a.jobs = reinterpret_cast<const Line3Job *>(static_cast<unsigned char *>(b->d_jobs) + L.offset);
+            a.njobs = L.njobs;
+            a.total_groups = L.nblocks;
+            a.work_off = L.work_off;
+            a.limiter = b->hs[0]->limiter;
+            a.err = err;
+            ce = launch_line3(prec, fp16, a, L.nthreads, L.smem, b->cap_stream);
+        } else if (L.kind >= 2) {
             Line2Args a{};
             a.jobs = reinterpret_cast<const Line2Job *>(static_cast<unsigned char *>(b->d_jobs) + L.offset);
             a.njobs = L.njobs;

@@ -67,19 +67,43 @@ __device__ __forceinline__ void ld_coef_chunk(const __half *p, float *o)
 // Chunk swizzle: within each complete group of 8 chunks, chunk c is stored at
 // c ^ ((c >> 3) & 7); the incomplete tail group (chunks >= mfull) is stored
 // unswizzled so that every index stays inside the line's m chunks.
+// The same from shared memory (plain loads).
+__device__ __forceinline__ void ld_coef_chunk_smem(const float *p, float *o)
+{
+    V16<float>::unpack(*reinterpret_cast<const float4 *>(p), o);
+}
+__device__ __forceinline__ void ld_coef_chunk_smem(const double *p, double *o)
+{
+    V16<double>::unpack(*reinterpret_cast<const double2 *>(p), o);
+}
+__device__ __forceinline__ void ld_coef_chunk_smem(const __half *p, float *o)
+{
+    const uint2 raw = *reinterpret_cast<const uint2 *>(p);
+    const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&raw.x));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&raw.y));
+    o[0] = a.x;
+    o[1] = a.y;
+    o[2] = b.x;
+    o[3] = b.y;
+}
+
 __device__ __forceinline__ int swz_chunk(int c, int mfull) { return c < mfull ? c ^ ((c >> 3) & 7) : c; }
 
-// van Leer L(L(a,b),L(c,d)) in FP32 with one division: when all four share a
-// strict sign the nesting equals 4abcd / (ab(c+d) + cd(a+b)).
+// van Leer L(L(a,b),L(c,d)) in FP32 with one division.  With a,b the two
+// differences of one cell and c,d those of the other, when all four share a
+// strict sign the nesting equals 4pq / (p(c+d) + q(a+b)), p = ab, q = cd.
+// Branch-free: p and q are clamped at 0 (a sign change within a cell gives
+// 0), and a sign change between the cells, (a+b)(c+d) <= 0, gives 0; products
+// below 1e-18 (differences below ~1e-9) also give 0, which keeps the
+// denominator a normal number.
 __device__ __forceinline__ float vanleer4_fast(float a, float b, float c, float d)
 {
-    // same strict sign of all four <=> ab > 0, cd > 0, ac > 0.  Products below
-    // 1e-18 (differences below ~1e-9) give 0, the nesting's limit there; this
-    // also keeps the denominator a normal number.
     const float p = a * b, q = c * d;
-    if (!(p > 1e-18f && q > 1e-18f && a * c > 0.f)) return 0.f;
-    const float den = fmaf(p, c + d, q * (a + b));
-    return __fdividef(4.f * p * q, den);
+    const float sab = a + b, scd = c + d;
+    const bool ok = (p > 1e-18f) & (q > 1e-18f) & (sab * scd > 0.f);
+    const float den = fmaf(p, scd, q * sab);
+    const float r = __fdividef(4.f * p * q, den);
+    return ok ? r : 0.f;
 }
 
 template <typename R> __device__ __forceinline__ R limit4_v2(int lim, R a, R b, R c, R d)
@@ -318,55 +342,42 @@ __global__ void __launch_bounds__(512, 2) line2_kernel(Line2Args args)
             }
         }
     } else {
-        // out[p][line] (position-major, nl wide).  Groups of N lanes take an
-        // N x N tile (N lines of the block x the N cells of one chunk): lane j
-        // reads chunk c of line j (16 bytes of T_old and of delta), the tile is
-        // transposed with N-1 rotating shuffles, and lane j writes cell
-        // c*N + j of the N lines as one 16-byte store.
+        // out[p][line] (position-major, nl wide): thread (group q4 of N lines,
+        // position p), group fastest, reads the N deltas of position p (one
+        // scalar per line, consecutive positions across lanes: no bank
+        // conflicts) and T_old, and writes the N lines as one 16-byte store.
         R *out = static_cast<R *>(J.Tout);
-        constexpr int logN = N == 4 ? 2 : 1;
-        const int quads = LPB / N;  // line groups; a power of two in this mode
+        const int quads = LPB / N;  // a power of two in this mode
         const int logQ = __ffs(quads) - 1;
-        const int j = threadIdx.x & (N - 1);
-        const int grp = threadIdx.x >> logN, ngrp = blockDim.x >> logN;
-        const int total = quads * m;
-        for (int base = 0; base < total; base += ngrp) {
-            const int idx = base + grp;
-            const bool ok = idx < total;
-            const int q4 = ok ? (idx & (quads - 1)) : 0;
-            const int c = ok ? (idx >> logQ) : 0;
-            const int lrow = q4 * N + j;
-            const int ln = line0 + lrow < nl ? line0 + lrow : nl - 1;
-            R a[N], d[N];
-            V16<R>::unpack(reinterpret_cast<const VT *>(Tin + (size_t)ln * n)[c], a);
-            V16<R>::unpack(reinterpret_cast<const VT *>(reinterpret_cast<R *>(smem_raw) + lrow * LS)[swz(c)], d);
+        const int q4 = threadIdx.x & (quads - 1);
+        const int l0 = q4 * N;
+        const R *src[N];
+        const R *sl[N];
 #pragma unroll
-            for (int v = 0; v < N; ++v) a[v] += d[v];
+        for (int v = 0; v < N; ++v) {
+            const int ln = line0 + l0 + v < nl ? line0 + l0 + v : nl - 1;
+            src[v] = Tin + (size_t)ln * n;
+            sl[v] = reinterpret_cast<R *>(smem_raw) + (l0 + v) * LS;
+        }
+        const bool vec_ok = (nl & (N - 1)) == 0 && line0 + l0 + N <= nl;
+        const int pstride = blockDim.x >> logQ;
+        for (int p = threadIdx.x >> logQ; p < n; p += pstride) {
+            const int ap = at(p);
             R o[N];
+            R sum = R(0);
 #pragma unroll
-            for (int r = 0; r < N; ++r) {
-                const int ks = (j - r) & (N - 1), kr = (j + r) & (N - 1);
-                R send = a[0];
-#pragma unroll
-                for (int v = 1; v < N; ++v) send = ks == v ? a[v] : send;
-                const R recv = __shfl_sync(full, send, kr, N);
-#pragma unroll
-                for (int v = 0; v < N; ++v) o[v] = kr == v ? recv : o[v];
+            for (int v = 0; v < N; ++v) {
+                o[v] = src[v][p] + sl[v][ap];
+                sum += o[v];
             }
-            if (ok) {
-                R sum = R(0);
+            bad |= !(fabs(sum) < R(INFINITY));
+            R *dst = out + (size_t)p * nl + line0 + l0;
+            if (vec_ok) {
+                *reinterpret_cast<VT *>(dst) = V16<R>::pack(o);
+            } else {
 #pragma unroll
-                for (int v = 0; v < N; ++v) sum += o[v];
-                bad |= !(fabs(sum) < R(INFINITY));
-                const int l0 = line0 + q4 * N;
-                R *dst = out + (size_t)(c * N + j) * nl + l0;
-                if ((nl & (N - 1)) == 0 && l0 + N <= nl) {
-                    *reinterpret_cast<VT *>(dst) = V16<R>::pack(o);
-                } else {
-#pragma unroll
-                    for (int v = 0; v < N; ++v)
-                        if (l0 + v < nl) dst[v] = o[v];
-                }
+                for (int v = 0; v < N; ++v)
+                    if (line0 + l0 + v < nl) dst[v] = o[v];
             }
         }
     }

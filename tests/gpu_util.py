@@ -36,7 +36,7 @@ class GpuGrid:
         P.aniso_set_option(self.h, P.ANISO_OPT_LIMITER, limiter)
         P.aniso_set_option(self.h, P.ANISO_OPT_ORDER, order)
         P.aniso_set_option(self.h, P.ANISO_OPT_GRAPH, int(graph))
-        P.aniso_set_option(self.h, P.ANISO_OPT_FAST_PATH, int(fast))
+        P.aniso_set_option(self.h, P.ANISO_OPT_FAST_PATH, int(fast))  # True/1 vectorised, 2 staged, 0 general
         self.bx = torch.tensor(inst.bx, dtype=self.dtype, device="cuda")
         self.by = torch.tensor(inst.by, dtype=self.dtype, device="cuda")
         P.aniso_set_field(self.h, self.bx, self.by)
