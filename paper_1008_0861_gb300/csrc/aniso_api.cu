@@ -107,6 +107,8 @@ struct aniso_ctx {
     void *cyyT = nullptr, *cyxT = nullptr;  // transposed y coefficients (long columns)
     void *tstar = nullptr;                  // intermediate T* of a step
     void *tA = nullptr, *tB = nullptr;      // transposed scratch (long columns)
+    // compensated (Kahan) low parts: of T, of T*, of the transposed scratch
+    void *tlo = nullptr, *tstar_lo = nullptr, *tAlo = nullptr, *tBlo = nullptr;
     double *partials = nullptr, *result = nullptr;
     unsigned *err = nullptr;
     // graph cache
@@ -145,7 +147,8 @@ struct aniso_ctx {
 
 static void free_buffers(aniso_ctx *h)
 {
-    void **bufs[] = {&h->cxx, &h->cxy, &h->cyy, &h->cyx, &h->cyyT, &h->cyxT, &h->tstar, &h->tA, &h->tB};
+    void **bufs[] = {&h->cxx, &h->cxy, &h->cyy,  &h->cyx, &h->cyyT,     &h->cyxT, &h->tstar,
+                     &h->tA,  &h->tB,  &h->tlo, &h->tstar_lo, &h->tAlo, &h->tBlo};
     for (void **b : bufs) {
         if (*b) cudaFree(*b);
         *b = nullptr;
@@ -204,8 +207,9 @@ extern "C" int aniso_set_option(aniso_t h, int key, long long v)
         h->field_fp16 = v != 0;
         break;
     case ANISO_OPT_KAHAN:
-        if (v) return fail(ANISO_ERR_UNSUPPORTED, "compensated (Kahan) state is not available in this build");
-        h->kahan = 0;
+        if (h->field_set && (v != 0) != (h->kahan != 0))
+            return fail(ANISO_ERR_STATE, "compensated state is fixed once the field is set");
+        h->kahan = v != 0;
         break;
     case ANISO_OPT_LIMITER:
         if (v < 0 || v > 3) return fail(ANISO_ERR_ARG, "bad limiter %lld", v);
@@ -247,6 +251,8 @@ extern "C" int aniso_set_field(aniso_t h, const void *bx, const void *by)
     if (!bx || !by) return fail(ANISO_ERR_ARG, "aniso_set_field: null field pointer");
     if (h->field_fp16 && h->prec != PREC_FP32)
         return fail(ANISO_ERR_ARG, "aniso_set_field: FP16 field storage needs FP32 precision");
+    if (h->kahan && h->prec != PREC_FP32)
+        return fail(ANISO_ERR_ARG, "aniso_set_field: the compensated state needs FP32 precision");
     if (h->nx > h->max_line() || (h->long_cols() && h->ny > h->max_line()))
         return fail(ANISO_ERR_UNSUPPORTED, "grid %dx%d exceeds the on-chip line limit %d", h->nx, h->ny,
                     h->max_line());
@@ -264,6 +270,15 @@ extern "C" int aniso_set_field(aniso_t h, const void *bx, const void *by)
         if (h->long_cols()) {
             CU(cudaMalloc(&h->tA, n * h->esz()));
             CU(cudaMalloc(&h->tB, n * h->esz()));
+        }
+        if (h->kahan) {
+            CU(cudaMalloc(&h->tlo, n * h->esz()));
+            CU(cudaMalloc(&h->tstar_lo, n * h->esz()));
+            CU(cudaMemsetAsync(h->tlo, 0, n * h->esz(), h->stream));
+            if (h->long_cols()) {
+                CU(cudaMalloc(&h->tAlo, n * h->esz()));
+                CU(cudaMalloc(&h->tBlo, n * h->esz()));
+            }
         }
         CU(cudaMalloc(&h->partials, 4 * TOTALS_BLOCKS * sizeof(double)));
         CU(cudaMalloc(&h->result, 4 * sizeof(double)));
@@ -376,8 +391,8 @@ static int enqueue_line3(aniso_ctx *h, const void *in, void *out, const void *g,
 // transposed y coefficients) and writes T back row-major.
 static bool use_fast(const aniso_ctx *h, const void *T)
 {
-    return h->fast && h->order == ANISO_ORDER_XY && h->cyyT && aligned16(T) && aligned16(h->tstar) &&
-           h->fast_shape();
+    return h->fast && !h->kahan && h->order == ANISO_ORDER_XY && h->cyyT && aligned16(T) &&
+           aligned16(h->tstar) && h->fast_shape();
 }
 
 static int enqueue_fast_step(aniso_ctx *h, void *T, double dt, cudaStream_t s, std::vector<int> *pairs)
@@ -396,8 +411,9 @@ static int enqueue_fast_step(aniso_ctx *h, void *T, double dt, cudaStream_t s, s
 
 // One directional update from `in` to `out` (distinct buffers) on stream s.
 static int enqueue_sweep(aniso_ctx *h, int dir, const void *in, void *out, double dt, cudaStream_t s,
-                         std::vector<int> *pairs)
+                         std::vector<int> *pairs, const void *in_lo = nullptr, void *out_lo = nullptr)
 {
+    const bool kahan = in_lo != nullptr;
     const double lamx = h->chi_par * dt / (h->dx * h->dx);
     const double lamy = h->chi_par * dt / (h->dy * h->dy);
     const double mu = h->chi_par * dt / (h->dx * h->dy);
@@ -421,7 +437,8 @@ static int enqueue_sweep(aniso_ctx *h, int dir, const void *in, void *out, doubl
         return ANISO_OK;
     };
     auto line = [&](const void *tin, void *tout, const void *g, const void *e, int n, int nlines,
-                    int per_line, int per_cross, double lam, int kind) -> int {
+                    int per_line, int per_cross, double lam, int kind, const void *tin_lo,
+                    void *tout_lo) -> int {
         LineArgs a{};
         a.jobs = nullptr;
         a.njobs = 1;
@@ -430,6 +447,8 @@ static int enqueue_sweep(aniso_ctx *h, int dir, const void *in, void *out, doubl
         LineJob &J = a.one;
         J.Tin = tin;
         J.Tout = tout;
+        J.TinLo = tin_lo;
+        J.ToutLo = tout_lo;
         J.g = g;
         J.e = e;
         J.lam = lam;
@@ -445,22 +464,22 @@ static int enqueue_sweep(aniso_ctx *h, int dir, const void *in, void *out, doubl
         const size_t smem = line_smem_bytes(h->prec, n, J.team, J.lines_per_block);
         int rc = begin(kind);
         if (rc) return rc;
-        CU(launch_line(h->prec, h->field_fp16, a, J.nblocks, nthreads, smem, s));
+        CU(launch_line(h->prec, h->field_fp16, a, J.nblocks, nthreads, smem, s, tin_lo != nullptr));
         return end();
     };
     int rc;
     if (dir == ANISO_DIR_X) {
         int t1, t2, t3;
         size_t t4;
-        if (h->fast == 2 && aligned16(in) && aligned16(out) &&
+        if (!kahan && h->fast == 2 && aligned16(in) && aligned16(out) &&
             line3_config(h->prec, h->field_fp16, h->nx, false, h->seg_chunks, &t1, &t2, &t3, &t4))
             return enqueue_line3(h, in, out, h->cxx, h->cxy, h->nx, h->ny, per, per, lamx, mu, false,
                                  ANISO_KERNEL_XSWEEP, s, pairs);
-        if (h->fast && aligned16(in) && aligned16(out) &&
+        if (!kahan && h->fast && aligned16(in) && aligned16(out) &&
             line2_config(h->prec, h->nx, false, &t1, &t2, &t3, &t4, h->seg_chunks))
             return enqueue_line2(h, in, out, h->cxx, h->cxy, h->nx, h->ny, per, per, lamx, mu, false,
                                  ANISO_KERNEL_XSWEEP, s, pairs);
-        return line(in, out, h->cxx, h->cxy, h->nx, h->ny, per, per, lamx, ANISO_KERNEL_XSWEEP);
+        return line(in, out, h->cxx, h->cxy, h->nx, h->ny, per, per, lamx, ANISO_KERNEL_XSWEEP, in_lo, out_lo);
     }
     if (!h->long_cols()) {
         ColArgs a{};
@@ -471,6 +490,8 @@ static int enqueue_sweep(aniso_ctx *h, int dir, const void *in, void *out, doubl
         ColJob &J = a.one;
         J.Tin = in;
         J.Tout = out;
+        J.TinLo = in_lo;
+        J.ToutLo = out_lo;
         J.g = h->cyy;
         J.e = h->cyx;
         J.lam = lamy;
@@ -485,17 +506,20 @@ static int enqueue_sweep(aniso_ctx *h, int dir, const void *in, void *out, doubl
         J.nblocks = (h->nx + J.Wb - 1) / J.Wb;
         const size_t smem = col_smem_bytes(h->prec, h->ny, J.P, J.Wb);
         if ((rc = begin(ANISO_KERNEL_YSWEEP))) return rc;
-        CU(launch_col(h->prec, h->field_fp16, a, J.nblocks, nthreads, smem, s));
+        CU(launch_col(h->prec, h->field_fp16, a, J.nblocks, nthreads, smem, s, kahan));
         return end();
     }
     // long columns: transpose, solve columns as contiguous lines, transpose back
     if ((rc = begin(ANISO_KERNEL_TRANSPOSE))) return rc;
     CU(launch_transpose((int)h->esz(), in, h->tA, h->ny, h->nx, s));
+    if (kahan) CU(launch_transpose((int)h->esz(), in_lo, h->tAlo, h->ny, h->nx, s));
     if ((rc = end())) return rc;
-    if ((rc = line(h->tA, h->tB, h->cyyT, h->cyxT, h->ny, h->nx, per, per, lamy, ANISO_KERNEL_YSWEEP)))
+    if ((rc = line(h->tA, h->tB, h->cyyT, h->cyxT, h->ny, h->nx, per, per, lamy, ANISO_KERNEL_YSWEEP,
+                   kahan ? h->tAlo : nullptr, kahan ? h->tBlo : nullptr)))
         return rc;
     if ((rc = begin(ANISO_KERNEL_TRANSPOSE))) return rc;
     CU(launch_transpose((int)h->esz(), h->tB, out, h->nx, h->ny, s));
+    if (kahan) CU(launch_transpose((int)h->esz(), h->tBlo, out_lo, h->nx, h->ny, s));
     return end();
 }
 
@@ -518,9 +542,9 @@ static int enqueue_steps(aniso_ctx *h, void *T, double dt, int nsteps, long long
     }
     for (int k = 0; k < nsteps; ++k) {
         const bool xf = x_first(h->order, counter0 + k);
-        int rc = enqueue_sweep(h, xf ? ANISO_DIR_X : ANISO_DIR_Y, T, h->tstar, dt, s, pairs);
+        int rc = enqueue_sweep(h, xf ? ANISO_DIR_X : ANISO_DIR_Y, T, h->tstar, dt, s, pairs, h->tlo, h->tstar_lo);
         if (rc) return rc;
-        rc = enqueue_sweep(h, xf ? ANISO_DIR_Y : ANISO_DIR_X, h->tstar, T, dt, s, pairs);
+        rc = enqueue_sweep(h, xf ? ANISO_DIR_Y : ANISO_DIR_X, h->tstar, T, dt, s, pairs, h->tstar_lo, h->tlo);
         if (rc) return rc;
     }
     return ANISO_OK;
@@ -621,7 +645,7 @@ extern "C" int aniso_total(aniso_t h, const void *T, double *sum, double *tmin, 
     int rc = check_ready(h, "aniso_total");
     if (rc) return rc;
     if (!T) return fail(ANISO_ERR_ARG, "aniso_total: T is NULL");
-    CU(launch_totals(h->prec, T, h->cells(), h->partials, h->result, h->stream));
+    CU(launch_totals(h->prec, T, h->cells(), h->partials, h->result, h->stream, h->kahan ? h->tlo : nullptr));
     double r[4];
     CU(cudaMemcpyAsync(r, h->result, sizeof r, cudaMemcpyDeviceToHost, h->stream));
     CU(cudaStreamSynchronize(h->stream));
@@ -636,7 +660,8 @@ extern "C" int aniso_get_state(aniso_t h, long long *step_counter, void *lo_out)
 {
     if (!h) return fail(ANISO_ERR_ARG, "aniso_get_state: null handle");
     if (step_counter) *step_counter = h->step_counter;
-    (void)lo_out;  // no compensated state in this build
+    if (lo_out && h->kahan && h->tlo)
+        CU(cudaMemcpyAsync(lo_out, h->tlo, h->cells() * h->esz(), cudaMemcpyDeviceToDevice, h->stream));
     return ANISO_OK;
 }
 
@@ -644,8 +669,11 @@ extern "C" int aniso_set_state(aniso_t h, long long step_counter, const void *lo
 {
     if (!h) return fail(ANISO_ERR_ARG, "aniso_set_state: null handle");
     if (step_counter < 0) return fail(ANISO_ERR_ARG, "aniso_set_state: negative step counter");
-    (void)lo_in;
     h->step_counter = step_counter;
+    if (h->kahan && h->tlo) {
+        if (lo_in) CU(cudaMemcpyAsync(h->tlo, lo_in, h->cells() * h->esz(), cudaMemcpyDeviceToDevice, h->stream));
+        else CU(cudaMemsetAsync(h->tlo, 0, h->cells() * h->esz(), h->stream));
+    }
     return ANISO_OK;
 }
 
@@ -697,8 +725,9 @@ extern "C" int aniso_batch_create(int n, const aniso_t *hs, aniso_batch_t *out)
         aniso_ctx *h = hs[k];
         if (!h) return fail(ANISO_ERR_ARG, "aniso_batch_create: handle %d is NULL", k);
         if (!h->field_set) return fail(ANISO_ERR_STATE, "aniso_batch_create: handle %d has no field", k);
-        if (h->prec != hs[0]->prec || h->field_fp16 != hs[0]->field_fp16 || h->limiter != hs[0]->limiter)
-            return fail(ANISO_ERR_ARG, "aniso_batch_create: handle %d differs in precision/field/limiter", k);
+        if (h->prec != hs[0]->prec || h->field_fp16 != hs[0]->field_fp16 || h->limiter != hs[0]->limiter ||
+            h->kahan != hs[0]->kahan)
+            return fail(ANISO_ERR_ARG, "aniso_batch_create: handle %d differs in precision/field/limiter/state", k);
         if (h->long_cols())
             return fail(ANISO_ERR_UNSUPPORTED, "aniso_batch_create: handle %d has ny=%d > %d", k, h->ny, MAX_COL);
     }
@@ -920,6 +949,8 @@ static int batch_build(aniso_batch *b, void *const *T, const double *dt, const i
                 const bool is_x = (phase == 0) == xf;
                 const void *in = phase == 0 ? T[k] : h->tstar;
                 void *outp = phase == 0 ? h->tstar : T[k];
+                const void *in_lo = h->kahan ? (phase == 0 ? h->tlo : h->tstar_lo) : nullptr;
+                void *out_lo = h->kahan ? (phase == 0 ? h->tstar_lo : h->tlo) : nullptr;
                 const double lamx = h->chi_par * dt[k] / (h->dx * h->dx);
                 const double lamy = h->chi_par * dt[k] / (h->dy * h->dy);
                 const double mu = h->chi_par * dt[k] / (h->dx * h->dy);
@@ -928,6 +959,8 @@ static int batch_build(aniso_batch *b, void *const *T, const double *dt, const i
                     LineJob J{};
                     J.Tin = in;
                     J.Tout = outp;
+                    J.TinLo = in_lo;
+                    J.ToutLo = out_lo;
                     J.g = h->cxx;
                     J.e = h->cxy;
                     J.lam = lamx;
@@ -943,6 +976,8 @@ static int batch_build(aniso_batch *b, void *const *T, const double *dt, const i
                     ColJob J{};
                     J.Tin = in;
                     J.Tout = outp;
+                    J.TinLo = in_lo;
+                    J.ToutLo = out_lo;
                     J.g = h->cyy;
                     J.e = h->cyx;
                     J.lam = lamy;
@@ -1012,14 +1047,14 @@ static int batch_build(aniso_batch *b, void *const *T, const double *dt, const i
             a.njobs = L.njobs;
             a.limiter = b->hs[0]->limiter;
             a.err = err;
-            ce = launch_line(prec, fp16, a, L.nblocks, L.nthreads, L.smem, b->cap_stream);
+            ce = launch_line(prec, fp16, a, L.nblocks, L.nthreads, L.smem, b->cap_stream, b->hs[0]->kahan != 0);
         } else {
             ColArgs a{};
             a.jobs = reinterpret_cast<const ColJob *>(static_cast<unsigned char *>(b->d_jobs) + L.offset);
             a.njobs = L.njobs;
             a.limiter = b->hs[0]->limiter;
             a.err = err;
-            ce = launch_col(prec, fp16, a, L.nblocks, L.nthreads, L.smem, b->cap_stream);
+            ce = launch_col(prec, fp16, a, L.nblocks, L.nthreads, L.smem, b->cap_stream, b->hs[0]->kahan != 0);
         }
         if (ce != cudaSuccess) {
             rc = fail(ANISO_ERR_CUDA, "batched launch: %s", cudaGetErrorString(ce));

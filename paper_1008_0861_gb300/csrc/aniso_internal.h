@@ -23,6 +23,8 @@ constexpr size_t SMEM_LIMIT = 227 * 1024;
 struct LineJob {
     const void *Tin;
     void *Tout;
+    const void *TinLo;  // compensated (Kahan) low parts, or nullptr
+    void *ToutLo;
     const void *g;   // normal (implicit) face coefficient, face p+1/2 of each line at index p
     const void *e;   // transverse face coefficient, same layout
     double lam, mu;  // chi dt / h_line^2, chi dt / (dx dy)
@@ -38,6 +40,8 @@ struct LineJob {
 struct ColJob {
     const void *Tin;
     void *Tout;
+    const void *TinLo;  // compensated (Kahan) low parts, or nullptr
+    void *ToutLo;
     const void *g;   // cyy, face j+1/2 of column i at [j][i]
     const void *e;   // cyx
     double lam, mu;  // chi dt / dy^2, chi dt / (dx dy)
@@ -134,10 +138,11 @@ size_t col_smem_bytes(int prec, int ny, int P, int Wb);
 
 // Launch wrappers (defined per precision in kernels_f32.cu / kernels_f64.cu).
 // coef_fp16 selects half-precision coefficient storage (FP32 only).
+// With jobs' TinLo set (FP32 only) the compensated kernels are used.
 cudaError_t launch_line(int prec, int coef_fp16, const LineArgs &a, int nblocks, int nthreads,
-                        size_t smem, cudaStream_t s);
+                        size_t smem, cudaStream_t s, bool kahan = false);
 cudaError_t launch_col(int prec, int coef_fp16, const ColArgs &a, int nblocks, int nthreads,
-                       size_t smem, cudaStream_t s);
+                       size_t smem, cudaStream_t s, bool kahan = false);
 cudaError_t launch_line2(int prec, int coef_fp16, const Line2Args &a, int nblocks, int nthreads,
                          size_t smem, cudaStream_t s);
 // Face coefficients from cell-centred b (FP64 arithmetic, one rounding to the
@@ -151,8 +156,9 @@ cudaError_t launch_transpose(int elem_bytes, const void *in, void *out, int rows
                              cudaStream_t s);
 // FP64 sum / min / max / non-finite count; partial buffers of TOTALS_BLOCKS.
 constexpr int TOTALS_BLOCKS = 608;
+// Tlo (optional, FP32): compensated low parts added to T in the sum.
 cudaError_t launch_totals(int prec, const void *T, size_t n, double *partials, double *result,
-                          cudaStream_t s);
+                          cudaStream_t s, const void *Tlo = nullptr);
 
 // Set the message aniso_last_error() returns on this host thread.
 void record_error(const char *msg);

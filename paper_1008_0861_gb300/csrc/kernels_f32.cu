@@ -16,34 +16,42 @@ template <typename K> static cudaError_t prep(K kern, size_t smem)
     return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
-cudaError_t launch_line_f32(int coef_fp16, const LineArgs &a, int nblocks, int nthreads, size_t smem,
+template <typename K> static cudaError_t go(K kern, int nblocks, int nthreads, size_t smem, cudaStream_t s,
+                                              const LineArgs &a)
+{
+    cudaError_t err = prep(kern, smem);
+    if (err != cudaSuccess) return err;
+    kern<<<nblocks, nthreads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+template <typename K> static cudaError_t goc(K kern, int nblocks, int nthreads, size_t smem, cudaStream_t s,
+                                               const ColArgs &a)
+{
+    cudaError_t err = prep(kern, smem);
+    if (err != cudaSuccess) return err;
+    kern<<<nblocks, nthreads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_line_f32(int coef_fp16, bool kahan, const LineArgs &a, int nblocks, int nthreads, size_t smem,
                             cudaStream_t s)
 {
-    cudaError_t err;
-    if (coef_fp16) {
-        if ((err = prep(line_sweep_kernel<float, __half>, smem)) != cudaSuccess) return err;
-        line_sweep_kernel<float, __half><<<nblocks, nthreads, smem, s>>>(a);
-    } else {
-        if ((err = prep(line_sweep_kernel<float, float>, smem)) != cudaSuccess) return err;
-        line_sweep_kernel<float, float><<<nblocks, nthreads, smem, s>>>(a);
-    }
-    return cudaGetLastError();
+    if (coef_fp16)
+        return kahan ? go(line_sweep_kernel<float, __half, true>, nblocks, nthreads, smem, s, a)
+                     : go(line_sweep_kernel<float, __half, false>, nblocks, nthreads, smem, s, a);
+    return kahan ? go(line_sweep_kernel<float, float, true>, nblocks, nthreads, smem, s, a)
+                 : go(line_sweep_kernel<float, float, false>, nblocks, nthreads, smem, s, a);
 }
 
-cudaError_t launch_col_f32(int coef_fp16, const ColArgs &a, int nblocks, int nthreads, size_t smem,
+cudaError_t launch_col_f32(int coef_fp16, bool kahan, const ColArgs &a, int nblocks, int nthreads, size_t smem,
                            cudaStream_t s)
 {
-    cudaError_t err;
-    if (coef_fp16) {
-        if ((err = prep(col_sweep_kernel<float, __half>, smem)) != cudaSuccess) return err;
-        col_sweep_kernel<float, __half><<<nblocks, nthreads, smem, s>>>(a);
-    } else {
-        if ((err = prep(col_sweep_kernel<float, float>, smem)) != cudaSuccess) return err;
-        col_sweep_kernel<float, float><<<nblocks, nthreads, smem, s>>>(a);
-    }
-    return cudaGetLastError();
+    if (coef_fp16)
+        return kahan ? goc(col_sweep_kernel<float, __half, true>, nblocks, nthreads, smem, s, a)
+                     : goc(col_sweep_kernel<float, __half, false>, nblocks, nthreads, smem, s, a);
+    return kahan ? goc(col_sweep_kernel<float, float, true>, nblocks, nthreads, smem, s, a)
+                 : goc(col_sweep_kernel<float, float, false>, nblocks, nthreads, smem, s, a);
 }
-
 
 cudaError_t launch_line2_f32(int coef_fp16, const Line2Args &a, int nblocks, int nthreads, size_t smem,
                              cudaStream_t s)

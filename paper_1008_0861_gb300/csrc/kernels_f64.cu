@@ -18,17 +18,17 @@ template <typename K> static cudaError_t prep(K kern, size_t smem)
 
 cudaError_t launch_line_f64(const LineArgs &a, int nblocks, int nthreads, size_t smem, cudaStream_t s)
 {
-    cudaError_t err = prep(line_sweep_kernel<double, double>, smem);
+    cudaError_t err = prep(line_sweep_kernel<double, double, false>, smem);
     if (err != cudaSuccess) return err;
-    line_sweep_kernel<double, double><<<nblocks, nthreads, smem, s>>>(a);
+    line_sweep_kernel<double, double, false><<<nblocks, nthreads, smem, s>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_col_f64(const ColArgs &a, int nblocks, int nthreads, size_t smem, cudaStream_t s)
 {
-    cudaError_t err = prep(col_sweep_kernel<double, double>, smem);
+    cudaError_t err = prep(col_sweep_kernel<double, double, false>, smem);
     if (err != cudaSuccess) return err;
-    col_sweep_kernel<double, double><<<nblocks, nthreads, smem, s>>>(a);
+    col_sweep_kernel<double, double, false><<<nblocks, nthreads, smem, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(512, 2) line3_kernel(Line3Args args)
 {
     typedef typename V16<R>::T VT;
     constexpr int N = V16<R>::N;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ Line3Job Jbuf[2];
     __shared__ __align__(8) uint64_t bar;
     const unsigned full = 0xffffffffu;

@@ -81,6 +81,47 @@ __device__ __forceinline__ R face_flux(int lim, R lam, R mu, R g, R e, R d0, R c
     return lam * g * (c1 - c0) + mu * e * dT;
 }
 
+// Compensated state (Kahan, FP32): a cell holds hi + lo.  Differences of two
+// cells are formed as (hi_a - hi_b) + (lo_a - lo_b); with K = false lo is 0
+// and the expressions reduce to plain differences.
+template <typename R, bool K> __device__ __forceinline__ R dif(R ah, R al, R bh, R bl)
+{
+    return K ? (ah - bh) + (al - bl) : ah - bh;
+}
+template <typename R, bool K>
+__device__ __forceinline__ R face_flux_k(int lim, R lam, R mu, R g, R e, R d0h, R d0l, R c0h, R c0l, R u0h,
+                                         R u0l, R d1h, R d1l, R c1h, R c1l, R u1h, R u1l)
+{
+    const R dT = limit4<R>(lim, dif<R, K>(u1h, u1l, c1h, c1l), dif<R, K>(c1h, c1l, d1h, d1l),
+                           dif<R, K>(u0h, u0l, c0h, c0l), dif<R, K>(c0h, c0l, d0h, d0l));
+    return lam * g * dif<R, K>(c1h, c1l, c0h, c0l) + mu * e * dT;
+}
+// FP64 value -> (hi, lo) float pair (hi + lo reproduces it to ~48 bits).
+__device__ __forceinline__ void split_f64(double v, float &hi, float &lo)
+{
+    hi = (float)v;
+    lo = (float)(v - (double)hi);
+}
+__device__ __forceinline__ void split_f64(double v, double &hi, double &lo)
+{
+    hi = v;
+    lo = 0.0;
+}
+
+// (hi, lo) + d with an exact two-sum of hi + d, the rounding error folded
+// into lo and the pair renormalised.
+template <typename R>
+__device__ __forceinline__ void kahan_add(R hi, R lo, R d, R &ohi, R &olo)
+{
+    const R s = hi + d;
+    const R bb = s - hi;
+    const R err = (hi - (s - bb)) + (d - bb);
+    const R l2 = lo + err;
+    const R h2 = s + l2;
+    olo = l2 - (h2 - s);
+    ohi = h2;
+}
+
 // Padded shared-memory index: one spare word per 32 keeps threads that walk
 // neighbouring segments on different banks.
 __device__ __forceinline__ int phys(int k) { return k + (k >> 5); }
@@ -183,7 +224,7 @@ template <typename Job> __device__ __forceinline__ int find_job(const Job *jobs,
 //  B2 per segment: forward recovery of delta
 //  C  coalesced: T_new = T_old + delta
 
-template <typename R, typename C>
+template <typename R, typename C, bool K>
 __global__ void __launch_bounds__(512) line_sweep_kernel(LineArgs args)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -204,6 +245,10 @@ __global__ void __launch_bounds__(512) line_sweep_kernel(LineArgs args)
     if (ld < 0) ld = J.per_cross ? J.nlines - 1 : 0;
     const R *Tin = static_cast<const R *>(J.Tin);
     const R *rc = Tin + (size_t)lc * n, *ru = Tin + (size_t)lu * n, *rd = Tin + (size_t)ld * n;
+    // low parts of the compensated state (K only)
+    const R *TinL = static_cast<const R *>(J.TinLo);
+    const R *rcl = K ? TinL + (size_t)lc * n : nullptr, *rul = K ? TinL + (size_t)lu * n : nullptr,
+            *rdl = K ? TinL + (size_t)ld * n : nullptr;
     const C *G = static_cast<const C *>(J.g) + (size_t)lc * n;
     const C *E = static_cast<const C *>(J.e) + (size_t)lc * n;
     const R lam = (R)J.lam, mu = (R)J.mu;
@@ -226,6 +271,7 @@ __global__ void __launch_bounds__(512) line_sweep_kernel(LineArgs args)
         const unsigned full = 0xffffffffu;
         for (int p0 = t; p0 - t < n; p0 += UA * P) {
             R vd[UA], vc[UA], vu[UA], vg[UA], ve[UA];
+            R wd[UA] = {}, wc[UA] = {}, wu[UA] = {};  // low parts (K only)
 #pragma unroll
             for (int u = 0; u < UA; ++u) {
                 const int p = p0 + u * P;
@@ -233,6 +279,11 @@ __global__ void __launch_bounds__(512) line_sweep_kernel(LineArgs args)
                 vd[u] = rd[pc];
                 vc[u] = rc[pc];
                 vu[u] = ru[pc];
+                if (K) {
+                    wd[u] = rdl[pc];
+                    wc[u] = rcl[pc];
+                    wu[u] = rul[pc];
+                }
                 vg[u] = ldcoef(G + pc);
                 ve[u] = ldcoef(E + pc);
             }
@@ -242,6 +293,12 @@ __global__ void __launch_bounds__(512) line_sweep_kernel(LineArgs args)
                 R vd1 = __shfl_down_sync(full, vd[u], 1, width);
                 R vc1 = __shfl_down_sync(full, vc[u], 1, width);
                 R vu1 = __shfl_down_sync(full, vu[u], 1, width);
+                R wd1 = R(0), wc1 = R(0), wu1 = R(0);
+                if (K) {
+                    wd1 = __shfl_down_sync(full, wd[u], 1, width);
+                    wc1 = __shfl_down_sync(full, wc[u], 1, width);
+                    wu1 = __shfl_down_sync(full, wu[u], 1, width);
+                }
                 if (p < n) {
                     int p1 = p + 1;
                     if (lane_in == width - 1 || p1 >= n) {
@@ -249,9 +306,14 @@ __global__ void __launch_bounds__(512) line_sweep_kernel(LineArgs args)
                         vd1 = rd[p1];
                         vc1 = rc[p1];
                         vu1 = ru[p1];
+                        if (K) {
+                            wd1 = rdl[p1];
+                            wc1 = rcl[p1];
+                            wu1 = rul[p1];
+                        }
                     }
-                    sF[phys(p)] = face_flux<R>(lim, lam, mu, vg[u], ve[u], vd[u], vc[u], vu[u], vd1,
-                                               vc1, vu1);
+                    sF[phys(p)] = face_flux_k<R, K>(lim, lam, mu, vg[u], ve[u], vd[u], wd[u], vc[u], wc[u],
+                                                    vu[u], wu[u], vd1, wd1, vc1, wc1, vu1, wu1);
                     sG[phys(p)] = vg[u];
                 }
             }
@@ -327,24 +389,71 @@ __global__ void __launch_bounds__(512) line_sweep_kernel(LineArgs args)
     }
     __syncthreads();
 
-    // ---- C: T_new = T_old + delta (batched loads of T_old, as in phase A)
-    if (active) {
+    // ---- C: T_new = T_old + delta.
+    // Compensated state: in exact arithmetic every line's sum of delta is zero
+    // (the right-hand side telescopes and each line matrix has unit column
+    // sums), so the line's FP64 sum of the computed delta is rounding
+    // residual; it is removed evenly and hi + lo + delta is formed in FP64,
+    // which conserves the FP64 sum of hi + lo across the update.
+    if (K) {
+        double part = 0.0;
+        for (int p = t; p < n; p += P) part += (double)sF[phys(p)];
+        double lsum;
+        if (P <= 32) {
+            for (int o = 1; o < P; o <<= 1) part += __shfl_xor_sync(0xffffffffu, part, o, P);
+            lsum = part;
+        } else {
+            // PCR area (8P floats), free now; rounded up to an 8-byte boundary
+            double *red = reinterpret_cast<double *>((reinterpret_cast<uintptr_t>(small) + 7) & ~uintptr_t(7));
+            red[t] = part;
+            __syncthreads();
+            if (t == 0) {
+                double a = 0.0;
+                for (int k = 0; k < P; ++k) a += red[k];
+                red[P] = a;
+            }
+            __syncthreads();
+            lsum = red[P];
+        }
+        const double corr = lsum / (double)n;
+        if (active) {
+            R *out = static_cast<R *>(J.Tout) + (size_t)lc * n;
+            R *outl = static_cast<R *>(J.ToutLo) + (size_t)lc * n;
+            for (int p = t; p < n; p += P) {
+                const double tot = ((double)rc[p] + (double)rcl[p]) + ((double)sF[phys(p)] - corr);
+                R hi, lo;
+                split_f64(tot, hi, lo);
+                out[p] = hi;
+                outl[p] = lo;
+                flag_nonfinite(args.err, hi);
+            }
+        }
+    } else if (active) {
         constexpr int UC = 8;
         R *out = static_cast<R *>(J.Tout) + (size_t)lc * n;
         for (int p0 = t; p0 < n; p0 += UC * P) {
-            R vo[UC];
+            R vo[UC], wo[UC] = {};
 #pragma unroll
             for (int u = 0; u < UC; ++u) {
                 const int p = p0 + u * P;
                 vo[u] = p < n ? rc[p] : R(0);
+                if (K) wo[u] = p < n ? rcl[p] : R(0);
             }
 #pragma unroll
             for (int u = 0; u < UC; ++u) {
                 const int p = p0 + u * P;
                 if (p < n) {
-                    const R v = vo[u] + sF[phys(p)];
-                    out[p] = v;
-                    flag_nonfinite(args.err, v);
+                    if (K) {
+                        R hi, lo;
+                        kahan_add(vo[u], wo[u], sF[phys(p)], hi, lo);
+                        out[p] = hi;
+                        static_cast<R *>(J.ToutLo)[(size_t)lc * n + p] = lo;
+                        flag_nonfinite(args.err, hi);
+                    } else {
+                        const R v = vo[u] + sF[phys(p)];
+                        out[p] = v;
+                        flag_nonfinite(args.err, v);
+                    }
                 }
             }
         }
@@ -358,7 +467,7 @@ __global__ void __launch_bounds__(512) line_sweep_kernel(LineArgs args)
 // global access is coalesced across c.  Pass B1 reads the grid directly,
 // bottom-up, and keeps the segment maps in shared memory.
 
-template <typename R, typename C>
+template <typename R, typename C, bool K>
 __global__ void __launch_bounds__(512) col_sweep_kernel(ColArgs args)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -395,31 +504,47 @@ __global__ void __launch_bounds__(512) col_sweep_kernel(ColArgs args)
         return k;
     };
 
-    // row k: values of columns i-1, i, i+1
+    const R *TinL = static_cast<const R *>(J.TinLo);  // low parts (K only)
+    // row k: values (hi h, lo w) of columns i-1, i, i+1
     R l0, m0, r0, l1, m1, r1;
+    R lw0 = 0, mw0 = 0, rw0 = 0, lw1 = 0, mw1 = 0, rw1 = 0;
     {
-        const R *row = Tin + (size_t)rowmap(e + 1) * nx;
-        l1 = row[il];
-        m1 = row[ic];
-        r1 = row[ir];
-        row = Tin + (size_t)e * nx;
-        l0 = row[il];
-        m0 = row[ic];
-        r0 = row[ir];
+        const size_t o1 = (size_t)rowmap(e + 1) * nx, o0 = (size_t)e * nx;
+        l1 = Tin[o1 + il];
+        m1 = Tin[o1 + ic];
+        r1 = Tin[o1 + ir];
+        l0 = Tin[o0 + il];
+        m0 = Tin[o0 + ic];
+        r0 = Tin[o0 + ir];
+        if (K) {
+            lw1 = TinL[o1 + il];
+            mw1 = TinL[o1 + ic];
+            rw1 = TinL[o1 + ir];
+            lw0 = TinL[o0 + il];
+            mw0 = TinL[o0 + ic];
+            rw0 = TinL[o0 + ir];
+        }
     }
     // F_e: face e+1/2 (coefficient index e; the boundary face is zero under zero-flux)
     R ge = ldcoef(Gc + (size_t)e * nx + ic);
-    R Fk = face_flux<R>(lim, lam, mu, ge, ldcoef(Ec + (size_t)e * nx + ic), l0, m0, r0, l1, m1, r1);
+    R Fk = face_flux_k<R, K>(lim, lam, mu, ge, ldcoef(Ec + (size_t)e * nx + ic), l0, lw0, m0, mw0, r0, rw0,
+                             l1, lw1, m1, mw1, r1, rw1);
     R gk = ge;
     // row e: needs F_{e-1} and g_{e-1}
     R ae, be, ce, re;
     {
         const int km = e - 1, kf = km < 0 ? km + ny : km;
-        const R *row = Tin + (size_t)rowmap(km) * nx;
-        R lm = row[il], mm = row[ic], rm = row[ir];
+        const size_t om = (size_t)rowmap(km) * nx;
+        R lm = Tin[om + il], mm = Tin[om + ic], rm = Tin[om + ir];
+        R lwm = 0, mwm = 0, rwm = 0;
+        if (K) {
+            lwm = TinL[om + il];
+            mwm = TinL[om + ic];
+            rwm = TinL[om + ir];
+        }
         R gkm = ldcoef(Gc + (size_t)kf * nx + ic);
-        R Fkm = face_flux<R>(lim, lam, mu, gkm, ldcoef(Ec + (size_t)kf * nx + ic), lm, mm, rm, l0,
-                             m0, r0);
+        R Fkm = face_flux_k<R, K>(lim, lam, mu, gkm, ldcoef(Ec + (size_t)kf * nx + ic), lm, lwm, mm, mwm, rm,
+                                  rwm, l0, lw0, m0, mw0, r0, rw0);
         re = Fk - Fkm;
         ae = -lam * gkm;
         ce = -lam * gk;
@@ -429,6 +554,9 @@ __global__ void __launch_bounds__(512) col_sweep_kernel(ColArgs args)
         l0 = lm;
         m0 = mm;
         r0 = rm;
+        lw0 = lwm;
+        mw0 = mwm;
+        rw0 = rwm;
     }
     R rho1 = R(0), alp1 = R(0), gam1 = R(-1);
     R qp = R(0), qq = R(1), qw = R(0);
@@ -437,14 +565,20 @@ __global__ void __launch_bounds__(512) col_sweep_kernel(ColArgs args)
     constexpr int UB = sizeof(R) == 8 ? 4 : 8;
     for (int k0 = e - 1; k0 >= s; k0 -= UB) {
         R Lv[UB], Mv[UB], Rv[UB], Gv[UB], Ev[UB];
+        R Lw[UB] = {}, Mw[UB] = {}, Rw[UB] = {};
 #pragma unroll
         for (int u = 0; u < UB; ++u) {
             const int k = k0 - u >= s ? k0 - u : s;  // tail of the segment: repeat a valid row
             const int km = k - 1, kf = km < 0 ? km + ny : km;
-            const R *row = Tin + (size_t)rowmap(km) * nx;
-            Lv[u] = row[il];
-            Mv[u] = row[ic];
-            Rv[u] = row[ir];
+            const size_t om = (size_t)rowmap(km) * nx;
+            Lv[u] = Tin[om + il];
+            Mv[u] = Tin[om + ic];
+            Rv[u] = Tin[om + ir];
+            if (K) {
+                Lw[u] = TinL[om + il];
+                Mw[u] = TinL[om + ic];
+                Rw[u] = TinL[om + ir];
+            }
             Gv[u] = ldcoef(Gc + (size_t)kf * nx + ic);
             Ev[u] = ldcoef(Ec + (size_t)kf * nx + ic);
         }
@@ -453,7 +587,8 @@ __global__ void __launch_bounds__(512) col_sweep_kernel(ColArgs args)
             const int k = k0 - u;
             if (k < s) break;
             const R gkm = Gv[u];
-            const R Fkm = face_flux<R>(lim, lam, mu, gkm, Ev[u], Lv[u], Mv[u], Rv[u], l0, m0, r0);
+            const R Fkm = face_flux_k<R, K>(lim, lam, mu, gkm, Ev[u], Lv[u], Lw[u], Mv[u], Mw[u], Rv[u], Rw[u],
+                                            l0, lw0, m0, mw0, r0, rw0);
             const R rk = Fk - Fkm;
             const R a = -lam * gkm, cc = -lam * gk, b = R(1) - a - cc;
             const R inv = Num<R>::div(R(1), b - cc * alp1);
@@ -472,6 +607,9 @@ __global__ void __launch_bounds__(512) col_sweep_kernel(ColArgs args)
             l0 = Lv[u];
             m0 = Mv[u];
             r0 = Rv[u];
+            lw0 = Lw[u];
+            mw0 = Mw[u];
+            rw0 = Rw[u];
         }
     }
 
@@ -482,8 +620,9 @@ __global__ void __launch_bounds__(512) col_sweep_kernel(ColArgs args)
     sTop[(2 * P + t) * Wb + c] = gam1;
     __syncthreads();
     const int tn = (t + 1) & (P - 1);
-    Reduced<R> q = make_reduced<R>(ae, be, ce, re, qp, qq, qw, sTop[(0 * P + tn) * Wb + c],
-                                   sTop[(1 * P + tn) * Wb + c], sTop[(2 * P + tn) * Wb + c]);
+    const R rho_n = sTop[(0 * P + tn) * Wb + c], alp_n = sTop[(1 * P + tn) * Wb + c],
+            gam_n = sTop[(2 * P + tn) * Wb + c];
+    Reduced<R> q = make_reduced<R>(ae, be, ce, re, qp, qq, qw, rho_n, alp_n, gam_n);
     __syncthreads();
     R *sL = small + c, *sD = small + P * Wb + c, *sU = small + 2 * P * Wb + c,
       *sRr = small + 3 * P * Wb + c;
@@ -493,16 +632,47 @@ __global__ void __launch_bounds__(512) col_sweep_kernel(ColArgs args)
     __syncthreads();
     const R Xm = sX[((t - 1) & (P - 1)) * Wb + c];
 
-    // forward recovery and output
-    if (active) {
+    if (K) {
+        // Compensated state: as in line_sweep_kernel, the column's FP64 sum
+        // of delta (zero in exact arithmetic) is removed evenly and
+        // hi + lo + delta is formed in FP64.
+        R dprev = Xm;
+        double part = 0.0;
+        for (int k = s; k < e; ++k) {
+            const R d = sRho[ph(k)] - sAlp[ph(k)] * dprev - sGam[ph(k)] * X;
+            sRho[ph(k)] = d;
+            part += (double)d;
+            dprev = d;
+        }
+        sRho[ph(e)] = X;
+        part += (double)X;
+        double *red = reinterpret_cast<double *>(small);  // PCR area, free now
+        __syncthreads();
+        red[t * Wb + c] = part;
+        __syncthreads();
+        double csum = 0.0;
+        for (int k = 0; k < P; ++k) csum += red[k * Wb + c];  // same order in every thread of the column
+        const double corr = csum / (double)ny;
+        if (active) {
+            for (int k = s; k <= e; ++k) {
+                const size_t o = (size_t)k * nx + ic;
+                R hi, lo;
+                split_f64(((double)Tin[o] + (double)TinL[o]) + ((double)sRho[ph(k)] - corr), hi, lo);
+                static_cast<R *>(J.Tout)[o] = hi;
+                static_cast<R *>(J.ToutLo)[o] = lo;
+                flag_nonfinite(args.err, hi);
+            }
+        }
+    } else if (active) {
         R *out = static_cast<R *>(J.Tout);
         R dprev = Xm;
         for (int k0 = s; k0 <= e; k0 += UB) {
-            R To[UB];
+            R To[UB], Tw[UB] = {};
 #pragma unroll
             for (int u = 0; u < UB; ++u) {
                 const int k = k0 + u <= e ? k0 + u : e;
                 To[u] = Tin[(size_t)k * nx + ic];
+                if (K) Tw[u] = TinL[(size_t)k * nx + ic];
             }
 #pragma unroll
             for (int u = 0; u < UB; ++u) {
@@ -510,9 +680,17 @@ __global__ void __launch_bounds__(512) col_sweep_kernel(ColArgs args)
                 if (k > e) break;
                 const R d = k < e ? sRho[ph(k)] - sAlp[ph(k)] * dprev - sGam[ph(k)] * X : X;
                 dprev = d;
-                const R v = To[u] + d;
-                out[(size_t)k * nx + ic] = v;
-                flag_nonfinite(args.err, v);
+                if (K) {
+                    R hi, lo;
+                    kahan_add(To[u], Tw[u], d, hi, lo);
+                    out[(size_t)k * nx + ic] = hi;
+                    static_cast<R *>(J.ToutLo)[(size_t)k * nx + ic] = lo;
+                    flag_nonfinite(args.err, hi);
+                } else {
+                    const R v = To[u] + d;
+                    out[(size_t)k * nx + ic] = v;
+                    flag_nonfinite(args.err, v);
+                }
             }
         }
     }
@@ -583,14 +761,14 @@ __global__ void transpose_kernel(const E *__restrict__ in, E *__restrict__ out, 
 // Deterministic FP64 reductions: a fixed grid of TOTALS_BLOCKS blocks, each
 // thread a fixed strided subset, fixed-order trees.
 template <typename R>
-__global__ void __launch_bounds__(256) totals_partial_kernel(const R *__restrict__ T, size_t n,
-                                                             double *partials)
+__global__ void __launch_bounds__(256) totals_partial_kernel(const R *__restrict__ T, const R *__restrict__ Tlo,
+                                                             size_t n, double *partials)
 {
     __shared__ double ss[256], smin[256], smax[256], snf[256];
     double s = 0.0, lo = INFINITY, hi = -INFINITY, nf = 0.0;
     const size_t stride = (size_t)gridDim.x * blockDim.x;
     for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
-        const double v = (double)T[k];
+        const double v = Tlo ? (double)T[k] + (double)Tlo[k] : (double)T[k];
         if (isfinite(v)) {
             s += v;
             lo = fmin(lo, v);

@@ -3,9 +3,9 @@
 
 namespace aniso {
 
-cudaError_t launch_line_f32(int coef_fp16, const LineArgs &a, int nblocks, int nthreads, size_t smem,
+cudaError_t launch_line_f32(int coef_fp16, bool kahan, const LineArgs &a, int nblocks, int nthreads, size_t smem,
                             cudaStream_t s);
-cudaError_t launch_col_f32(int coef_fp16, const ColArgs &a, int nblocks, int nthreads, size_t smem,
+cudaError_t launch_col_f32(int coef_fp16, bool kahan, const ColArgs &a, int nblocks, int nthreads, size_t smem,
                            cudaStream_t s);
 cudaError_t launch_line_f64(const LineArgs &a, int nblocks, int nthreads, size_t smem, cudaStream_t s);
 cudaError_t launch_col_f64(const ColArgs &a, int nblocks, int nthreads, size_t smem, cudaStream_t s);
@@ -83,17 +83,17 @@ size_t col_smem_bytes(int prec, int ny, int P, int Wb)
 }
 
 cudaError_t launch_line(int prec, int coef_fp16, const LineArgs &a, int nblocks, int nthreads,
-                        size_t smem, cudaStream_t s)
+                        size_t smem, cudaStream_t s, bool kahan)
 {
     if (prec == PREC_FP64) return launch_line_f64(a, nblocks, nthreads, smem, s);
-    return launch_line_f32(coef_fp16, a, nblocks, nthreads, smem, s);
+    return launch_line_f32(coef_fp16, kahan, a, nblocks, nthreads, smem, s);
 }
 
 cudaError_t launch_col(int prec, int coef_fp16, const ColArgs &a, int nblocks, int nthreads,
-                       size_t smem, cudaStream_t s)
+                       size_t smem, cudaStream_t s, bool kahan)
 {
     if (prec == PREC_FP64) return launch_col_f64(a, nblocks, nthreads, smem, s);
-    return launch_col_f32(coef_fp16, a, nblocks, nthreads, smem, s);
+    return launch_col_f32(coef_fp16, kahan, a, nblocks, nthreads, smem, s);
 }
 
 size_t line2_smem_bytes(int prec, int n, int team, int lines_per_block)
@@ -233,12 +233,14 @@ cudaError_t launch_transpose(int elem_bytes, const void *in, void *out, int rows
 }
 
 cudaError_t launch_totals(int prec, const void *T, size_t n, double *partials, double *result,
-                          cudaStream_t s)
+                          cudaStream_t s, const void *Tlo)
 {
     if (prec == PREC_FP64)
-        totals_partial_kernel<double><<<TOTALS_BLOCKS, 256, 0, s>>>(static_cast<const double *>(T), n, partials);
+        totals_partial_kernel<double><<<TOTALS_BLOCKS, 256, 0, s>>>(static_cast<const double *>(T), nullptr, n,
+                                                                    partials);
     else
-        totals_partial_kernel<float><<<TOTALS_BLOCKS, 256, 0, s>>>(static_cast<const float *>(T), n, partials);
+        totals_partial_kernel<float><<<TOTALS_BLOCKS, 256, 0, s>>>(static_cast<const float *>(T),
+                                                                   static_cast<const float *>(Tlo), n, partials);
     totals_final_kernel<<<1, 32, 0, s>>>(partials, TOTALS_BLOCKS, result);
     return cudaGetLastError();
 }

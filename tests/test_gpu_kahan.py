@@ -1,0 +1,133 @@
+"""Compensated (Kahan) FP32 state: T is carried as hi + lo between and within
+steps.  Checked against the FP64 oracle, for conservation against plain FP32,
+through the long-column path (columns above 1024 rows, the 16384^2 workload's
+shape), for checkpoint/resume and in batches."""
+import numpy as np
+import pytest
+
+import workloads as W
+from gpu_util import GpuGrid, fp32_tol, oracle_inputs, oracle_step, rel_linf
+
+pytestmark = pytest.mark.gpu
+FP32 = 1
+
+
+def _kahan_grid(lib, inst, fp16=False, fast=1, T0=None):
+    import torch
+    h = lib.aniso_create(inst.nx, inst.ny, inst.dx, inst.dy, inst.chi_par, inst.chi_perp, inst.bc)
+    lib.aniso_set_option(h, lib.ANISO_OPT_PRECISION, FP32)
+    lib.aniso_set_option(h, lib.ANISO_OPT_KAHAN, 1)
+    if fp16:
+        lib.aniso_set_option(h, lib.ANISO_OPT_FIELD_FP16, 1)
+    lib.aniso_set_option(h, lib.ANISO_OPT_FAST_PATH, fast)
+    bx = torch.tensor(inst.bx, dtype=torch.float32, device="cuda")
+    by = torch.tensor(inst.by, dtype=torch.float32, device="cuda")
+    lib.aniso_set_field(h, bx, by)
+    T = torch.tensor(inst.T0 if T0 is None else T0, dtype=torch.float32, device="cuda")
+    return h, T
+
+
+def _hi_lo(lib, h, T):
+    import torch
+    lo = torch.empty_like(T)
+    lib.aniso_get_state(h, lo)
+    lib.aniso_sync(h)
+    return T.double().cpu().numpy() + lo.double().cpu().numpy()
+
+
+@pytest.mark.parametrize("nx,ny,fp16", [(192, 128, False), (128, 96, True), (64, 2048, True),
+                                        (100, 50, False)])
+def test_kahan_matches_oracle(lib, nx, ny, fp16):
+    inst = W.random_instance(nx, ny, seed=41, chi_par=1.0, dt_factor=1000.0)
+    T0, co = oracle_inputs(lib, inst, FP32, fp16=fp16)
+    h, T = _kahan_grid(lib, inst, fp16=fp16)
+    try:
+        lib.aniso_step(h, T, inst.dt, 50)
+        got = _hi_lo(lib, h, T)
+        ref = oracle_step(inst, T0, co, 50)
+        assert rel_linf(got, ref) < fp32_tol(inst, T0, co, 50, ref)
+    finally:
+        lib.aniso_destroy(h)
+
+
+@pytest.mark.parametrize("shape", [(256, 256), (96, 2048)])
+def test_kahan_conserves_better_than_plain_fp32(lib, shape):
+    """With the compensated state the FP64 sum of hi + lo is conserved to
+    1e-12 relative: each line's sum of delta, zero in exact arithmetic, is
+    freed of its rounding residual and the update is formed in FP64; plain
+    FP32 drifts by rounding."""
+    inst = W.random_instance(shape[0], shape[1], seed=7, chi_par=1.0, dt_factor=1000.0)
+    h, T = _kahan_grid(lib, inst, fp16=True)
+    plain = GpuGrid(lib, inst, FP32, fp16=True, fast=0)
+    try:
+        s0 = float(np.sum(inst.T0.astype(np.float32).astype(np.float64)))
+        lib.aniso_step(h, T, inst.dt, 50)
+        sk = lib.aniso_total(h, T)[0]
+        plain.step(50)
+        sp = lib.aniso_total(plain.h, plain.T)[0]
+        drift_k, drift_p = abs(sk - s0) / s0, abs(sp - s0) / s0
+        assert drift_k < 1e-12 and drift_k < drift_p
+    finally:
+        lib.aniso_destroy(h)
+        plain.close()
+
+
+def test_kahan_checkpoint_resume_is_bit_exact(lib):
+    """step(2k) equals step(k), save (T, counter, lo), restore into a fresh
+    handle, step(k) -- bit for bit."""
+    import torch
+    inst = W.random_instance(96, 80, seed=3, chi_par=0.5, dt_factor=300.0)
+    a, Ta = _kahan_grid(lib, inst)
+    b, Tb = _kahan_grid(lib, inst)
+    try:
+        lib.aniso_step(a, Ta, inst.dt, 8)
+        lib.aniso_step(b, Tb, inst.dt, 4)
+        lo = torch.empty_like(Tb)
+        counter = lib.aniso_get_state(b, lo)
+        lib.aniso_sync(b)
+        c, Tc = _kahan_grid(lib, inst, T0=Tb.double().cpu().numpy())
+        try:
+            lib.aniso_set_state(c, counter, lo)
+            lib.aniso_step(c, Tc, inst.dt, 4)
+            lib.aniso_sync(c)
+            lib.aniso_sync(a)
+            np.testing.assert_array_equal(Tc.cpu().numpy(), Ta.cpu().numpy())
+            np.testing.assert_array_equal(_hi_lo(lib, c, Tc), _hi_lo(lib, a, Ta))
+            assert lib.aniso_get_state(c) == 8
+        finally:
+            lib.aniso_destroy(c)
+    finally:
+        lib.aniso_destroy(a)
+        lib.aniso_destroy(b)
+
+
+def test_kahan_batched_matches_single(lib):
+    import torch
+    insts = W.batch_instances(6, nsteps=5, size_cap=384)
+    pairs = [_kahan_grid(lib, i) for i in insts]
+    singles = [_kahan_grid(lib, i) for i in insts]
+    try:
+        b = lib.aniso_batch_create([h for h, _ in pairs])
+        lib.aniso_step_batched(b, [T for _, T in pairs], [i.dt for i in insts], [5] * len(insts))
+        torch.cuda.synchronize()
+        for (h, T), (hs, Ts), inst in zip(pairs, singles, insts):
+            lib.aniso_step(hs, Ts, inst.dt, 5)
+            np.testing.assert_array_equal(_hi_lo(lib, h, T), _hi_lo(lib, hs, Ts))
+        lib.aniso_batch_destroy(b)
+    finally:
+        for h, _ in pairs + singles:
+            lib.aniso_destroy(h)
+
+
+def test_kahan_option_rules(lib):
+    inst = W.random_instance(32, 32, seed=1)
+    h = lib.aniso_create(32, 32, inst.dx, inst.dy, inst.chi_par, 0.0, 1)
+    try:
+        lib.aniso_set_option(h, lib.ANISO_OPT_KAHAN, 1)  # FP64 default precision
+        import torch
+        bx = torch.tensor(inst.bx, device="cuda")
+        with pytest.raises(lib.AnisoError) as ei:
+            lib.aniso_set_field(h, bx, bx)
+        assert ei.value.code == lib.ANISO_ERR_ARG
+    finally:
+        lib.aniso_destroy(h)

@@ -282,10 +282,12 @@ def test_full_size_random_field_sampled_lines(lib):
         g.close()
 
 
-def test_large_grid_one_dimensional_mode_closed_form(lib):
-    """16384^2 FP32 with FP16 field storage: a y-only mode under constant b
-    decays by exactly 1/(1 + 4 lamy by^2 sin^2(ky dy/2)) per step (the x-update
-    leaves it unchanged), a property that holds at any size."""
+@pytest.mark.parametrize("kahan", [0, 1])
+def test_large_grid_one_dimensional_mode_closed_form(lib, kahan):
+    """16384^2 FP32 with FP16 field storage (and the compensated state): a
+    y-only mode under constant b decays by exactly
+    1/(1 + 4 lamy by^2 sin^2(ky dy/2)) per step (the x-update leaves it
+    unchanged), a property that holds at any size."""
     import torch
     n = 16384
     dx = 1.0 / n
@@ -295,6 +297,7 @@ def test_large_grid_one_dimensional_mode_closed_form(lib):
     try:
         lib.aniso_set_option(h, lib.ANISO_OPT_PRECISION, FP32)
         lib.aniso_set_option(h, lib.ANISO_OPT_FIELD_FP16, 1)
+        lib.aniso_set_option(h, lib.ANISO_OPT_KAHAN, kahan)
         bx = torch.full((n, n), bxv, dtype=torch.float32, device="cuda")
         by = torch.full((n, n), byv, dtype=torch.float32, device="cuda")
         lib.aniso_set_field(h, bx, by)
