@@ -182,9 +182,9 @@ const char *aniso_last_error(void);
  * field set) so that one launch per sweep advances all of them: the
  * paper's update applied to independent grids of uneven sizes, fields and
  * timesteps.  The batch uses the first handle's stream and options
- * GRAPH/PROFILE.  The handles must outlive the batch.  Errors:
- * ANISO_ERR_ARG, ANISO_ERR_STATE, ANISO_ERR_UNSUPPORTED (ny above the
- * on-chip column limit of 1024). */
+ * GRAPH/PROFILE.  The handles must outlive the batch.  Grids with more than
+ * 1024 rows take their y-updates through the transpose path, captured into the
+ * same graph.  Errors: ANISO_ERR_ARG, ANISO_ERR_STATE. */
 int aniso_batch_create(int n, const aniso_t *hs, aniso_batch_t *out);
 
 /* Advance grid k of the batch by nsteps[k] steps of size dt[k] in place on

@@ -728,8 +728,6 @@ extern "C" int aniso_batch_create(int n, const aniso_t *hs, aniso_batch_t *out)
         if (h->prec != hs[0]->prec || h->field_fp16 != hs[0]->field_fp16 || h->limiter != hs[0]->limiter ||
             h->kahan != hs[0]->kahan)
             return fail(ANISO_ERR_ARG, "aniso_batch_create: handle %d differs in precision/field/limiter/state", k);
-        if (h->long_cols())
-            return fail(ANISO_ERR_UNSUPPORTED, "aniso_batch_create: handle %d has ny=%d > %d", k, h->ny, MAX_COL);
     }
     aniso_batch *b = new aniso_batch;
     b->hs.assign(hs, hs + n);
@@ -765,6 +763,12 @@ static int batch_build(aniso_batch *b, void *const *T, const double *dt, const i
         int njobs, nblocks, nthreads;
         size_t smem;
         int work_off = 0;
+        // kind 6: one grid's sweep captured on its own (columns above the
+        // on-chip limit go through the transpose path)
+        int inst = -1, dir = 0;
+        const void *in = nullptr, *in_lo = nullptr;
+        void *out = nullptr, *out_lo = nullptr;
+        double dt = 0;
     };
     std::vector<unsigned char> blob;
     std::vector<Launch> launches;  // in enqueue order
@@ -879,6 +883,7 @@ static int batch_build(aniso_batch *b, void *const *T, const double *dt, const i
             std::vector<Line2Job> fl;
             std::vector<Line3Job> tl;
             std::vector<int> tl_nt;
+            std::vector<Launch> solo;
             for (int k = 0; k < n; ++k) {
                 if (s >= nsteps[k]) continue;
                 aniso_ctx *h = b->hs[k];
@@ -951,6 +956,18 @@ static int batch_build(aniso_batch *b, void *const *T, const double *dt, const i
                 void *outp = phase == 0 ? h->tstar : T[k];
                 const void *in_lo = h->kahan ? (phase == 0 ? h->tlo : h->tstar_lo) : nullptr;
                 void *out_lo = h->kahan ? (phase == 0 ? h->tstar_lo : h->tlo) : nullptr;
+                if (!is_x && h->long_cols()) {
+                    Launch L{6, 0, 0, 0, 0, 0};
+                    L.inst = k;
+                    L.dir = ANISO_DIR_Y;
+                    L.in = in;
+                    L.out = outp;
+                    L.in_lo = in_lo;
+                    L.out_lo = out_lo;
+                    L.dt = dt[k];
+                    solo.push_back(L);
+                    continue;
+                }
                 const double lamx = h->chi_par * dt[k] / (h->dx * h->dx);
                 const double lamy = h->chi_par * dt[k] / (h->dy * h->dy);
                 const double mu = h->chi_par * dt[k] / (h->dx * h->dy);
@@ -993,6 +1010,7 @@ static int batch_build(aniso_batch *b, void *const *T, const double *dt, const i
             add_line2(fl, phase);
             add_line(xl);
             add_col(yl);
+            launches.insert(launches.end(), solo.begin(), solo.end());
         }
     }
     // device copy of the job lists
@@ -1014,6 +1032,15 @@ static int batch_build(aniso_batch *b, void *const *T, const double *dt, const i
     int rc = ANISO_OK;
     unsigned *err = b->hs[0]->err;
     for (const Launch &L : launches) {
+        if (L.kind == 6) {
+            aniso_ctx *h = b->hs[L.inst];
+            const int saved = h->profile;  // these sweeps are not profiled inside the batch
+            h->profile = 0;
+            rc = enqueue_sweep(h, L.dir, L.in, L.out, L.dt, b->cap_stream, nullptr, L.in_lo, L.out_lo);
+            h->profile = saved;
+            if (rc) break;
+            continue;
+        }
         int pidx = -1;
         if (b->profile) {
             pidx = b->prof.take((L.kind == 0 || L.kind == 2 || L.kind == 4) ? ANISO_KERNEL_XSWEEP
