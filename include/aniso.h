@@ -71,9 +71,12 @@ enum {
     ANISO_OPT_STREAM = 5,     /* cudaStream_t cast to integer; 0 = legacy default stream */
     ANISO_OPT_GRAPH = 6,      /* 1 (default): replay aniso_step loops from a captured CUDA graph */
     ANISO_OPT_PROFILE = 7,    /* 1: time every sweep launch with CUDA events (aniso_kernel_times) */
-    ANISO_OPT_FAST_PATH = 8,  /* 1 (default): vectorised line kernel with transposed intermediate
-                                 for the x-then-y order; 2: the same with rows staged by bulk
-                                 asynchronous copies in persistent blocks; 0: general kernels only */
+    ANISO_OPT_FAST_PATH = 8,  /* kernels of the x-then-y order with a transposed intermediate:
+                                 3 (default): warp-autonomous line kernel (coalesced flux phase,
+                                 per-lane segment elimination, shuffle-only line solve);
+                                 1: block-synchronous vectorised line kernel; 2: the same with rows
+                                 staged by bulk asynchronous copies in persistent blocks;
+                                 0: general kernels only */
     ANISO_OPT_SEGMENT = 9     /* cells per thread segment of the vectorised kernel, in 16-byte
                                  chunks (0 = default 4; larger: fewer threads per line) */
 };

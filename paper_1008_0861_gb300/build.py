@@ -9,7 +9,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libaniso.so")
-SOURCES = ["aniso_api.cu", "kernels_f32.cu", "kernels_f64.cu", "util_kernels.cu", "noalloc.cu"]
+SOURCES = ["aniso_api.cu", "kernels_f32.cu", "kernels_f64.cu", "util_kernels.cu", "noalloc.cu",
+           "kernels_line4.cu"]
 HEADERS = ["aniso_internal.h", "sweep_kernels.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]

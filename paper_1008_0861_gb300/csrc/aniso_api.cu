@@ -98,7 +98,7 @@ struct aniso_ctx {
     int nx = 0, ny = 0, bc = 0;
     double dx = 0, dy = 0, chi_par = 0, chi_perp = 0;
     int prec = PREC_FP64, field_fp16 = 0, kahan = 0, limiter = LIM_VANLEER, order = ANISO_ORDER_XY;
-    int use_graph = 1, profile = 0, fast = 1, seg_chunks = 0;
+    int use_graph = 1, profile = 0, fast = 3, seg_chunks = 0;
     cudaStream_t stream = 0;
     long long step_counter = 0;
     bool field_set = false;
@@ -128,11 +128,15 @@ struct aniso_ctx {
     int vec() const { return prec == PREC_FP64 ? 2 : 4; }
     // Grid shapes the vectorised x-then-y path handles: both line lengths a
     // multiple of the 16-byte vector and short enough for transposed output.
-    // 3: staged persistent kernel (line3, option value 2), 2: line2, 0: neither.
+    // 4: warp-per-line kernel (line4, option value 3), 3: staged persistent
+    // kernel (line3, option value 2), 2: line2, 0: none of them.
     int fast_kind() const
     {
         int a, b, c;
         size_t d;
+        if (fast == 3 && line4_config(prec, nx, true, 0, &a, &b, &c, &d) &&
+            line4_config(prec, ny, true, 0, &a, &b, &c, &d))
+            return 4;
         if (fast == 2 && line3_config(prec, field_fp16, nx, true, seg_chunks, &a, &b, &c, &d) &&
             line3_config(prec, field_fp16, ny, true, seg_chunks, &a, &b, &c, &d))
             return 3;
@@ -230,7 +234,7 @@ extern "C" int aniso_set_option(aniso_t h, int key, long long v)
         h->profile = v != 0;
         break;
     case ANISO_OPT_FAST_PATH:
-        if (v < 0 || v > 2) return fail(ANISO_ERR_ARG, "bad fast-path value %lld", v);
+        if (v < 0 || v > 3) return fail(ANISO_ERR_ARG, "bad fast-path value %lld", v);
         h->fast = (int)v;
         drop_graph(h);
         break;
@@ -298,7 +302,7 @@ static bool aligned16(const void *p) { return ((uintptr_t)p & 15) == 0; }
 // One vectorised line update (line2_kernel) of `nlines` lines of n cells.
 static int enqueue_line2(aniso_ctx *h, const void *in, void *out, const void *g, const void *e, int n,
                          int nlines, int per_line, int per_cross, double lam, double mu, bool transposed,
-                         int kind, cudaStream_t s, std::vector<int> *pairs)
+                         int kind, cudaStream_t s, std::vector<int> *pairs, bool v4 = false)
 {
     Line2Args a{};
     a.jobs = nullptr;
@@ -319,8 +323,10 @@ static int enqueue_line2(aniso_ctx *h, const void *in, void *out, const void *g,
     J.transpose_out = transposed ? 1 : 0;
     int nthreads;
     size_t smem;
-    if (!line2_config(h->prec, n, transposed, &J.team, &J.lines_per_block, &nthreads, &smem, h->seg_chunks))
-        return fail(ANISO_ERR_UNSUPPORTED, "vectorised line kernel cannot take n=%d", n);
+    const bool ok = v4 ? line4_config(h->prec, n, transposed, 0, &J.team, &J.lines_per_block, &nthreads, &smem)
+                       : line2_config(h->prec, n, transposed, &J.team, &J.lines_per_block, &nthreads, &smem,
+                                      h->seg_chunks);
+    if (!ok) return fail(ANISO_ERR_UNSUPPORTED, "vectorised line kernel cannot take n=%d", n);
     J.block0 = 0;
     J.nblocks = (nlines + J.lines_per_block - 1) / J.lines_per_block;
     int pidx = -1;
@@ -330,7 +336,8 @@ static int enqueue_line2(aniso_ctx *h, const void *in, void *out, const void *g,
         if (pidx < 0) return fail(ANISO_ERR_CUDA, "event creation failed");
         CU(cudaEventRecordWithFlags(h->prof.pool[pidx].a, s, rec_flags));
     }
-    CU(launch_line2(h->prec, h->field_fp16, a, J.nblocks, nthreads, smem, s));
+    CU(v4 ? launch_line4(h->prec, h->field_fp16, a, J.nblocks, nthreads, smem, s)
+          : launch_line2(h->prec, h->field_fp16, a, J.nblocks, nthreads, smem, s));
     if (h->profile) {
         CU(cudaEventRecordWithFlags(h->prof.pool[pidx].b, s, rec_flags));
         if (pairs) pairs->push_back(pidx);
@@ -401,12 +408,19 @@ static int enqueue_fast_step(aniso_ctx *h, void *T, double dt, cudaStream_t s, s
     const double lamy = h->chi_par * dt / (h->dy * h->dy);
     const double mu = h->chi_par * dt / (h->dx * h->dy);
     const int per = h->bc == ANISO_BC_PERIODIC;
-    auto launch = h->fast_kind() == 3 ? enqueue_line3 : enqueue_line2;
-    int rc = launch(h, T, h->tstar, h->cxx, h->cxy, h->nx, h->ny, per, per, lamx, mu, true,
-                    ANISO_KERNEL_XSWEEP, s, pairs);
+    const int fk = h->fast_kind();
+    if (fk == 3) {
+        int rc = enqueue_line3(h, T, h->tstar, h->cxx, h->cxy, h->nx, h->ny, per, per, lamx, mu, true,
+                               ANISO_KERNEL_XSWEEP, s, pairs);
+        if (rc) return rc;
+        return enqueue_line3(h, h->tstar, T, h->cyyT, h->cyxT, h->ny, h->nx, per, per, lamy, mu, true,
+                             ANISO_KERNEL_YSWEEP, s, pairs);
+    }
+    int rc = enqueue_line2(h, T, h->tstar, h->cxx, h->cxy, h->nx, h->ny, per, per, lamx, mu, true,
+                           ANISO_KERNEL_XSWEEP, s, pairs, fk == 4);
     if (rc) return rc;
-    return launch(h, h->tstar, T, h->cyyT, h->cyxT, h->ny, h->nx, per, per, lamy, mu, true,
-                  ANISO_KERNEL_YSWEEP, s, pairs);
+    return enqueue_line2(h, h->tstar, T, h->cyyT, h->cyxT, h->ny, h->nx, per, per, lamy, mu, true,
+                         ANISO_KERNEL_YSWEEP, s, pairs, fk == 4);
 }
 
 // One directional update from `in` to `out` (distinct buffers) on stream s.
@@ -475,6 +489,10 @@ static int enqueue_sweep(aniso_ctx *h, int dir, const void *in, void *out, doubl
             line3_config(h->prec, h->field_fp16, h->nx, false, h->seg_chunks, &t1, &t2, &t3, &t4))
             return enqueue_line3(h, in, out, h->cxx, h->cxy, h->nx, h->ny, per, per, lamx, mu, false,
                                  ANISO_KERNEL_XSWEEP, s, pairs);
+        if (!kahan && h->fast == 3 && aligned16(in) && aligned16(out) &&
+            line4_config(h->prec, h->nx, false, 0, &t1, &t2, &t3, &t4))
+            return enqueue_line2(h, in, out, h->cxx, h->cxy, h->nx, h->ny, per, per, lamx, mu, false,
+                                 ANISO_KERNEL_XSWEEP, s, pairs, true);
         if (!kahan && h->fast && aligned16(in) && aligned16(out) &&
             line2_config(h->prec, h->nx, false, &t1, &t2, &t3, &t4, h->seg_chunks))
             return enqueue_line2(h, in, out, h->cxx, h->cxy, h->nx, h->ny, per, per, lamx, mu, false,
@@ -758,7 +776,7 @@ static int batch_build(aniso_batch *b, void *const *T, const double *dt, const i
     // Every (global step, phase) launch is one list of line jobs (x) and one
     // of column jobs (y).  Identical lists are shared.
     struct Launch {
-        int kind;  // 0 line, 1 col, 2/3 line2 (x/y), 4/5 line3 (x/y)
+        int kind;  // 0 line, 1 col, 2/3 line2 (x/y), 4/5 line3 (x/y), 7/8 line4 (x/y)
         size_t offset;
         int njobs, nblocks, nthreads;
         size_t smem;
@@ -842,6 +860,30 @@ static int batch_build(aniso_batch *b, void *const *T, const double *dt, const i
         launches.push_back(L);
     };
 
+    // line4 jobs: one launch, NW-warp blocks, per-job team and lines per block
+    auto add_line4 = [&](std::vector<Line2Job> &jobs, int kind_xy) {
+        if (jobs.empty()) return;
+        std::stable_sort(jobs.begin(), jobs.end(),
+                         [](const Line2Job &a, const Line2Job &c) { return (long long)a.n * a.nlines > (long long)c.n * c.nlines; });
+        int blocks = 0, nthreads = 0;
+        size_t smem = 0;
+        for (auto &J : jobs) {
+            int nt;
+            size_t sm;
+            line4_config(prec, J.n, true, 0, &J.team, &J.lines_per_block, &nt, &sm);
+            nthreads = std::max(nthreads, nt);
+            smem = std::max(smem, sm);
+            J.block0 = blocks;
+            J.nblocks = (J.nlines + J.lines_per_block - 1) / J.lines_per_block;
+            blocks += J.nblocks;
+        }
+        Launch L{kind_xy == 0 ? 7 : 8, blob.size(), (int)jobs.size(), blocks, nthreads, smem};
+        const unsigned char *p = reinterpret_cast<const unsigned char *>(jobs.data());
+        blob.insert(blob.end(), p, p + jobs.size() * sizeof(Line2Job));
+        while (blob.size() % 16) blob.push_back(0);
+        launches.push_back(L);
+    };
+
     // line3 jobs: one launch per block size (normally a single launch)
     auto add_line3 = [&](std::vector<Line3Job> &all, std::vector<int> &nts, int phase_xy) {
         if (all.empty()) return;
@@ -880,7 +922,7 @@ static int batch_build(aniso_batch *b, void *const *T, const double *dt, const i
         for (int phase = 0; phase < 2; ++phase) {
             std::vector<LineJob> xl;
             std::vector<ColJob> yl;
-            std::vector<Line2Job> fl;
+            std::vector<Line2Job> fl, fl4;
             std::vector<Line3Job> tl;
             std::vector<int> tl_nt;
             std::vector<Launch> solo;
@@ -946,8 +988,12 @@ static int batch_build(aniso_batch *b, void *const *T, const double *dt, const i
                     J.per_line = per;
                     J.per_cross = per;
                     J.transpose_out = 1;
-                    line2_config(prec, J.n, true, &J.team, &J.lines_per_block, &nt, &sm, h->seg_chunks);
-                    fl.push_back(J);
+                    if (h->fast_kind() == 4) {
+                        fl4.push_back(J);  // team and block shape set by add_line4
+                    } else {
+                        line2_config(prec, J.n, true, &J.team, &J.lines_per_block, &nt, &sm, h->seg_chunks);
+                        fl.push_back(J);
+                    }
                     continue;
                 }
                 const bool xf = x_first(h->order, h->step_counter + s);
@@ -1008,6 +1054,7 @@ static int batch_build(aniso_batch *b, void *const *T, const double *dt, const i
             }
             add_line3(tl, tl_nt, phase);
             add_line2(fl, phase);
+            add_line4(fl4, phase);
             add_line(xl);
             add_col(yl);
             launches.insert(launches.end(), solo.begin(), solo.end());
@@ -1043,8 +1090,9 @@ static int batch_build(aniso_batch *b, void *const *T, const double *dt, const i
         }
         int pidx = -1;
         if (b->profile) {
-            pidx = b->prof.take((L.kind == 0 || L.kind == 2 || L.kind == 4) ? ANISO_KERNEL_XSWEEP
-                                                                            : ANISO_KERNEL_YSWEEP);
+            pidx = b->prof.take((L.kind == 0 || L.kind == 2 || L.kind == 4 || L.kind == 7)
+                                    ? ANISO_KERNEL_XSWEEP
+                                    : ANISO_KERNEL_YSWEEP);
             if (pidx < 0 || cudaEventRecordWithFlags(b->prof.pool[pidx].a, b->cap_stream,
                                                      cudaEventRecordExternal) != cudaSuccess) {
                 rc = fail(ANISO_ERR_CUDA, "profiling event failed");
@@ -1052,7 +1100,14 @@ static int batch_build(aniso_batch *b, void *const *T, const double *dt, const i
             }
         }
         cudaError_t ce;
-        if (L.kind >= 4) {
+        if (L.kind == 7 || L.kind == 8) {
+            Line2Args a{};
+            a.jobs = reinterpret_cast<const Line2Job *>(static_cast<unsigned char *>(b->d_jobs) + L.offset);
+            a.njobs = L.njobs;
+            a.limiter = b->hs[0]->limiter;
+            a.err = err;
+            ce = launch_line4(prec, fp16, a, L.nblocks, L.nthreads, L.smem, b->cap_stream);
+        } else if (L.kind >= 4) {
             Line3Args a{};
             a.jobs = reinterpret_cast<const Line3Job *>(static_cast<unsigned char *>(b->d_jobs) + L.offset);
             a.njobs = L.njobs;

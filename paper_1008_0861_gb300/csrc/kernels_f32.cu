@@ -8,7 +8,7 @@ namespace aniso {
 // still fits under the per-block limit.
 template <typename K> static cudaError_t prep(K kern, size_t smem)
 {
-    if (smem <= 48 * 1024) return cudaSuccess;
+    if (smem <= 47 * 1024) return cudaSuccess;  // static shared memory counts too
     cudaFuncAttributes fa;
     cudaError_t e = cudaFuncGetAttributes(&fa, kern);
     if (e != cudaSuccess) return e;

@@ -1,0 +1,37 @@
+// Instantiations of the warp-per-line kernel (FP32 with FP32 or FP16 face
+// coefficients, FP64), one variant per limiter family.
+#include "line4_kernel.cuh"
+
+namespace aniso {
+
+template <typename K> static cudaError_t run4(K kern, const Line2Args &a, int nblocks, int nthreads, size_t smem,
+                                              cudaStream_t s)
+{
+    if (smem > 47 * 1024) {  // static shared memory counts against the 48 KB default
+        cudaFuncAttributes fa;
+        cudaError_t e = cudaFuncGetAttributes(&fa, kern);
+        if (e != cudaSuccess) return e;
+        if ((size_t)fa.maxDynamicSharedSizeBytes < smem &&
+            (e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+                cudaSuccess)
+            return e;
+    }
+    kern<<<nblocks, nthreads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_line4(int prec, int coef_fp16, const Line2Args &a, int nblocks, int nthreads, size_t smem,
+                         cudaStream_t s)
+{
+    const bool vl = a.limiter == LIM_VANLEER;
+    if (prec == PREC_FP64)
+        return vl ? run4(line4_kernel<double, double, true>, a, nblocks, nthreads, smem, s)
+                  : run4(line4_kernel<double, double, false>, a, nblocks, nthreads, smem, s);
+    if (coef_fp16)
+        return vl ? run4(line4_kernel<float, __half, true>, a, nblocks, nthreads, smem, s)
+                  : run4(line4_kernel<float, __half, false>, a, nblocks, nthreads, smem, s);
+    return vl ? run4(line4_kernel<float, float, true>, a, nblocks, nthreads, smem, s)
+              : run4(line4_kernel<float, float, false>, a, nblocks, nthreads, smem, s);
+}
+
+}  // namespace aniso

@@ -1,0 +1,383 @@
+// line4_kernel.cuh -- warp-autonomous update of contiguous lines (Eq. xup on
+// rows; Eq. yup on the column-major copy T*).
+//
+// Same linear algebra as line_sweep_kernel and line2_kernel (delta form,
+// bottom-up segment elimination, PCR of the segment-end unknowns, forward
+// recovery; see sweep_kernels.cuh).  What differs is the organisation:
+//  - a line belongs to a team of P <= 32 lanes of one warp (32/P lines per
+//    warp); no phase waits for another warp except the final transposed
+//    store, so warps of a block drift apart and overlap each other's loads
+//    and arithmetic;
+//  - face fluxes are computed with coalesced 16-byte loads (lane t takes
+//    chunks t, t+P, ..., the next round in flight during this one), the
+//    limited transverse difference as Eq. vanLeer nests it: once per cell
+//    v = L(T_after - T, T - T_before), then once per face L(v_p, v_{p+1}),
+//    so every cell's inner value serves both of its faces;
+//  - F and lam*g go to the warp's shared area, where each lane then walks
+//    its own segment bottom-up (a row is eliminated as soon as the flux of
+//    the face below it is known), storing (rho, alpha, gamma) in place; the
+//    segment-end system is solved with warp shuffles; recovery writes delta
+//    in place;
+//  - T_new = T_old + delta leaves either line-major (coalesced) or,
+//    staged in the same area, position-major (`nlines` wide) with the
+//    lines of a block packed into 16-byte stores: the x-update writes T*
+//    column-major and the y-update writes T^{n+1} back row-major.
+// Shared arrays hold whole 16-byte chunks at c ^ ((c >> log2 U) & 7) within
+// complete groups of 8 (U = chunks per segment), so that both the
+// chunk-parallel phases and the segment walks touch distinct bank groups.
+// FP32 reciprocals use the hardware approximation (rcp.approx.ftz.f32,
+// within 1 ulp); FP64 divides exactly.  Each block first asks for its input
+// rows to be brought into L2 with bulk prefetches.
+#pragma once
+#include "line2_kernel.cuh"
+
+namespace aniso {
+
+// Raw 16 bytes of T / N coefficients, converted only when used (so that a
+// prefetch does not wait on its own load).
+__device__ __forceinline__ float4 ld_raw(const float *p) { return __ldg(reinterpret_cast<const float4 *>(p)); }
+__device__ __forceinline__ double2 ld_raw(const double *p) { return __ldg(reinterpret_cast<const double2 *>(p)); }
+__device__ __forceinline__ uint2 ld_raw(const __half *p) { return __ldg(reinterpret_cast<const uint2 *>(p)); }
+__device__ __forceinline__ void unpack_raw(const float4 &v, float *o) { V16<float>::unpack(v, o); }
+__device__ __forceinline__ void unpack_raw(const double2 &v, double *o) { V16<double>::unpack(v, o); }
+__device__ __forceinline__ void unpack_raw(const uint2 &v, float *o)
+{
+    const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&v.x));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&v.y));
+    o[0] = a.x;
+    o[1] = a.y;
+    o[2] = b.x;
+    o[3] = b.y;
+}
+
+// Bulk prefetch of a byte range into L2 (no destination, no completion).
+__device__ __forceinline__ void l2_prefetch(const void *p, size_t bytes)
+{
+    if (bytes == 0 || bytes > 0xffffffffu || ((reinterpret_cast<uintptr_t>(p) | bytes) & 15)) return;
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"((unsigned)bytes) : "memory");
+}
+
+__device__ __forceinline__ float frcp_approx(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+template <typename R> struct Fast;
+template <> struct Fast<float> {
+    static __device__ __forceinline__ float rcp(float x) { return frcp_approx(x); }
+    static __device__ __forceinline__ float div(float a, float b) { return a * frcp_approx(b); }
+};
+template <> struct Fast<double> {
+    static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+    static __device__ __forceinline__ double div(double a, double b) { return a / b; }
+};
+
+// One level of the nested limiter (Eq. vanLeer: L(a,b) = 2ab/(a+b) when a, b
+// share a strict sign, else 0; minmod / MC as in lim2; the arithmetic mean
+// for LIM_ARITH, whose nesting gives the mean of the four differences).
+template <typename R> __device__ __forceinline__ R lim_level(int lim, R a, R b)
+{
+    if (lim == LIM_ARITH) return R(0.5) * (a + b);
+    return lim2<R>(lim, a, b);
+}
+// van Leer in FP32: a positive product is the strict-sign test (a + b is then
+// nonzero); one approximate reciprocal.
+__device__ __forceinline__ float vl_level(float a, float b)
+{
+    const float p = a * b;
+    const float r = (p + p) * frcp_approx(a + b);
+    return p > 0.f ? r : 0.f;
+}
+template <typename R, bool VL> __device__ __forceinline__ R level(int lim, R a, R b)
+{
+    return lim_level<R>(lim, a, b);
+}
+template <> __device__ __forceinline__ float level<float, true>(int, float a, float b) { return vl_level(a, b); }
+
+// PCR over a team of P <= 32 lanes (width-P shuffles), as pcr_warp.
+template <typename R> __device__ __forceinline__ R pcr_team(Reduced<R> q, int t, int P)
+{
+    const unsigned full = 0xffffffffu;
+    for (int h = 1; h < P; h <<= 1) {
+        const int tm = (t - h) & (P - 1), tp = (t + h) & (P - 1);
+        const R Lm = __shfl_sync(full, q.L, tm, P), Dm = __shfl_sync(full, q.D, tm, P);
+        const R Um = __shfl_sync(full, q.U, tm, P), Rm = __shfl_sync(full, q.Rr, tm, P);
+        const R Lp = __shfl_sync(full, q.L, tp, P), Dp = __shfl_sync(full, q.D, tp, P);
+        const R Up = __shfl_sync(full, q.U, tp, P), Rp = __shfl_sync(full, q.Rr, tp, P);
+        const R k1 = Fast<R>::div(q.L, Dm), k2 = Fast<R>::div(q.U, Dp);
+        q.D = q.D - k1 * Um - k2 * Lp;
+        q.Rr = q.Rr - k1 * Rm - k2 * Rp;
+        q.L = -k1 * Lm;
+        q.U = -k2 * Up;
+    }
+    return Fast<R>::div(q.Rr, q.L + q.D + q.U);
+}
+
+template <typename R, typename C, bool VL>
+__global__ void __launch_bounds__(256, 2) line4_kernel(Line2Args args)
+{
+    typedef typename V16<R>::T VT;
+    constexpr int N = V16<R>::N;
+    constexpr int LOGN = N == 4 ? 2 : 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ Line2Job J;
+    if (threadIdx.x == 0) J = args.jobs ? args.jobs[find_job(args.jobs, args.njobs)] : args.one;
+    __syncthreads();
+
+    const int lim = args.limiter;
+    const int P = J.team, n = J.n, m = n / N, nl = J.nlines, LPB = J.lines_per_block;
+    const int logP = __ffs(P) - 1;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int logL = 5 - logP;  // 32 / P lines per warp
+    const int q = lane >> logP, t = lane & (P - 1);
+    const int line0 = (blockIdx.x - J.block0) * LPB;
+    const int line = line0 + (warp << logL) + q;
+    const bool active = line < nl;
+    const int lc = active ? line : nl - 1;
+    int lu = lc + 1, ld = lc - 1;
+    if (lu >= nl) lu = J.per_cross ? 0 : nl - 1;  // mirrored ghost line
+    if (ld < 0) ld = J.per_cross ? nl - 1 : 0;
+    const R *Tin = static_cast<const R *>(J.Tin);
+    const R *rc = Tin + (size_t)lc * n, *ru = Tin + (size_t)lu * n, *rd = Tin + (size_t)ld * n;
+    const C *G = static_cast<const C *>(J.g) + (size_t)lc * n;
+    const C *E = static_cast<const C *>(J.e) + (size_t)lc * n;
+    const R lam = (R)J.lam, mu = (R)J.mu;
+    const unsigned full = 0xffffffffu;
+
+    // The block's input rows (its lines and the two neighbouring lines of T,
+    // its coefficient rows) start streaming into L2 at once, so that the
+    // warps' loads below find them there.  A hint only: issued when the
+    // range is 16-byte aligned.
+    if (threadIdx.x == 0) {
+        const int f0 = line0 > 0 ? line0 - 1 : 0, f1 = min(line0 + LPB + 1, nl), g1 = min(line0 + LPB, nl);
+        l2_prefetch(Tin + (size_t)f0 * n, (size_t)(f1 - f0) * n * sizeof(R));
+        l2_prefetch(static_cast<const C *>(J.g) + (size_t)line0 * n, (size_t)(g1 - line0) * n * sizeof(C));
+        l2_prefetch(static_cast<const C *>(J.e) + (size_t)line0 * n, (size_t)(g1 - line0) * n * sizeof(C));
+    }
+
+    // segment of lane t: chunks [c_lo, c_lo + Ut); the first rr lanes one more
+    const int U = m >> logP, rr = m & (P - 1);
+    const int Ut = U + (t < rr ? 1 : 0);
+    const int c_lo = t * U + (t < rr ? t : rr);
+    const int V = U + (rr ? 1 : 0);  // chunk rounds of the coalesced phases
+    const int WA = m << logL;        // chunks per array in one warp's area
+    const int mfull = m & ~7, logU = 31 - __clz(U);
+    VT *wbase = reinterpret_cast<VT *>(smem_raw) + (size_t)warp * 3 * WA;
+    VT *sA = wbase + q * m;           // F -> rho -> delta -> T_new
+    VT *sB = wbase + WA + q * m;      // lam*g -> alpha
+    VT *sC = wbase + 2 * WA + q * m;  // gamma
+    auto swz = [mfull, logU](int c) { return c < mfull ? c ^ ((c >> logU) & 7) : c; };
+
+    // ---- A: face fluxes and lam*g, coalesced (lane t: chunks v*P + t), last round first
+    {
+        const VT *vd = reinterpret_cast<const VT *>(rd), *vc = reinterpret_cast<const VT *>(rc),
+                 *vu = reinterpret_cast<const VT *>(ru);
+        R Tcar = R(0), vcar = R(0);  // cell 0 of chunk (v+1)P, from the team's lane 0
+        // the next round's loads are issued before this round's arithmetic
+        int cl = min(((V - 1) << logP) + t, m - 1);
+        VT xd = vd[cl], xc = vc[cl], xu = vu[cl];
+        auto xg = ld_raw(G + cl * N), xe = ld_raw(E + cl * N);
+        for (int v = V - 1; v >= 0; --v) {
+            const int c = (v << logP) + t;
+            R Td[N], Tc[N], Tu[N], Gv[N], Ev[N];
+            V16<R>::unpack(xd, Td);
+            V16<R>::unpack(xc, Tc);
+            V16<R>::unpack(xu, Tu);
+            unpack_raw(xg, Gv);
+            unpack_raw(xe, Ev);
+            const int cur = cl;
+            if (v > 0) {
+                cl = ((v - 1) << logP) + t;  // always < m
+                xd = vd[cl];
+                xc = vc[cl];
+                xu = vu[cl];
+                xg = ld_raw(G + cl * N);
+                xe = ld_raw(E + cl * N);
+            }
+            R vv[N];
+#pragma unroll
+            for (int j = 0; j < N; ++j) vv[j] = level<R, VL>(lim, Tu[j] - Tc[j], Tc[j] - Td[j]);
+            R nT = __shfl_down_sync(full, Tc[0], 1, P), nv = __shfl_down_sync(full, vv[0], 1, P);
+            if (t == P - 1) {
+                nT = Tcar;
+                nv = vcar;
+            }
+            if (cur == m - 1) {  // the cell after the line: periodic wrap or mirrored ghost
+                const int p1 = J.per_line ? 0 : n - 1;
+                nT = rc[p1];
+                nv = level<R, VL>(lim, ru[p1] - nT, nT - rd[p1]);
+            }
+            Tcar = __shfl_sync(full, Tc[0], 0, P);
+            vcar = __shfl_sync(full, vv[0], 0, P);
+            R F[N], lg[N];
+#pragma unroll
+            for (int j = 0; j < N; ++j) {
+                const R Tnx = j + 1 < N ? Tc[j + 1] : nT;
+                const R vnx = j + 1 < N ? vv[j + 1] : nv;
+                lg[j] = lam * Gv[j];
+                F[j] = lg[j] * (Tnx - Tc[j]) + mu * Ev[j] * level<R, VL>(lim, vv[j], vnx);
+            }
+            if (c < m) {
+                sA[swz(c)] = V16<R>::pack(F);
+                sB[swz(c)] = V16<R>::pack(lg);
+            }
+        }
+    }
+    __syncwarp();
+
+    // ---- B1: bottom-up elimination of lane t's segment
+    R rho1 = R(0), alp1 = R(0), gam1 = R(-1);
+    R qp = R(0), qq = R(1), qw = R(0);
+    R ae = R(0), be = R(1), ce = R(0), re = R(0);
+    {
+        auto elim = [&](R Fk, R Fkm, R lgk, R lgkm, R &ro_, R &ao_, R &go_) {
+            // row k: -lgkm d_{k-1} + (1 + lgkm + lgk) d_k - lgk d_{k+1} = Fk - Fkm
+            const R inv = Fast<R>::rcp((R(1) + lgkm + lgk) + lgk * alp1);
+            const R alp = -lgkm * inv, gam = lgk * gam1 * inv, rho = ((Fk - Fkm) + lgk * rho1) * inv;
+            ro_ = rho;
+            ao_ = alp;
+            go_ = gam;
+            qp = qp + qq * rho;
+            qw = qw - qq * gam;
+            qq = -qq * alp;
+            rho1 = rho;
+            alp1 = alp;
+            gam1 = gam;
+        };
+        R Fpend = R(0), lgpend = R(0), Flast = R(0), lglast = R(0);
+        R ro[N], ao[N], go[N];  // maps of the chunk above, waiting for its row 0
+#pragma unroll
+        for (int v = 0; v < N; ++v) ro[v] = ao[v] = go[v] = R(0);
+        for (int u = Ut - 1; u >= 0; --u) {
+            const int c = c_lo + u;
+            R F[N], lg[N], co[N], cao[N], cgo[N];
+            V16<R>::unpack(sA[swz(c)], F);
+            V16<R>::unpack(sB[swz(c)], lg);
+            if (u == Ut - 1) {
+                // row e (last cell of the segment) enters the reduced system
+                ae = -lg[N - 2];
+                ce = -lg[N - 1];
+                be = R(1) - ae - ce;
+                re = F[N - 1] - F[N - 2];
+                Flast = F[N - 1];
+                lglast = lg[N - 1];
+                co[N - 1] = cao[N - 1] = cgo[N - 1] = R(0);
+#pragma unroll
+                for (int j = N - 2; j >= 1; --j) elim(F[j], F[j - 1], lg[j], lg[j - 1], co[j], cao[j], cgo[j]);
+            } else {
+                // row 0 of the chunk above, then this chunk's rows N-1 .. 1
+                elim(Fpend, F[N - 1], lgpend, lg[N - 1], ro[0], ao[0], go[0]);
+                sA[swz(c + 1)] = V16<R>::pack(ro);
+                sB[swz(c + 1)] = V16<R>::pack(ao);
+                sC[swz(c + 1)] = V16<R>::pack(go);
+#pragma unroll
+                for (int j = N - 1; j >= 1; --j) elim(F[j], F[j - 1], lg[j], lg[j - 1], co[j], cao[j], cgo[j]);
+            }
+            Fpend = F[0];
+            lgpend = lg[0];
+#pragma unroll
+            for (int j = 1; j < N; ++j) {
+                ro[j] = co[j];
+                ao[j] = cao[j];
+                go[j] = cgo[j];
+            }
+        }
+        // row s needs the face below the segment: the previous lane's last face
+        const int tp = (t - 1) & (P - 1);
+        const R Fprev = __shfl_sync(full, Flast, tp, P), lgprev = __shfl_sync(full, lglast, tp, P);
+        elim(Fpend, Fprev, lgpend, lgprev, ro[0], ao[0], go[0]);
+        sA[swz(c_lo)] = V16<R>::pack(ro);
+        sB[swz(c_lo)] = V16<R>::pack(ao);
+        sC[swz(c_lo)] = V16<R>::pack(go);
+    }
+
+    // ---- R: reduced system of the line in the segment-end unknowns
+    R X, Xm;
+    {
+        const int tn = (t + 1) & (P - 1);
+        const R rho_n = __shfl_sync(full, rho1, tn, P), alp_n = __shfl_sync(full, alp1, tn, P),
+                gam_n = __shfl_sync(full, gam1, tn, P);
+        X = pcr_team<R>(make_reduced<R>(ae, be, ce, re, qp, qq, qw, rho_n, alp_n, gam_n), t, P);
+        Xm = __shfl_sync(full, X, (t - 1) & (P - 1), P);
+    }
+
+    // ---- B2: forward recovery of lane t's segment (delta over rho)
+    {
+        R dprev = Xm;
+        for (int u = 0; u < Ut; ++u) {
+            const int c = c_lo + u;
+            R r4[N], a4[N], g4[N], d[N];
+            V16<R>::unpack(sA[swz(c)], r4);
+            V16<R>::unpack(sB[swz(c)], a4);
+            V16<R>::unpack(sC[swz(c)], g4);
+#pragma unroll
+            for (int j = 0; j < N; ++j) {
+                d[j] = (u == Ut - 1 && j == N - 1) ? X : r4[j] - a4[j] * dprev - g4[j] * X;
+                dprev = d[j];
+            }
+            sA[swz(c)] = V16<R>::pack(d);
+        }
+    }
+    __syncwarp();
+
+    // ---- C: T_new = T_old + delta, coalesced
+    bool bad = false;
+    {
+        const VT *vc = reinterpret_cast<const VT *>(rc);
+        VT *vout = reinterpret_cast<VT *>(static_cast<R *>(J.Tout) + (size_t)lc * n);
+        for (int v = 0; v < V; ++v) {
+            const int c = (v << logP) + t;
+            if (c >= m) break;
+            R to[N], d[N];
+            V16<R>::unpack(vc[c], to);
+            V16<R>::unpack(sA[swz(c)], d);
+            R sum = R(0);
+#pragma unroll
+            for (int j = 0; j < N; ++j) {
+                to[j] += d[j];
+                sum += to[j];
+            }
+            bad |= !(fabs(sum) < R(INFINITY));  // a NaN or infinity in the chunk
+            if (!J.transpose_out) {
+                if (active) vout[c] = V16<R>::pack(to);
+            } else {
+                sA[swz(c)] = V16<R>::pack(to);
+            }
+        }
+    }
+
+    // ---- transposed store: out[p][line], N lines per 16-byte store; a
+    // thread writes all of the block's line groups of one position in turn
+    if (J.transpose_out) {
+        __syncthreads();
+        R *out = static_cast<R *>(J.Tout);
+        const int groups = LPB >> LOGN;
+        const bool vec_ok = (nl & (N - 1)) == 0;
+        for (int p = threadIdx.x; p < n; p += blockDim.x) {
+            const int sc = swz(p >> LOGN), j = p & (N - 1);
+            for (int grp = 0; grp < groups; ++grp) {
+                R o[N];
+#pragma unroll
+                for (int i = 0; i < N; ++i) {
+                    const int lb = (grp << LOGN) + i;
+                    const VT *src = reinterpret_cast<const VT *>(smem_raw) + (size_t)(lb >> logL) * 3 * WA +
+                                    (lb & ((1 << logL) - 1)) * m + sc;
+                    o[i] = reinterpret_cast<const R *>(src)[j];
+                }
+                const int l0 = line0 + (grp << LOGN);
+                R *dst = out + (size_t)p * nl + l0;
+                if (vec_ok && l0 + N <= nl) {
+                    *reinterpret_cast<VT *>(dst) = V16<R>::pack(o);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < N; ++i)
+                        if (l0 + i < nl) dst[i] = o[i];
+                }
+            }
+        }
+    }
+    if (bad && active) atomicOr(args.err, 1u);
+}
+
+}  // namespace aniso

@@ -179,6 +179,36 @@ bool line3_config(int prec, int coef_fp16, int n, bool transposed, int seg_chunk
     return false;
 }
 
+// Warp-autonomous line kernel: a team of P <= 32 lanes per line with about
+// 4 chunks (16 FP32 / 8 FP64 cells) per lane or more, at most 16 chunks a
+// lane; the warp's shared area holds 3 arrays of its lines' chunks.  Blocks
+// of `warps` warps (default 4); with a transposed output the block's line
+// count must fill whole 16-byte stores.
+bool line4_config(int prec, int n, bool transposed, int warps, int *team, int *lines_per_block,
+                  int *nthreads, size_t *smem)
+{
+    const int N = prec == PREC_FP64 ? 2 : 4;
+    if (n % N != 0 || n < 2 * N) return false;
+    if (transposed && n > MAX_LINE2_TRANSPOSED) return false;
+    const int m = n / N;
+    int P = pow2floor(m / 4 > 0 ? m / 4 : 1);
+    if (P > 32) P = 32;
+    const int U = m / P, V = U + (m % P ? 1 : 0);
+    if (V > 16) return false;
+    int NW = warps > 0 ? warps : 4;
+    if (NW > 8) NW = 8;
+    const int L = 32 / P;
+    while (transposed && (NW * L) % N != 0) NW *= 2;
+    if (NW > 8) return false;
+    const size_t sm = (size_t)NW * 3 * L * m * 16;
+    if (sm > SMEM_LIMIT - 1024) return false;
+    *team = P;
+    *lines_per_block = NW * L;
+    *nthreads = NW * 32;
+    *smem = sm;
+    return true;
+}
+
 cudaError_t launch_line3(int prec, int coef_fp16, const Line3Args &a, int nthreads, size_t smem, cudaStream_t s)
 {
     if (prec == PREC_FP64) return launch_line3_f64(a, nthreads, smem, s);

@@ -24,7 +24,7 @@ def np_dtype(P, prec):
 class GpuGrid:
     """One handle with its field set and T resident on the device."""
 
-    def __init__(self, P, inst, prec, fp16=False, limiter=0, order=0, graph=True, T0=None, fast=True):
+    def __init__(self, P, inst, prec, fp16=False, limiter=0, order=0, graph=True, T0=None, fast=None):
         import torch
         self.P, self.inst, self.prec = P, inst, prec
         self.dtype = torch_dtype(P, prec)
@@ -36,7 +36,8 @@ class GpuGrid:
         P.aniso_set_option(self.h, P.ANISO_OPT_LIMITER, limiter)
         P.aniso_set_option(self.h, P.ANISO_OPT_ORDER, order)
         P.aniso_set_option(self.h, P.ANISO_OPT_GRAPH, int(graph))
-        P.aniso_set_option(self.h, P.ANISO_OPT_FAST_PATH, int(fast))  # True/1 vectorised, 2 staged, 0 general
+        if fast is not None:  # None: the library default (3); 1 line2, 2 staged line3, 0 general
+            P.aniso_set_option(self.h, P.ANISO_OPT_FAST_PATH, int(fast))
         self.bx = torch.tensor(inst.bx, dtype=self.dtype, device="cuda")
         self.by = torch.tensor(inst.by, dtype=self.dtype, device="cuda")
         P.aniso_set_field(self.h, self.bx, self.by)
