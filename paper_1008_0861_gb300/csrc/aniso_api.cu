@@ -532,9 +532,23 @@ static int enqueue_sweep(aniso_ctx *h, int dir, const void *in, void *out, doubl
     CU(launch_transpose((int)h->esz(), in, h->tA, h->ny, h->nx, s));
     if (kahan) CU(launch_transpose((int)h->esz(), in_lo, h->tAlo, h->ny, h->nx, s));
     if ((rc = end())) return rc;
-    if ((rc = line(h->tA, h->tB, h->cyyT, h->cyxT, h->ny, h->nx, per, per, lamy, ANISO_KERNEL_YSWEEP,
-                   kahan ? h->tAlo : nullptr, kahan ? h->tBlo : nullptr)))
-        return rc;
+    {
+        // the columns are contiguous lines now: the vectorised kernels take them when they can
+        int t1, t2, t3;
+        size_t t4;
+        if (!kahan && h->fast == 3 && aligned16(h->tA) && aligned16(h->tB) &&
+            line4_config(h->prec, h->ny, false, 0, &t1, &t2, &t3, &t4))
+            rc = enqueue_line2(h, h->tA, h->tB, h->cyyT, h->cyxT, h->ny, h->nx, per, per, lamy, mu, false,
+                               ANISO_KERNEL_YSWEEP, s, pairs, true);
+        else if (!kahan && h->fast && aligned16(h->tA) && aligned16(h->tB) &&
+                 line2_config(h->prec, h->ny, false, &t1, &t2, &t3, &t4, h->seg_chunks))
+            rc = enqueue_line2(h, h->tA, h->tB, h->cyyT, h->cyxT, h->ny, h->nx, per, per, lamy, mu, false,
+                               ANISO_KERNEL_YSWEEP, s, pairs);
+        else
+            rc = line(h->tA, h->tB, h->cyyT, h->cyxT, h->ny, h->nx, per, per, lamy, ANISO_KERNEL_YSWEEP,
+                      kahan ? h->tAlo : nullptr, kahan ? h->tBlo : nullptr);
+        if (rc) return rc;
+    }
     if ((rc = begin(ANISO_KERNEL_TRANSPOSE))) return rc;
     CU(launch_transpose((int)h->esz(), h->tB, out, h->nx, h->ny, s));
     if (kahan) CU(launch_transpose((int)h->esz(), h->tBlo, out_lo, h->nx, h->ny, s));
