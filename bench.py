@@ -38,6 +38,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--instances", type=int, default=N_INST)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="skip the block-shape autotuner")
     ap.add_argument("--segment", type=int, default=0,
                     help="16-byte chunks per thread segment (0: library default)")
     ap.add_argument("--fast", type=int, default=-1,
@@ -255,6 +256,14 @@ def main():
     batch = P.aniso_batch_create(handles)
     P.aniso_set_option(handles[0], P.ANISO_OPT_PROFILE, 0)
     dts = [i.dt for i in insts]
+    tuned = None
+    if not args.no_tune and args.fast < 0 and not args.segment:
+        # block shape (lines per block, PCR depth) by measurement, outside the timed region
+        choice, tune_ms = P.aniso_batch_autotune(batch, Ts, dts, nsteps=2, reps=2)
+        if choice >= 0:
+            f, w, sc = P.aniso_autotune_candidate(choice)
+            tuned = {"choice": choice, "fast_path": f, "warps_per_block": w, "chunks_per_lane": sc,
+                     "ms_per_2_steps": tune_ms}
     nsteps = [STEPS_PER_CALL] * len(insts)
     cells = sum(i.cells for i in insts)
     cell_steps = cells * STEPS_PER_CALL
@@ -326,7 +335,8 @@ def main():
                    "steps_per_call": STEPS_PER_CALL,
                    "l2": "inputs larger than L2: %.2f GB resident per GPU (T, T*, 4 coefficient arrays)"
                          % (cells * 4 * 6 / 1e9),
-                   "parallelism": "independent instances per GPU (no collective)"},
+                   "parallelism": "independent instances per GPU (no collective)",
+                   "autotuned": tuned},
         "roofline": {"bound": "hbm", "kernel": names[dom], "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak if achieved else None,
                      "peak_source": peak_note, "traffic": ncu_traffic(names[dom]),

@@ -77,8 +77,11 @@ enum {
                                  1: block-synchronous vectorised line kernel; 2: the same with rows
                                  staged by bulk asynchronous copies in persistent blocks;
                                  0: general kernels only */
-    ANISO_OPT_SEGMENT = 9     /* cells per thread segment of the vectorised kernel, in 16-byte
-                                 chunks (0 = default 4; larger: fewer threads per line) */
+    ANISO_OPT_SEGMENT = 9,    /* cells per thread segment of the vectorised kernels, in 16-byte
+                                 chunks (0 = default 4; larger: fewer threads per line and so a
+                                 shallower PCR) */
+    ANISO_OPT_BLOCK_WARPS = 10 /* warps per block of the warp-autonomous kernel (0 = default 4;
+                                  1, 2, 4 or 8): lines per block = warps x lines per warp */
 };
 enum { ANISO_PREC_FP64 = 0, ANISO_PREC_FP32 = 1 };
 enum {
@@ -198,6 +201,27 @@ int aniso_batch_create(int n, const aniso_t *hs, aniso_batch_t *out);
 int aniso_step_batched(aniso_batch_t b, void *const *T, const double *dt, const int *nsteps);
 
 void aniso_batch_destroy(aniso_batch_t b);
+
+/* Block-shape autotuner for aniso_step_batched (the batched configuration
+ * asks for rows per block and PCR depth chosen by measurement; the paper has
+ * no counterpart).  For each candidate of a fixed table (fast-path kernel,
+ * warps per block of the warp-autonomous kernel, 16-byte chunks per lane,
+ * which sets the team size and so the PCR depth), the batch's steps run on
+ * device copies of T[k] (`nsteps` steps per call, one untimed call, then
+ * `reps` calls timed with CUDA events on the batch's stream); the fastest
+ * candidate's options are set in every handle of the batch.
+ * T[k]: device pointers as for aniso_step_batched, read only; dt[k] > 0.
+ * nsteps >= 1, reps >= 1.  Outputs (may be NULL): *choice = the candidate's
+ * index (-1 when no grid of the batch takes the fast path: nothing is
+ * changed), *best_ms = its time per call.  The handles' step counters are
+ * restored.  Allocates (and frees) one scratch buffer the size of all grids.
+ * Synchronises the batch's stream.  ANISO_ERR_OOM when the scratch buffer
+ * cannot be allocated; the handles keep their options on any error. */
+int aniso_batch_autotune(aniso_batch_t b, void *const *T, const double *dt, int nsteps, int reps,
+                         int *choice, double *best_ms);
+/* The autotuner's candidate `index`: fast-path option value, warps per block
+ * (0 = default) and chunks per lane.  ANISO_ERR_ARG when out of range. */
+int aniso_autotune_candidate(int index, int *fast, int *warps, int *seg);
 
 /* aniso_step without any device allocation.  (No counterpart in the paper: it
  * exists for callers that are not allowed to allocate GPU memory, such as code

@@ -31,6 +31,7 @@ ANISO_OPT_GRAPH = 6
 ANISO_OPT_PROFILE = 7
 ANISO_OPT_FAST_PATH = 8
 ANISO_OPT_SEGMENT = 9
+ANISO_OPT_BLOCK_WARPS = 10
 ANISO_PREC_FP64 = 0
 ANISO_PREC_FP32 = 1
 ANISO_LIM_VANLEER = 0
@@ -49,7 +50,8 @@ ANISO_KERNEL_TRANSPOSE = 2
 EXPORTED = ("aniso_create", "aniso_set_option", "aniso_set_field", "aniso_step", "aniso_sweep",
             "aniso_total", "aniso_get_state", "aniso_set_state", "aniso_sync",
             "aniso_kernel_times", "aniso_destroy", "aniso_last_error", "aniso_batch_create",
-            "aniso_step_batched", "aniso_batch_destroy", "aniso_step_noalloc")
+            "aniso_step_batched", "aniso_batch_destroy", "aniso_step_noalloc",
+            "aniso_batch_autotune", "aniso_autotune_candidate")
 
 
 class AnisoError(RuntimeError):
@@ -89,6 +91,8 @@ def load():
         "aniso_step_batched": (i, [vp, P(vp), P(d), P(i)]),
         "aniso_batch_destroy": (None, [vp]),
         "aniso_step_noalloc": (i, [i, i, d, d, d, d, i, i, vp, vp, vp, d, i, vp]),
+        "aniso_batch_autotune": (i, [vp, P(vp), P(d), i, i, P(i), P(d)]),
+        "aniso_autotune_candidate": (i, [i, P(i), P(i), P(i)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -187,6 +191,26 @@ def aniso_step_batched(batch, Ts, dts, nsteps):
     darr = (ctypes.c_double * n)(*[float(x) for x in dts])
     narr = (ctypes.c_int * n)(*[int(x) for x in nsteps])
     _check(load().aniso_step_batched(batch, Tarr, darr, narr))
+
+
+def aniso_batch_autotune(batch, Ts, dts, nsteps=2, reps=3):
+    """Time the batched fast path's block shapes on copies of Ts and keep the
+    fastest in every handle of the batch.  Returns (index, ms per call) or
+    (-1, 0.0) when no grid is on the fast path."""
+    n = len(Ts)
+    Tarr = (ctypes.c_void_p * n)(*[t.data_ptr() if hasattr(t, "data_ptr") else int(t) for t in Ts])
+    darr = (ctypes.c_double * n)(*[float(x) for x in dts])
+    ch, ms = ctypes.c_int(), ctypes.c_double()
+    _check(load().aniso_batch_autotune(batch, Tarr, darr, int(nsteps), int(reps), ctypes.byref(ch),
+                                       ctypes.byref(ms)))
+    return ch.value, ms.value
+
+
+def aniso_autotune_candidate(index):
+    """(fast-path option, warps per block, chunks per lane) of a tuner choice."""
+    f, w, s = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(load().aniso_autotune_candidate(int(index), ctypes.byref(f), ctypes.byref(w), ctypes.byref(s)))
+    return f.value, w.value, s.value
 
 
 def aniso_batch_destroy(batch):

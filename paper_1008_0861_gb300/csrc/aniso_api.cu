@@ -98,7 +98,7 @@ struct aniso_ctx {
     int nx = 0, ny = 0, bc = 0;
     double dx = 0, dy = 0, chi_par = 0, chi_perp = 0;
     int prec = PREC_FP64, field_fp16 = 0, kahan = 0, limiter = LIM_VANLEER, order = ANISO_ORDER_XY;
-    int use_graph = 1, profile = 0, fast = 3, seg_chunks = 0;
+    int use_graph = 1, profile = 0, fast = 3, seg_chunks = 0, l4_warps = 0;
     cudaStream_t stream = 0;
     long long step_counter = 0;
     bool field_set = false;
@@ -134,8 +134,8 @@ struct aniso_ctx {
     {
         int a, b, c;
         size_t d;
-        if (fast == 3 && line4_config(prec, nx, true, 0, &a, &b, &c, &d) &&
-            line4_config(prec, ny, true, 0, &a, &b, &c, &d))
+        if (fast == 3 && line4_config(prec, nx, true, l4_warps, seg_chunks, &a, &b, &c, &d) &&
+            line4_config(prec, ny, true, l4_warps, seg_chunks, &a, &b, &c, &d))
             return 4;
         if (fast == 2 && line3_config(prec, field_fp16, nx, true, seg_chunks, &a, &b, &c, &d) &&
             line3_config(prec, field_fp16, ny, true, seg_chunks, &a, &b, &c, &d))
@@ -238,6 +238,12 @@ extern "C" int aniso_set_option(aniso_t h, int key, long long v)
         h->fast = (int)v;
         drop_graph(h);
         break;
+    case ANISO_OPT_BLOCK_WARPS:
+        if (v != 0 && v != 1 && v != 2 && v != 4 && v != 8)
+            return fail(ANISO_ERR_ARG, "bad warps per block %lld (0, 1, 2, 4 or 8)", v);
+        h->l4_warps = (int)v;
+        drop_graph(h);
+        break;
     case ANISO_OPT_SEGMENT:
         if (v < 0 || v > 64) return fail(ANISO_ERR_ARG, "bad segment length %lld", v);
         h->seg_chunks = (int)v;
@@ -323,7 +329,8 @@ static int enqueue_line2(aniso_ctx *h, const void *in, void *out, const void *g,
     J.transpose_out = transposed ? 1 : 0;
     int nthreads;
     size_t smem;
-    const bool ok = v4 ? line4_config(h->prec, n, transposed, 0, &J.team, &J.lines_per_block, &nthreads, &smem)
+    const bool ok = v4 ? line4_config(h->prec, n, transposed, h->l4_warps, h->seg_chunks, &J.team,
+                                      &J.lines_per_block, &nthreads, &smem)
                        : line2_config(h->prec, n, transposed, &J.team, &J.lines_per_block, &nthreads, &smem,
                                       h->seg_chunks);
     if (!ok) return fail(ANISO_ERR_UNSUPPORTED, "vectorised line kernel cannot take n=%d", n);
@@ -490,7 +497,7 @@ static int enqueue_sweep(aniso_ctx *h, int dir, const void *in, void *out, doubl
             return enqueue_line3(h, in, out, h->cxx, h->cxy, h->nx, h->ny, per, per, lamx, mu, false,
                                  ANISO_KERNEL_XSWEEP, s, pairs);
         if (!kahan && h->fast == 3 && aligned16(in) && aligned16(out) &&
-            line4_config(h->prec, h->nx, false, 0, &t1, &t2, &t3, &t4))
+            line4_config(h->prec, h->nx, false, h->l4_warps, h->seg_chunks, &t1, &t2, &t3, &t4))
             return enqueue_line2(h, in, out, h->cxx, h->cxy, h->nx, h->ny, per, per, lamx, mu, false,
                                  ANISO_KERNEL_XSWEEP, s, pairs, true);
         if (!kahan && h->fast && aligned16(in) && aligned16(out) &&
@@ -537,7 +544,7 @@ static int enqueue_sweep(aniso_ctx *h, int dir, const void *in, void *out, doubl
         int t1, t2, t3;
         size_t t4;
         if (!kahan && h->fast == 3 && aligned16(h->tA) && aligned16(h->tB) &&
-            line4_config(h->prec, h->ny, false, 0, &t1, &t2, &t3, &t4))
+            line4_config(h->prec, h->ny, false, h->l4_warps, h->seg_chunks, &t1, &t2, &t3, &t4))
             rc = enqueue_line2(h, h->tA, h->tB, h->cyyT, h->cyxT, h->ny, h->nx, per, per, lamy, mu, false,
                                ANISO_KERNEL_YSWEEP, s, pairs, true);
         else if (!kahan && h->fast && aligned16(h->tA) && aligned16(h->tB) &&
@@ -874,18 +881,31 @@ static int batch_build(aniso_batch *b, void *const *T, const double *dt, const i
         launches.push_back(L);
     };
 
-    // line4 jobs: one launch, NW-warp blocks, per-job team and lines per block
+    // line4 jobs: one launch, NW-warp blocks, per-job team and lines per block;
+    // the block shape (warps, chunks per lane) is the first grid's, for all
+    int shape_rc = ANISO_OK;
     auto add_line4 = [&](std::vector<Line2Job> &jobs, int kind_xy) {
         if (jobs.empty()) return;
+        const int warps = b->hs[0]->l4_warps, seg = b->hs[0]->seg_chunks;
         std::stable_sort(jobs.begin(), jobs.end(),
                          [](const Line2Job &a, const Line2Job &c) { return (long long)a.n * a.nlines > (long long)c.n * c.nlines; });
-        int blocks = 0, nthreads = 0;
-        size_t smem = 0;
+        // one block size for the launch: the largest any job needs, then every
+        // job's lines per block for that many warps
+        int nthreads = 0;
         for (auto &J : jobs) {
             int nt;
             size_t sm;
-            line4_config(prec, J.n, true, 0, &J.team, &J.lines_per_block, &nt, &sm);
-            nthreads = std::max(nthreads, nt);
+            if (line4_config(prec, J.n, true, warps, seg, &J.team, &J.lines_per_block, &nt, &sm))
+                nthreads = std::max(nthreads, nt);
+        }
+        int blocks = 0;
+        size_t smem = 0;
+        for (auto &J : jobs) {
+            int nt = 0;
+            size_t sm = 0;
+            if (!line4_config(prec, J.n, true, nthreads / 32, seg, &J.team, &J.lines_per_block, &nt, &sm) ||
+                nt != nthreads)
+                shape_rc = fail(ANISO_ERR_UNSUPPORTED, "batch: line length %d does not fit the block shape", J.n);
             smem = std::max(smem, sm);
             J.block0 = blocks;
             J.nblocks = (J.nlines + J.lines_per_block - 1) / J.lines_per_block;
@@ -1074,6 +1094,7 @@ static int batch_build(aniso_batch *b, void *const *T, const double *dt, const i
             launches.insert(launches.end(), solo.begin(), solo.end());
         }
     }
+    if (shape_rc) return shape_rc;
     // device copy of the job lists
     if (b->d_jobs && b->d_jobs_bytes < blob.size()) {
         cudaFree(b->d_jobs);
@@ -1218,6 +1239,144 @@ extern "C" int aniso_step_batched(aniso_batch_t b, void *const *T, const double 
     CU(cudaGraphLaunch(b->gexec, b->stream));
     if (b->profile) b->prof.pending.insert(b->prof.pending.end(), b->g_pairs.begin(), b->g_pairs.end());
     for (int k = 0; k < n; ++k) b->hs[k]->step_counter += nsteps[k];
+    return ANISO_OK;
+}
+
+// Candidates of the block-shape autotuner: kernel option, warps per block
+// (warp-autonomous kernel), 16-byte chunks per lane / segment.
+struct Cand {
+    int fast, warps, seg;
+};
+static const Cand kTuneCands[] = {{3, 4, 4}, {3, 8, 4}, {3, 4, 8}, {3, 8, 8}, {3, 4, 2}, {3, 8, 2},
+                                  {1, 0, 4}, {1, 0, 8}};
+static const int kTuneCount = (int)(sizeof(kTuneCands) / sizeof(kTuneCands[0]));
+
+// Block-shape autotuner of the batched fast path: every candidate (kernel,
+// warps per block, chunks per lane) runs `reps` timed graph replays of
+// `nsteps` steps on device copies of the grids (after one untimed build and
+// replay); the fastest is kept in every handle of the batch.  The caller's
+// T, the handles' step counters and their profiling setting are unchanged.
+extern "C" int aniso_batch_autotune(aniso_batch_t b, void *const *T, const double *dt, int nsteps, int reps,
+                                    int *choice, double *best_ms)
+{
+    if (!b) return fail(ANISO_ERR_ARG, "aniso_batch_autotune: null batch");
+    if (!T || !dt) return fail(ANISO_ERR_ARG, "aniso_batch_autotune: null array");
+    if (nsteps < 1 || reps < 1) return fail(ANISO_ERR_ARG, "aniso_batch_autotune: nsteps and reps must be >= 1");
+    const int n = (int)b->hs.size();
+    if (choice) *choice = -1;
+    if (best_ms) *best_ms = 0.0;
+    for (int k = 0; k < n; ++k) {
+        if (!T[k]) return fail(ANISO_ERR_ARG, "aniso_batch_autotune: T[%d] is NULL", k);
+        if (!(dt[k] > 0)) return fail(ANISO_ERR_ARG, "aniso_batch_autotune: dt[%d] must be > 0", k);
+    }
+    const Cand *cands = kTuneCands;
+    const int ncand = kTuneCount;
+    // nothing to tune unless some grid is on the fast path
+    bool any = false;
+    for (aniso_ctx *h : b->hs) any = any || (!h->kahan && h->order == ANISO_ORDER_XY && h->cyyT);
+    if (!any) return ANISO_OK;
+
+    struct Saved {
+        int fast, warps, seg;
+        long long counter;
+    };
+    std::vector<Saved> saved(n);
+    for (int k = 0; k < n; ++k)
+        saved[k] = {b->hs[k]->fast, b->hs[k]->l4_warps, b->hs[k]->seg_chunks, b->hs[k]->step_counter};
+    const int saved_profile = b->profile;
+    b->profile = 0;
+
+    // device copies of the grids, 256-byte aligned
+    std::vector<size_t> off(n);
+    size_t total = 0;
+    for (int k = 0; k < n; ++k) {
+        off[k] = total;
+        total += (b->hs[k]->cells() * b->hs[k]->esz() + 255) & ~(size_t)255;
+    }
+    void *scratch = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = ANISO_OK, best = -1;
+    float best_t = 0.f;
+    std::vector<void *> Ts(n);
+    std::vector<int> ns(n, nsteps);
+    auto apply = [&](int fast, int warps, int seg) {
+        for (aniso_ctx *h : b->hs) {
+            h->fast = fast;
+            h->l4_warps = warps;
+            h->seg_chunks = seg;
+            drop_graph(h);
+        }
+        batch_drop(b);
+    };
+    if (cudaMalloc(&scratch, std::max<size_t>(total, 256)) != cudaSuccess) {
+        rc = fail(ANISO_ERR_OOM, "aniso_batch_autotune: %zu bytes of scratch", total);
+    } else if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        rc = fail(ANISO_ERR_CUDA, "aniso_batch_autotune: event creation failed");
+    } else {
+        for (int k = 0; k < n; ++k) Ts[k] = static_cast<unsigned char *>(scratch) + off[k];
+        for (int ci = 0; ci < ncand && rc == ANISO_OK; ++ci) {
+            apply(cands[ci].fast, cands[ci].warps, cands[ci].seg);
+            for (int k = 0; k < n && rc == ANISO_OK; ++k)
+                if (cudaMemcpyAsync(Ts[k], T[k], b->hs[k]->cells() * b->hs[k]->esz(), cudaMemcpyDeviceToDevice,
+                                    b->stream) != cudaSuccess)
+                    rc = fail(ANISO_ERR_CUDA, "aniso_batch_autotune: copy failed");
+            if (rc) break;
+            const int r0 = aniso_step_batched(b, Ts.data(), dt, ns.data());  // build + warm
+            if (r0 == ANISO_ERR_UNSUPPORTED) continue;                        // shape does not fit
+            if (r0) {
+                rc = r0;
+                break;
+            }
+            if (cudaEventRecord(e0, b->stream) != cudaSuccess) {
+                rc = fail(ANISO_ERR_CUDA, "aniso_batch_autotune: event record failed");
+                break;
+            }
+            for (int r = 0; r < reps && rc == ANISO_OK; ++r) rc = aniso_step_batched(b, Ts.data(), dt, ns.data());
+            if (rc) break;
+            float ms = 0.f;
+            if (cudaEventRecord(e1, b->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                rc = fail(ANISO_ERR_CUDA, "aniso_batch_autotune: timing failed");
+                break;
+            }
+            if (best < 0 || ms < best_t) {
+                best = ci;
+                best_t = ms;
+            }
+        }
+    }
+    cudaStreamSynchronize(b->stream);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (scratch) cudaFree(scratch);
+    for (int k = 0; k < n; ++k) b->hs[k]->step_counter = saved[k].counter;
+    if (best >= 0 && rc == ANISO_OK) {
+        apply(cands[best].fast, cands[best].warps, cands[best].seg);
+        if (choice) *choice = best;
+        if (best_ms) *best_ms = best_t / reps;
+    } else {
+        for (int k = 0; k < n; ++k) {
+            aniso_ctx *h = b->hs[k];
+            h->fast = saved[k].fast;
+            h->l4_warps = saved[k].warps;
+            h->seg_chunks = saved[k].seg;
+            drop_graph(h);
+        }
+        batch_drop(b);
+    }
+    b->profile = saved_profile;
+    return rc;
+}
+
+// The candidate table of aniso_batch_autotune (kernel option, warps per
+// block, chunks per lane), for callers that report the choice.
+extern "C" int aniso_autotune_candidate(int index, int *fast, int *warps, int *seg)
+{
+    if (index < 0 || index >= kTuneCount)
+        return fail(ANISO_ERR_ARG, "aniso_autotune_candidate: index %d out of range", index);
+    if (fast) *fast = kTuneCands[index].fast;
+    if (warps) *warps = kTuneCands[index].warps;
+    if (seg) *seg = kTuneCands[index].seg;
     return ANISO_OK;
 }
 

@@ -132,8 +132,10 @@ bool line2_config(int prec, int n, bool transposed, int *team, int *lines_per_bl
                   size_t *smem, int seg_chunks = 0);
 size_t line2_smem_bytes(int prec, int n, int team, int lines_per_block);
 // line4 (warp per line): returns false when the line cannot use it.
-// warps: warps per block (0 = default of 4).
-bool line4_config(int prec, int n, bool transposed, int warps, int *team, int *lines_per_block,
+// warps: warps per block (0 = default of 4); seg_chunks: target 16-byte
+// chunks per lane (0 = default of 4), which sets the team size and so the
+// PCR depth.
+bool line4_config(int prec, int n, bool transposed, int warps, int seg_chunks, int *team, int *lines_per_block,
                   int *nthreads, size_t *smem);
 cudaError_t launch_line4(int prec, int coef_fp16, const Line2Args &a, int nblocks, int nthreads,
                          size_t smem, cudaStream_t s);

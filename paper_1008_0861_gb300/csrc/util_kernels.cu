@@ -180,18 +180,18 @@ bool line3_config(int prec, int coef_fp16, int n, bool transposed, int seg_chunk
 }
 
 // Warp-autonomous line kernel: a team of P <= 32 lanes per line with about
-// 4 chunks (16 FP32 / 8 FP64 cells) per lane or more, at most 16 chunks a
-// lane; the warp's shared area holds 3 arrays of its lines' chunks.  Blocks
+// seg_chunks (default 4: 16 FP32 / 8 FP64 cells) chunks per lane or more, at
+// most 16 chunks a lane; the warp's shared area holds 3 arrays of its lines' chunks.  Blocks
 // of `warps` warps (default 4); with a transposed output the block's line
 // count must fill whole 16-byte stores.
-bool line4_config(int prec, int n, bool transposed, int warps, int *team, int *lines_per_block,
+bool line4_config(int prec, int n, bool transposed, int warps, int seg_chunks, int *team, int *lines_per_block,
                   int *nthreads, size_t *smem)
 {
     const int N = prec == PREC_FP64 ? 2 : 4;
     if (n % N != 0 || n < 2 * N) return false;
     if (transposed && n > MAX_LINE2_TRANSPOSED) return false;
-    const int m = n / N;
-    int P = pow2floor(m / 4 > 0 ? m / 4 : 1);
+    const int m = n / N, sc = seg_chunks > 0 ? seg_chunks : 4;
+    int P = pow2floor(m / sc > 0 ? m / sc : 1);
     if (P > 32) P = 32;
     const int U = m / P, V = U + (m % P ? 1 : 0);
     if (V > 16) return false;

@@ -66,3 +66,18 @@ def test_create_validates_arguments(built):
 def test_library_does_not_reference_the_oracle(built):
     data = open(built, "rb").read()
     assert b"or_xsweep" not in data and b"liboracle" not in data
+
+
+def test_autotune_candidate_table(built):
+    """The tuner's candidates are valid option values (no GPU needed)."""
+    import paper_1008_0861_gb300 as P
+    k = 0
+    while True:
+        try:
+            fast, warps, seg = P.aniso_autotune_candidate(k)
+        except P.AnisoError as e:
+            assert e.code == P.ANISO_ERR_ARG
+            break
+        assert fast in (1, 3) and warps in (0, 1, 2, 4, 8) and 1 <= seg <= 64
+        k += 1
+    assert k >= 4
