@@ -6,8 +6,9 @@ the GPU library (``paper_1008_0861_gb300``) and imports nothing from it.
 
 The arithmetic lives in ``aniso_oracle.c`` (plain C, FP64, written from
 Section 2 of Sharma & Hammett, arXiv:1008.0861: Eqs. xup and yup, the limited
-face differences after them, Eq. vanLeer and Eq. op_2step).  This module only
-marshals numpy arrays to it, and does the one encoding step the paper leaves
+face differences after them, Eq. vanLeer and Eq. op_2step).  This module
+marshals numpy arrays to it, composes those sweeps into the 4-step scheme of
+Eq. 4step (step4), and does the one encoding step the paper leaves
 to the implementation: rounding stored face coefficients to FP16 with numpy
 (round-to-nearest-even) when a test asks for the FP16-field variant.
 
@@ -193,6 +194,30 @@ def step(T, co: Coeffs, bc, dt, dx, dy, chi_par, nsteps=1, step0=0,
                          lamx, lamy, mu, int(limiter), int(order), int(step0), int(nsteps), _p(T))
     if rc:
         raise MemoryError("oracle scratch allocation failed")
+    return T
+
+
+def step4(T, co: Coeffs, bc, dt, dx, dy, chi_par, nsteps=1, step0=0,
+          order=ORDER_XY, limiter=LIM_VANLEER):
+    """nsteps steps of the 4-step scheme, Eq. 4step:
+        T^{n+1} = (1 + dt Dyy/2)^-2 (1 - dt Dyx) (1 + dt Dxx/2)^-2 (1 - dt Dxy) T^n.
+    Each direction is the update of Eq. xup / Eq. yup with its implicit (normal)
+    part taken over dt/2 and the explicit transverse part over dt, followed by a
+    fully implicit dt/2 update of the same direction (no transverse term).
+    `order` as in step(): the reversed order swaps the x and y parts."""
+    T = _f64(T).copy()
+    lamx, lamy, mu = lambdas(dt, dx, dy, chi_par)
+
+    def xpart(U):
+        return xsweep(xsweep(U, co, bc, 0.5 * lamx, mu, limiter), co, bc, 0.5 * lamx, 0.0, limiter)
+
+    def ypart(U):
+        return ysweep(ysweep(U, co, bc, 0.5 * lamy, mu, limiter), co, bc, 0.5 * lamy, 0.0, limiter)
+
+    for s in range(nsteps):
+        k = step0 + s
+        x_first = order == ORDER_XY or (order == ORDER_ALTERNATE and k % 2 == 0)
+        T = ypart(xpart(T)) if x_first else xpart(ypart(T))
     return T
 
 

@@ -118,6 +118,37 @@ def test_fourier_mode_amplification_eq_amp(nx, ny, mx, my, alpha, fac):
     np.testing.assert_allclose(Ts, r1 * T0, atol=1e-13)
 
 
+@pytest.mark.parametrize("nx,ny,mx,my,alpha,fac", [
+    (16, 12, 1, 2, 0.3, 10.0), (16, 16, 3, -5, 2.1, 100.0), (10, 14, 4, 1, -0.7, 1000.0),
+    (12, 9, 5, 3, 1.2, 3.0)])
+def test_four_step_fourier_mode_amplification(nx, ny, mx, my, alpha, fac):
+    """Eq. 4step on a Fourier mode (constant b, periodic, arithmetic-mean
+    transverse average): each direction multiplies by the explicit transverse
+    factor of Eqs. amp1/amp2 and divides by its implicit half-step factor
+    twice, r = num^2 / ((1 + 2 lamx bx^2 sin^2(tx/2))^2 (1 + 2 lamy by^2 sin^2(ty/2))^2)."""
+    chi = 0.7
+    dx, dy = 1.0 / nx, 1.0 / ny
+    dt = fac * W.cfl_dt(dx, dy, chi)
+    bxv, byv = math.cos(alpha), math.sin(alpha)
+    co = O.face_coeffs(np.full((ny, nx), bxv), np.full((ny, nx), byv), O.BC_PERIODIC)
+    x = (np.arange(nx) + 0.5) * dx
+    y = (np.arange(ny) + 0.5) * dy
+    kx, ky = 2 * math.pi * mx, 2 * math.pi * my
+    T0 = np.cos(kx * x[None, :] + ky * y[:, None] - 0.9)
+    lamx, lamy, mu = O.lambdas(dt, dx, dy, chi)
+    tx, ty = kx * dx, ky * dy
+    num = 1.0 - mu * bxv * byv * math.sin(tx) * math.sin(ty)
+    rx = num / (1.0 + 2.0 * lamx * bxv ** 2 * math.sin(tx / 2) ** 2) ** 2
+    ry = num / (1.0 + 2.0 * lamy * byv ** 2 * math.sin(ty / 2) ** 2) ** 2
+    for order in (O.ORDER_XY, O.ORDER_YX):
+        T1 = O.step4(T0, co, O.BC_PERIODIC, dt, dx, dy, chi, order=order, limiter=O.LIM_ARITH)
+        np.testing.assert_allclose(T1, rx * ry * T0, atol=1e-13)
+    # and it differs from the 2-step factor unless the implicit parts vanish
+    r2 = num / (1.0 + 4.0 * lamx * bxv ** 2 * math.sin(tx / 2) ** 2) * \
+        num / (1.0 + 4.0 * lamy * byv ** 2 * math.sin(ty / 2) ** 2)
+    assert abs(rx * ry - r2) > 1e-6
+
+
 @pytest.mark.parametrize("alpha", [0.25, 1.0, 2.5, -2.0])
 @pytest.mark.parametrize("order", [O.ORDER_XY, O.ORDER_YX])
 def test_one_dimensional_data_reduces_to_backward_euler(alpha, order):
@@ -175,9 +206,12 @@ def _cell(i, j, nx, ny, periodic):
     return min(max(j, 0), ny - 1) * nx + min(max(i, 0), nx - 1)   # mirrored ghost
 
 
-def _dense_step_matrix(nx, ny, bc, co, lamx, lamy, mu, x_first=True):
+def _dense_step_matrix(nx, ny, bc, co, lamx, lamy, mu, x_first=True, four_step=False):
     """Eq. op_2step assembled densely for the arithmetic-mean transverse
-    average: (I+dt Dyy)^-1 (I-dt Dyx) (I+dt Dxx)^-1 (I-dt Dxy)."""
+    average: (I+dt Dyy)^-1 (I-dt Dyx) (I+dt Dxx)^-1 (I-dt Dxy); with
+    four_step, Eq. 4step: (I+dt Dyy/2)^-2 (I-dt Dyx) (I+dt Dxx/2)^-2 (I-dt Dxy)."""
+    if four_step:
+        lamx, lamy = 0.5 * lamx, 0.5 * lamy
     per = bc == O.BC_PERIODIC
     N = nx * ny
     Ax, Ex, Ay, Ey = (np.zeros((N, N)) for _ in range(4))
@@ -215,6 +249,9 @@ def _dense_step_matrix(nx, ny, bc, co, lamx, lamy, mu, x_first=True):
                     Ey[k, _cell(ci, cj, nx, ny, per)] += sgn_face * mu * e * 0.25 * s
     Mx = np.linalg.solve(Ax, Ex)
     My = np.linalg.solve(Ay, Ey)
+    if four_step:
+        Mx = np.linalg.solve(Ax, Mx)
+        My = np.linalg.solve(Ay, My)
     return My @ Mx if x_first else Mx @ My
 
 
@@ -232,6 +269,33 @@ def test_step_matches_dense_operator(nx, ny, bc):
         M = _dense_step_matrix(nx, ny, bc, co, lamx, lamy, mu, x_first=xf)
         T1 = O.step(T0, co, bc, dt, dx, dy, chi, order=order, limiter=O.LIM_ARITH)
         np.testing.assert_allclose(T1.ravel(), M @ T0.ravel(), atol=1e-12)
+
+
+@pytest.mark.parametrize("nx,ny,bc", [(6, 5, O.BC_PERIODIC), (5, 7, O.BC_ZEROFLUX), (4, 6, O.BC_ZEROFLUX)])
+def test_four_step_matches_dense_operator(nx, ny, bc):
+    """Eq. 4step assembled densely (random b, chi_perp > 0, both boundary
+    conditions) against step4, both orders."""
+    rng = np.random.default_rng(nx * 7 + ny + 3 * bc)
+    ang = rng.uniform(0, 2 * math.pi, (ny, nx))
+    co = O.face_coeffs(np.cos(ang), np.sin(ang), bc, chi_par=1.0, chi_perp=0.05)
+    dx, dy, chi = 1.1 / nx, 1.0 / ny, 0.3
+    dt = 40 * W.cfl_dt(dx, dy, chi)
+    lamx, lamy, mu = O.lambdas(dt, dx, dy, chi)
+    T0 = rng.normal(size=(ny, nx))
+    for order, xf in ((O.ORDER_XY, True), (O.ORDER_YX, False)):
+        M = _dense_step_matrix(nx, ny, bc, co, lamx, lamy, mu, x_first=xf, four_step=True)
+        T1 = O.step4(T0, co, bc, dt, dx, dy, chi, order=order, limiter=O.LIM_ARITH)
+        np.testing.assert_allclose(T1.ravel(), M @ T0.ravel(), atol=1e-12)
+
+
+@pytest.mark.parametrize("bc", [O.BC_PERIODIC, O.BC_ZEROFLUX])
+def test_four_step_conserves(bc):
+    inst = W.random_instance(24, 20, seed=5, dt_factor=500.0) if bc == O.BC_PERIODIC else \
+        W.ring_instance(24, ny=20, dt_factor=500.0)
+    co = O.face_coeffs(inst.bx, inst.by, bc, inst.chi_par)
+    T1 = O.step4(inst.T0, co, bc, inst.dt, inst.dx, inst.dy, inst.chi_par, nsteps=5)
+    s0, s1 = np.sum(inst.T0), np.sum(T1)
+    assert abs(s1 - s0) <= 1e-12 * abs(s0)
 
 
 def test_alternating_order_follows_step_counter():
