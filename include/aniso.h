@@ -80,10 +80,18 @@ enum {
     ANISO_OPT_SEGMENT = 9,    /* cells per thread segment of the vectorised kernels, in 16-byte
                                  chunks (0 = default 4; larger: fewer threads per line and so a
                                  shallower PCR) */
-    ANISO_OPT_BLOCK_WARPS = 10 /* warps per block of the warp-autonomous kernel (0 = default 4;
-                                  1, 2, 4 or 8): lines per block = warps x lines per warp */
+    ANISO_OPT_BLOCK_WARPS = 10, /* warps per block of the warp-autonomous kernel (0 = default 4;
+                                   1, 2, 4 or 8): lines per block = warps x lines per warp */
+    ANISO_OPT_SCHEME = 11      /* ANISO_SCHEME_2STEP (default) or ANISO_SCHEME_4STEP; the 4-step
+                                  scheme runs on single handles (aniso_step, not batches) with
+                                  the plain state; ANISO_ERR_UNSUPPORTED with the compensated one */
 };
 enum { ANISO_PREC_FP64 = 0, ANISO_PREC_FP32 = 1 };
+enum {
+    ANISO_SCHEME_2STEP = 0, /* Eq. op_2step: one semi-implicit update per direction */
+    ANISO_SCHEME_4STEP = 1  /* Eq. 4step: per direction, the semi-implicit update with its implicit
+                               part over dt/2, then a fully implicit dt/2 update (Section 2.1) */
+};
 enum {
     ANISO_LIM_VANLEER = 0, /* Eq. vanLeer (default) */
     ANISO_LIM_ARITH = 1,   /* arithmetic mean of the four differences: the linear

@@ -32,6 +32,9 @@ ANISO_OPT_PROFILE = 7
 ANISO_OPT_FAST_PATH = 8
 ANISO_OPT_SEGMENT = 9
 ANISO_OPT_BLOCK_WARPS = 10
+ANISO_OPT_SCHEME = 11
+ANISO_SCHEME_2STEP = 0
+ANISO_SCHEME_4STEP = 1
 ANISO_PREC_FP64 = 0
 ANISO_PREC_FP32 = 1
 ANISO_LIM_VANLEER = 0

@@ -98,7 +98,8 @@ struct aniso_ctx {
     int nx = 0, ny = 0, bc = 0;
     double dx = 0, dy = 0, chi_par = 0, chi_perp = 0;
     int prec = PREC_FP64, field_fp16 = 0, kahan = 0, limiter = LIM_VANLEER, order = ANISO_ORDER_XY;
-    int use_graph = 1, profile = 0, fast = 3, seg_chunks = 0, l4_warps = 0;
+    int use_graph = 1, profile = 0, fast = 3, seg_chunks = 0, l4_warps = 0, scheme = 0;
+    void *t4 = nullptr;  // intermediate of the 4-step scheme
     cudaStream_t stream = 0;
     long long step_counter = 0;
     bool field_set = false;
@@ -151,8 +152,8 @@ struct aniso_ctx {
 
 static void free_buffers(aniso_ctx *h)
 {
-    void **bufs[] = {&h->cxx, &h->cxy, &h->cyy,  &h->cyx, &h->cyyT,     &h->cyxT, &h->tstar,
-                     &h->tA,  &h->tB,  &h->tlo, &h->tstar_lo, &h->tAlo, &h->tBlo};
+    void **bufs[] = {&h->cxx, &h->cxy, &h->cyy,      &h->cyx,  &h->cyyT, &h->cyxT, &h->tstar,
+                     &h->tA,  &h->tB,  &h->tlo, &h->tstar_lo, &h->tAlo, &h->tBlo, &h->t4};
     for (void **b : bufs) {
         if (*b) cudaFree(*b);
         *b = nullptr;
@@ -213,7 +214,17 @@ extern "C" int aniso_set_option(aniso_t h, int key, long long v)
     case ANISO_OPT_KAHAN:
         if (h->field_set && (v != 0) != (h->kahan != 0))
             return fail(ANISO_ERR_STATE, "compensated state is fixed once the field is set");
+        if (v && h->scheme == ANISO_SCHEME_4STEP)
+            return fail(ANISO_ERR_UNSUPPORTED, "the compensated state runs the 2-step scheme only");
         h->kahan = v != 0;
+        break;
+    case ANISO_OPT_SCHEME:
+        if (v != ANISO_SCHEME_2STEP && v != ANISO_SCHEME_4STEP) return fail(ANISO_ERR_ARG, "bad scheme %lld", v);
+        if (v == ANISO_SCHEME_4STEP && h->kahan)
+            return fail(ANISO_ERR_UNSUPPORTED, "the compensated state runs the 2-step scheme only");
+        if (v == ANISO_SCHEME_4STEP && !h->t4) CU(cudaMalloc(&h->t4, h->cells() * 8));  // either precision
+        h->scheme = (int)v;
+        drop_graph(h);
         break;
     case ANISO_OPT_LIMITER:
         if (v < 0 || v > 3) return fail(ANISO_ERR_ARG, "bad limiter %lld", v);
@@ -431,13 +442,16 @@ static int enqueue_fast_step(aniso_ctx *h, void *T, double dt, cudaStream_t s, s
 }
 
 // One directional update from `in` to `out` (distinct buffers) on stream s.
+// ls, ms scale the implicit (normal) and explicit (transverse) parts: the
+// half-step updates of Eq. 4step use (1/2, 1) and (1/2, 0).
 static int enqueue_sweep(aniso_ctx *h, int dir, const void *in, void *out, double dt, cudaStream_t s,
-                         std::vector<int> *pairs, const void *in_lo = nullptr, void *out_lo = nullptr)
+                         std::vector<int> *pairs, const void *in_lo = nullptr, void *out_lo = nullptr,
+                         double ls = 1.0, double ms = 1.0)
 {
     const bool kahan = in_lo != nullptr;
-    const double lamx = h->chi_par * dt / (h->dx * h->dx);
-    const double lamy = h->chi_par * dt / (h->dy * h->dy);
-    const double mu = h->chi_par * dt / (h->dx * h->dy);
+    const double lamx = ls * h->chi_par * dt / (h->dx * h->dx);
+    const double lamy = ls * h->chi_par * dt / (h->dy * h->dy);
+    const double mu = ms * h->chi_par * dt / (h->dx * h->dy);
     const int per = h->bc == ANISO_BC_PERIODIC;
     int pidx = -1;
     // inside a stream capture only an "external" record becomes an event
@@ -572,6 +586,20 @@ static bool x_first(int order, long long counter)
 static int enqueue_steps(aniso_ctx *h, void *T, double dt, int nsteps, long long counter0,
                          cudaStream_t s, std::vector<int> *pairs)
 {
+    if (h->scheme == ANISO_SCHEME_4STEP) {
+        // Eq. 4step: per direction, the semi-implicit update with its implicit
+        // part over dt/2, then a fully implicit dt/2 update (no transverse term)
+        for (int k = 0; k < nsteps; ++k) {
+            const bool xf = x_first(h->order, counter0 + k);
+            const int d1 = xf ? ANISO_DIR_X : ANISO_DIR_Y, d2 = xf ? ANISO_DIR_Y : ANISO_DIR_X;
+            int rc;
+            if ((rc = enqueue_sweep(h, d1, T, h->t4, dt, s, pairs, nullptr, nullptr, 0.5, 1.0))) return rc;
+            if ((rc = enqueue_sweep(h, d1, h->t4, h->tstar, dt, s, pairs, nullptr, nullptr, 0.5, 0.0))) return rc;
+            if ((rc = enqueue_sweep(h, d2, h->tstar, h->t4, dt, s, pairs, nullptr, nullptr, 0.5, 1.0))) return rc;
+            if ((rc = enqueue_sweep(h, d2, h->t4, T, dt, s, pairs, nullptr, nullptr, 0.5, 0.0))) return rc;
+        }
+        return ANISO_OK;
+    }
     if (use_fast(h, T)) {
         for (int k = 0; k < nsteps; ++k) {
             int rc = enqueue_fast_step(h, T, dt, s, pairs);
@@ -767,6 +795,8 @@ extern "C" int aniso_batch_create(int n, const aniso_t *hs, aniso_batch_t *out)
         if (h->prec != hs[0]->prec || h->field_fp16 != hs[0]->field_fp16 || h->limiter != hs[0]->limiter ||
             h->kahan != hs[0]->kahan)
             return fail(ANISO_ERR_ARG, "aniso_batch_create: handle %d differs in precision/field/limiter/state", k);
+        if (h->scheme != ANISO_SCHEME_2STEP)
+            return fail(ANISO_ERR_UNSUPPORTED, "aniso_batch_create: handle %d runs the 4-step scheme", k);
     }
     aniso_batch *b = new aniso_batch;
     b->hs.assign(hs, hs + n);
