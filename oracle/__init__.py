@@ -8,7 +8,8 @@ The arithmetic lives in ``aniso_oracle.c`` (plain C, FP64, written from
 Section 2 of Sharma & Hammett, arXiv:1008.0861: Eqs. xup and yup, the limited
 face differences after them, Eq. vanLeer and Eq. op_2step).  This module
 marshals numpy arrays to it, composes those sweeps into the 4-step scheme of
-Eq. 4step (step4), and does the one encoding step the paper leaves
+Eq. 4step (step4), runs the explicit limited scheme built from the same face
+fluxes (explicit_step), and does the one encoding step the paper leaves
 to the implementation: rounding stored face coefficients to FP16 with numpy
 (round-to-nearest-even) when a test asks for the FP16-field variant.
 
@@ -65,6 +66,8 @@ def _load():
         lib.or_ysweep.argtypes = [i, i, i, _D, _D, d, d, i, _D, _D]
         lib.or_step.restype = i
         lib.or_step.argtypes = [i, i, i, _D, _D, _D, _D, d, d, d, i, i, ll, i, _D]
+        lib.or_explicit_step.restype = i
+        lib.or_explicit_step.argtypes = [i, i, i, _D, _D, _D, _D, d, d, d, i, i, _D]
         lib.or_totals.restype = None
         lib.or_totals.argtypes = [sz, _D, _D, _D, _D]
         lib.or_num_threads.restype = i
@@ -218,6 +221,20 @@ def step4(T, co: Coeffs, bc, dt, dx, dy, chi_par, nsteps=1, step0=0,
         k = step0 + s
         x_first = order == ORDER_XY or (order == ORDER_ALTERNATE and k % 2 == 0)
         T = ypart(xpart(T)) if x_first else xpart(ypart(T))
+    return T
+
+
+def explicit_step(T, co: Coeffs, bc, dt, dx, dy, chi_par, nsteps=1, limiter=LIM_VANLEER):
+    """nsteps steps of the explicit limited scheme: the unsplit explicit form
+    of the face fluxes of Eqs. xup and yup, every flux from T^n (the explicit
+    method the paper compares against)."""
+    T = _f64(T).copy()
+    ny, nx = T.shape
+    lamx, lamy, mu = lambdas(dt, dx, dy, chi_par)
+    rc = _load().or_explicit_step(nx, ny, int(bc), _p(co.cxx), _p(co.cxy), _p(co.cyy), _p(co.cyx),
+                                  lamx, lamy, mu, int(limiter), int(nsteps), _p(T))
+    if rc:
+        raise MemoryError("oracle scratch allocation failed")
     return T
 
 

@@ -357,6 +357,70 @@ int or_step(int nx, int ny, int bc, const double *cxx, const double *cxy, const 
     return 0;
 }
 
+/* ------------------------------------------------ explicit limited step */
+
+/* Flux through x face (i+1/2, j) of the explicit step: the normal part of
+ * Eq. xup and its limited transverse part, both from T.  Zero through a
+ * zero-flux boundary face; rows outside the grid are mirrored (zero-flux) or
+ * wrapped (periodic), as in the sweeps. */
+static double ex_fx(int nx, int ny, int per, const double *cxx, const double *cxy, double lamx,
+                    double mu, int lim, const double *T, int i, int j)
+{
+    if (!per && i == nx - 1) return 0.0;
+    int ip = (i + 1) % nx;
+    int jm = j - 1, jp = j + 1;
+    if (jm < 0) jm = per ? ny - 1 : 0;
+    if (jp >= ny) jp = per ? 0 : ny - 1;
+    const double *rm = T + (size_t)jm * nx, *r0 = T + (size_t)j * nx, *rp = T + (size_t)jp * nx;
+    double dT = or_limit4(lim, rp[ip] - r0[ip], r0[ip] - rm[ip], rp[i] - r0[i], r0[i] - rm[i]);
+    return lamx * cxx[(size_t)j * nx + i] * (r0[ip] - r0[i]) + mu * cxy[(size_t)j * nx + i] * dT;
+}
+
+/* Flux through y face (i, j+1/2) (second DeltaT-bar equation after Eq. yup). */
+static double ex_fy(int nx, int ny, int per, const double *cyy, const double *cyx, double lamy,
+                    double mu, int lim, const double *T, int i, int j)
+{
+    if (!per && j == ny - 1) return 0.0;
+    int jp = (j + 1) % ny;
+    int im = i - 1, ip = i + 1;
+    if (im < 0) im = per ? nx - 1 : 0;
+    if (ip >= nx) ip = per ? 0 : nx - 1;
+    const double *r0 = T + (size_t)j * nx, *r1 = T + (size_t)jp * nx;
+    double dT = or_limit4(lim, r1[ip] - r1[i], r1[i] - r1[im], r0[ip] - r0[i], r0[i] - r0[im]);
+    return lamy * cyy[(size_t)j * nx + i] * (r1[i] - r0[i]) + mu * cyx[(size_t)j * nx + i] * dT;
+}
+
+/* nsteps steps of the explicit limited scheme, in place on T: the unsplit
+ * explicit form of the face fluxes of Eqs. xup and yup, every flux taken at
+ * T^n (the explicit method the paper compares against, Sections 1 and 3.1):
+ *   T^{n+1}_ij = T^n_ij + Fx(i+1/2,j) - Fx(i-1/2,j) + Fy(i,j+1/2) - Fy(i,j-1/2).
+ * Returns 0, or -1 if scratch could not be allocated. */
+int or_explicit_step(int nx, int ny, int bc, const double *cxx, const double *cxy, const double *cyy,
+                     const double *cyx, double lamx, double lamy, double mu, int lim, int nsteps,
+                     double *T)
+{
+    int per = bc == OR_BC_PERIODIC;
+    double *Tn = (double *)malloc(sizeof(double) * (size_t)nx * ny);
+    if (!Tn) return -1;
+    for (int n = 0; n < nsteps; ++n) {
+#pragma omp parallel for schedule(static)
+        for (int j = 0; j < ny; ++j) {
+            for (int i = 0; i < nx; ++i) {
+                double fxp = ex_fx(nx, ny, per, cxx, cxy, lamx, mu, lim, T, i, j);
+                double fxm = i > 0 ? ex_fx(nx, ny, per, cxx, cxy, lamx, mu, lim, T, i - 1, j)
+                                   : (per ? ex_fx(nx, ny, per, cxx, cxy, lamx, mu, lim, T, nx - 1, j) : 0.0);
+                double fyp = ex_fy(nx, ny, per, cyy, cyx, lamy, mu, lim, T, i, j);
+                double fym = j > 0 ? ex_fy(nx, ny, per, cyy, cyx, lamy, mu, lim, T, i, j - 1)
+                                   : (per ? ex_fy(nx, ny, per, cyy, cyx, lamy, mu, lim, T, i, ny - 1) : 0.0);
+                Tn[(size_t)j * nx + i] = T[(size_t)j * nx + i] + (fxp - fxm) + (fyp - fym);
+            }
+        }
+        memcpy(T, Tn, sizeof(double) * (size_t)nx * ny);
+    }
+    free(Tn);
+    return 0;
+}
+
 /* FP64 sum (plain left-to-right), minimum and maximum of n values. */
 void or_totals(size_t n, const double *T, double *sum, double *tmin, double *tmax)
 {

@@ -408,3 +408,75 @@ def test_ring_nonmonotonicity_matches_paper():
         elif check == "positive":
             assert tmin > 0.0
     assert rels[0] < rels[1] < rels[2]
+
+
+# ------------------------------------------------- explicit limited step
+
+@pytest.mark.parametrize("nx,ny,mx,my,alpha,fac", [
+    (16, 12, 1, 2, 0.3, 0.4), (16, 16, 3, -5, 2.1, 0.25), (10, 14, 4, 1, -0.7, 0.5), (12, 9, 5, 3, 1.2, 5.0)])
+def test_explicit_step_fourier_mode(nx, ny, mx, my, alpha, fac):
+    """Constant b, periodic, arithmetic-mean transverse average: one explicit
+    step multiplies cos(k.x) by 1 - dt (Dxx + Dyy + Dxy + Dyx), whose symbols
+    are those of Eqs. amp1/amp2: 4 lamx bx^2 sin^2(tx/2), 4 lamy by^2
+    sin^2(ty/2) and mu bx by sin(tx) sin(ty) for each transverse operator."""
+    chi = 0.7
+    dx, dy = 1.0 / nx, 1.0 / ny
+    dt = fac * W.cfl_dt(dx, dy, chi)
+    bxv, byv = math.cos(alpha), math.sin(alpha)
+    co = O.face_coeffs(np.full((ny, nx), bxv), np.full((ny, nx), byv), O.BC_PERIODIC)
+    x = (np.arange(nx) + 0.5) * dx
+    y = (np.arange(ny) + 0.5) * dy
+    kx, ky = 2 * math.pi * mx, 2 * math.pi * my
+    T0 = np.cos(kx * x[None, :] + ky * y[:, None] + 0.2)
+    lamx, lamy, mu = O.lambdas(dt, dx, dy, chi)
+    tx, ty = kx * dx, ky * dy
+    r = (1.0 - 4 * lamx * bxv ** 2 * math.sin(tx / 2) ** 2 - 4 * lamy * byv ** 2 * math.sin(ty / 2) ** 2
+         - 2 * mu * bxv * byv * math.sin(tx) * math.sin(ty))
+    T1 = O.explicit_step(T0, co, O.BC_PERIODIC, dt, dx, dy, chi, limiter=O.LIM_ARITH)
+    np.testing.assert_allclose(T1, r * T0, atol=1e-13)
+
+
+def test_explicit_step_one_dimensional_is_ftcs():
+    """b = x, T depending on x only: the textbook FTCS update
+    T_i + lam (T_{i+1} - 2 T_i + T_{i-1}), any limiter."""
+    nx, ny = 24, 6
+    rng = np.random.default_rng(4)
+    Tx = rng.normal(size=nx)
+    T0 = np.tile(Tx, (ny, 1))
+    co = O.face_coeffs(np.ones((ny, nx)), np.zeros((ny, nx)), O.BC_PERIODIC)
+    dx, dy, chi, dt = 1.0 / nx, 1.0 / ny, 1.0, 0.3 / nx ** 2
+    lam = chi * dt / dx ** 2
+    ref = Tx + lam * (np.roll(Tx, -1) - 2 * Tx + np.roll(Tx, 1))
+    for lim in (O.LIM_VANLEER, O.LIM_ARITH, O.LIM_MC):
+        T1 = O.explicit_step(T0, co, O.BC_PERIODIC, dt, dx, dy, chi, limiter=lim)
+        np.testing.assert_allclose(T1, np.tile(ref, (ny, 1)), atol=1e-14)
+
+
+@pytest.mark.parametrize("bc", [O.BC_PERIODIC, O.BC_ZEROFLUX])
+def test_explicit_step_conserves(bc):
+    inst = W.random_instance(20, 16, seed=2, dt_factor=0.4) if bc == O.BC_PERIODIC else \
+        W.ring_instance(20, ny=16, dt_factor=0.4)
+    co = O.face_coeffs(inst.bx, inst.by, bc, inst.chi_par)
+    T1 = O.explicit_step(inst.T0, co, bc, inst.dt, inst.dx, inst.dy, inst.chi_par, nsteps=7)
+    assert abs(np.sum(T1) - np.sum(inst.T0)) <= 1e-12 * abs(np.sum(inst.T0))
+
+
+def test_explicit_ring_minimum_matches_paper():
+    """Section 3.1, caption of the minimum-temperature figure: the explicit
+    method without limiters at ncfl = 1 reaches min T = -0.41 on the 512^2 ring
+    (10 / 0.1); with the van Leer limiter there are no oscillations at a
+    CFL-stable step.  Stored in tests/golden with the citation."""
+    g = json.load(open(os.path.join(GOLDEN, "ring_explicit_paper_values.json")))
+    n, chi = g["n"], g["chi_par"]
+    inst = W.ring_instance(n, t_hot=g["T_hot"], t_cold=g["T_cold"], chi_par=chi, dt_factor=1.0)
+    dt = g["ncfl"] * inst.dx ** 2 / (4 * chi)   # Eq. ncfl
+    co = O.face_coeffs(inst.bx, inst.by, O.BC_ZEROFLUX, chi)
+    lows = {}
+    for lim in (O.LIM_ARITH, O.LIM_VANLEER):
+        T, lo = inst.T0.copy(), np.inf
+        for _ in range(g["steps_checked"] // 50):
+            T = O.explicit_step(T, co, O.BC_ZEROFLUX, dt, inst.dx, inst.dy, chi, nsteps=50, limiter=lim)
+            lo = min(lo, T.min())
+        lows[lim] = lo
+    assert abs(lows[O.LIM_ARITH] - g["min_T_without_limiter"]) < g["min_T_tolerance"]
+    assert lows[O.LIM_VANLEER] >= g["T_cold"] * (1 - 1e-12)
