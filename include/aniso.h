@@ -82,15 +82,19 @@ enum {
                                  shallower PCR) */
     ANISO_OPT_BLOCK_WARPS = 10, /* warps per block of the warp-autonomous kernel (0 = default 4;
                                    1, 2, 4 or 8): lines per block = warps x lines per warp */
-    ANISO_OPT_SCHEME = 11      /* ANISO_SCHEME_2STEP (default) or ANISO_SCHEME_4STEP; the 4-step
-                                  scheme runs on single handles (aniso_step, not batches) with
+    ANISO_OPT_SCHEME = 11      /* ANISO_SCHEME_2STEP (default), _4STEP or _EXPLICIT; the other
+                                  schemes run on single handles (aniso_step, not batches) with
                                   the plain state; ANISO_ERR_UNSUPPORTED with the compensated one */
 };
 enum { ANISO_PREC_FP64 = 0, ANISO_PREC_FP32 = 1 };
 enum {
     ANISO_SCHEME_2STEP = 0, /* Eq. op_2step: one semi-implicit update per direction */
-    ANISO_SCHEME_4STEP = 1  /* Eq. 4step: per direction, the semi-implicit update with its implicit
+    ANISO_SCHEME_4STEP = 1, /* Eq. 4step: per direction, the semi-implicit update with its implicit
                                part over dt/2, then a fully implicit dt/2 update (Section 2.1) */
+    ANISO_SCHEME_EXPLICIT = 2 /* the explicit limited scheme the paper compares against: the face
+                                 fluxes of Eqs. xup and yup all from T^n, applied explicitly;
+                                 stable only up to about the explicit limit (kernel timings are
+                                 reported under ANISO_KERNEL_XSWEEP) */
 };
 enum {
     ANISO_LIM_VANLEER = 0, /* Eq. vanLeer (default) */

@@ -35,6 +35,7 @@ ANISO_OPT_BLOCK_WARPS = 10
 ANISO_OPT_SCHEME = 11
 ANISO_SCHEME_2STEP = 0
 ANISO_SCHEME_4STEP = 1
+ANISO_SCHEME_EXPLICIT = 2
 ANISO_PREC_FP64 = 0
 ANISO_PREC_FP32 = 1
 ANISO_LIM_VANLEER = 0

@@ -214,13 +214,14 @@ extern "C" int aniso_set_option(aniso_t h, int key, long long v)
     case ANISO_OPT_KAHAN:
         if (h->field_set && (v != 0) != (h->kahan != 0))
             return fail(ANISO_ERR_STATE, "compensated state is fixed once the field is set");
-        if (v && h->scheme == ANISO_SCHEME_4STEP)
+        if (v && h->scheme != ANISO_SCHEME_2STEP)
             return fail(ANISO_ERR_UNSUPPORTED, "the compensated state runs the 2-step scheme only");
         h->kahan = v != 0;
         break;
     case ANISO_OPT_SCHEME:
-        if (v != ANISO_SCHEME_2STEP && v != ANISO_SCHEME_4STEP) return fail(ANISO_ERR_ARG, "bad scheme %lld", v);
-        if (v == ANISO_SCHEME_4STEP && h->kahan)
+        if (v != ANISO_SCHEME_2STEP && v != ANISO_SCHEME_4STEP && v != ANISO_SCHEME_EXPLICIT)
+            return fail(ANISO_ERR_ARG, "bad scheme %lld", v);
+        if (v != ANISO_SCHEME_2STEP && h->kahan)
             return fail(ANISO_ERR_UNSUPPORTED, "the compensated state runs the 2-step scheme only");
         if (v == ANISO_SCHEME_4STEP && !h->t4) CU(cudaMalloc(&h->t4, h->cells() * 8));  // either precision
         h->scheme = (int)v;
@@ -586,6 +587,44 @@ static bool x_first(int order, long long counter)
 static int enqueue_steps(aniso_ctx *h, void *T, double dt, int nsteps, long long counter0,
                          cudaStream_t s, std::vector<int> *pairs)
 {
+    if (h->scheme == ANISO_SCHEME_EXPLICIT) {
+        // explicit limited steps, T -> T* -> T ...; an odd count ends with a copy back
+        ExpArgs a{};
+        a.cxx = h->cxx;
+        a.cxy = h->cxy;
+        a.cyy = h->cyy;
+        a.cyx = h->cyx;
+        a.lamx = h->chi_par * dt / (h->dx * h->dx);
+        a.lamy = h->chi_par * dt / (h->dy * h->dy);
+        a.mu = h->chi_par * dt / (h->dx * h->dy);
+        a.nx = h->nx;
+        a.ny = h->ny;
+        a.per = h->bc == ANISO_BC_PERIODIC;
+        a.limiter = h->limiter;
+        a.err = h->err;
+        // rows per thread: enough threads to fill the GPU, longer strips on big grids
+        const long long cols = ((h->nx + 31) / 32) * 32LL;
+        a.rows = (int)std::max(1LL, std::min(32LL, cols * h->ny / (152LL * 2048)));
+        const unsigned rec = pairs ? cudaEventRecordExternal : cudaEventRecordDefault;
+        for (int k = 0; k < nsteps; ++k) {
+            a.Tin = (k & 1) ? h->tstar : T;
+            a.Tout = (k & 1) ? T : h->tstar;
+            int pidx = -1;
+            if (h->profile) {
+                pidx = h->prof.take(ANISO_KERNEL_XSWEEP);
+                if (pidx < 0) return fail(ANISO_ERR_CUDA, "event creation failed");
+                CU(cudaEventRecordWithFlags(h->prof.pool[pidx].a, s, rec));
+            }
+            CU(launch_explicit(h->prec, h->field_fp16, a, s));
+            if (h->profile) {
+                CU(cudaEventRecordWithFlags(h->prof.pool[pidx].b, s, rec));
+                if (pairs) pairs->push_back(pidx);
+                else h->prof.pending.push_back(pidx);
+            }
+        }
+        if (nsteps & 1) CU(cudaMemcpyAsync(T, h->tstar, h->cells() * h->esz(), cudaMemcpyDeviceToDevice, s));
+        return ANISO_OK;
+    }
     if (h->scheme == ANISO_SCHEME_4STEP) {
         // Eq. 4step: per direction, the semi-implicit update with its implicit
         // part over dt/2, then a fully implicit dt/2 update (no transverse term)
@@ -796,7 +835,7 @@ extern "C" int aniso_batch_create(int n, const aniso_t *hs, aniso_batch_t *out)
             h->kahan != hs[0]->kahan)
             return fail(ANISO_ERR_ARG, "aniso_batch_create: handle %d differs in precision/field/limiter/state", k);
         if (h->scheme != ANISO_SCHEME_2STEP)
-            return fail(ANISO_ERR_UNSUPPORTED, "aniso_batch_create: handle %d runs the 4-step scheme", k);
+            return fail(ANISO_ERR_UNSUPPORTED, "aniso_batch_create: handle %d runs another scheme than Eq. op_2step", k);
     }
     aniso_batch *b = new aniso_batch;
     b->hs.assign(hs, hs + n);

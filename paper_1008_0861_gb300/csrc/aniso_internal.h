@@ -131,6 +131,20 @@ cudaError_t launch_line3(int prec, int coef_fp16, const Line3Args &a, int nthrea
 bool line2_config(int prec, int n, bool transposed, int *team, int *lines_per_block, int *nthreads,
                   size_t *smem, int seg_chunks = 0);
 size_t line2_smem_bytes(int prec, int n, int team, int lines_per_block);
+// Explicit limited step (explicit_kernel): one launch per step, blocks of
+// 32 x 8 threads, each thread a column of `rows` rows.
+struct ExpArgs {
+    const void *Tin;
+    void *Tout;
+    const void *cxx, *cxy, *cyy, *cyx;
+    double lamx, lamy, mu;
+    int nx, ny, per;
+    int rows;  // rows per thread strip
+    int limiter;
+    unsigned *err;
+};
+cudaError_t launch_explicit(int prec, int coef_fp16, const ExpArgs &a, cudaStream_t s);
+
 // line4 (warp per line): returns false when the line cannot use it.
 // warps: warps per block (0 = default of 4); seg_chunks: target 16-byte
 // chunks per lane (0 = default of 4), which sets the team size and so the

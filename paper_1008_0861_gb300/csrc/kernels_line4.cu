@@ -1,6 +1,6 @@
-// Instantiations of the warp-per-line kernel (FP32 with FP32 or FP16 face
-// coefficients, FP64), one variant per limiter family.
-#include "line4_kernel.cuh"
+// Instantiations of the warp-per-line kernel and of the explicit step (FP32
+// with FP32 or FP16 face coefficients, FP64), one variant per limiter family.
+#include "explicit_kernel.cuh"
 
 namespace aniso {
 
@@ -32,6 +32,27 @@ cudaError_t launch_line4(int prec, int coef_fp16, const Line2Args &a, int nblock
                   : run4(line4_kernel<float, __half, false>, a, nblocks, nthreads, smem, s);
     return vl ? run4(line4_kernel<float, float, true>, a, nblocks, nthreads, smem, s)
               : run4(line4_kernel<float, float, false>, a, nblocks, nthreads, smem, s);
+}
+
+template <typename K> static cudaError_t run_explicit(K kern, const ExpArgs &a, cudaStream_t s)
+{
+    const int rows_total = (a.ny + a.rows - 1) / a.rows;
+    const dim3 block(32, 8), grid((a.nx + 31) / 32, (rows_total + 7) / 8);
+    kern<<<grid, block, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_explicit(int prec, int coef_fp16, const ExpArgs &a, cudaStream_t s)
+{
+    const bool vl = a.limiter == LIM_VANLEER;
+    if (prec == PREC_FP64)
+        return vl ? run_explicit(explicit_kernel<double, double, true>, a, s)
+                  : run_explicit(explicit_kernel<double, double, false>, a, s);
+    if (coef_fp16)
+        return vl ? run_explicit(explicit_kernel<float, __half, true>, a, s)
+                  : run_explicit(explicit_kernel<float, __half, false>, a, s);
+    return vl ? run_explicit(explicit_kernel<float, float, true>, a, s)
+              : run_explicit(explicit_kernel<float, float, false>, a, s);
 }
 
 }  // namespace aniso
