@@ -222,6 +222,49 @@ def fp64_plain_compare(P, torch):
         P.aniso_destroy(h)
 
 
+def explicit_speedup(P, torch):
+    """The paper's speed-up claim (Section 3.1: the semi-implicit step at ncfl
+    = 1000 against the explicit method at ncfl = 1): time to reach t = 20 on
+    the 512^2 ring (T 10 / 0.1), FP32, both through aniso_step on the GPU."""
+    import workloads as W
+    inst = W.ring_instance(512, t_hot=10.0, t_cold=0.1, chi_par=0.01, dt_factor=1.0)
+    t_end = 20.0
+    out = {"workload": "ring 512^2, T 10/0.1, chi_par 0.01, zero-flux, FP32, t = 0 -> 20"}
+    for name, scheme, ncfl in (("explicit", P.ANISO_SCHEME_EXPLICIT, 1.0),
+                               ("semi_implicit", P.ANISO_SCHEME_2STEP, 1000.0)):
+        dt = ncfl * inst.dx ** 2 / (4 * inst.chi_par)  # Eq. ncfl
+        nsteps = int(round(t_end / dt))
+        h = P.aniso_create(inst.nx, inst.ny, inst.dx, inst.dy, inst.chi_par, 0.0, inst.bc)
+        try:
+            P.aniso_set_option(h, P.ANISO_OPT_PRECISION, P.ANISO_PREC_FP32)
+            P.aniso_set_option(h, P.ANISO_OPT_SCHEME, scheme)
+            bx = torch.tensor(inst.bx, dtype=torch.float32, device="cuda")
+            by = torch.tensor(inst.by, dtype=torch.float32, device="cuda")
+            P.aniso_set_field(h, bx, by)
+            T = torch.tensor(inst.T0, dtype=torch.float32, device="cuda")
+            chunk = min(nsteps, 1000)
+            P.aniso_step(h, T.clone(), dt, chunk)  # builds the graph
+            T = torch.tensor(inst.T0, dtype=torch.float32, device="cuda")
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            done = 0
+            e0.record()
+            while done < nsteps:
+                k = min(chunk, nsteps - done)
+                P.aniso_step(h, T, dt, k)
+                done += k
+            e1.record()
+            P.aniso_sync(h)
+            ms = e0.elapsed_time(e1)
+            _, lo, hi, _ = P.aniso_total(h, T)
+            out[name] = {"ncfl": ncfl, "steps": nsteps, "ms": ms, "min_T": lo, "max_T": hi,
+                         "Gcell_steps_per_s": inst.cells * nsteps / (ms * 1e-3) / 1e9}
+        finally:
+            P.aniso_destroy(h)
+    out["speedup"] = out["explicit"]["ms"] / out["semi_implicit"]["ms"]
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -367,6 +410,7 @@ def main():
         line["accuracy"] = {"rel_linf_vs_fp64_oracle": max(errs),
                             "sample": "instances 0-1, one 200-step call"}
         line["fp64_plain"] = fp64_plain_compare(P, torch)
+        line["speedup_vs_explicit"] = explicit_speedup(P, torch)
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(insts)
         print(json.dumps(line), flush=True)

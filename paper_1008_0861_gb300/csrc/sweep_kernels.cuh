@@ -122,6 +122,45 @@ __device__ __forceinline__ void kahan_add(R hi, R lo, R d, R &ohi, R &olo)
     ohi = h2;
 }
 
+// Error-free transformations (Knuth's TwoSum; Dekker's FastTwoSum, |a| >= |b|):
+// a + b == s + e exactly in the working precision.
+template <typename R> __device__ __forceinline__ void two_sum(R a, R b, R &s, R &e)
+{
+    s = a + b;
+    const R bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+template <typename R> __device__ __forceinline__ void fast_two_sum(R a, R b, R &s, R &e)
+{
+    s = a + b;
+    e = b - (s - a);
+}
+// Compensated accumulator: the running sum is s + c.
+template <typename R> struct CSum {
+    R s = R(0), c = R(0);
+    __device__ __forceinline__ void add(R x)
+    {
+        R t, e;
+        two_sum(s, x, t, e);
+        s = t;
+        c += e;
+    }
+};
+// (hi, lo) + (d - corr), corr = ch + cl, in double-word arithmetic of the
+// working precision (relative error of order 2^-2p): d - corr as an exact
+// pair, then the pair sum renormalised so that |ol| <= ulp(oh)/2.
+template <typename R>
+__device__ __forceinline__ void dw_update(R hi, R lo, R d, R ch, R cl, R &oh, R &ol)
+{
+    R dh, dl;
+    two_sum(d, -ch, dh, dl);
+    dl -= cl;
+    R sh, se;
+    two_sum(hi, dh, sh, se);
+    se += lo + dl;
+    fast_two_sum(sh, se, oh, ol);
+}
+
 // Padded shared-memory index: one spare word per 32 keeps threads that walk
 // neighbouring segments on different banks.
 __device__ __forceinline__ int phys(int k) { return k + (k >> 5); }
@@ -392,12 +431,15 @@ __global__ void __launch_bounds__(512) line_sweep_kernel(LineArgs args)
     // ---- C: T_new = T_old + delta.
     // Compensated state: in exact arithmetic every line's sum of delta is zero
     // (the right-hand side telescopes and each line matrix has unit column
-    // sums), so the line's FP64 sum of the computed delta is rounding
-    // residual; it is removed evenly and hi + lo + delta is formed in FP64,
-    // which conserves the FP64 sum of hi + lo across the update.
+    // sums), so the line's compensated sum of the computed delta is rounding
+    // residual; it is removed evenly and hi + lo + delta - corr is formed in
+    // double-word FP32 arithmetic, which conserves the sum of hi + lo across
+    // the update to far below FP32 rounding.  FP64 only combines the threads'
+    // partial sums (a few operations per thread, none per cell).
     if (K) {
-        double part = 0.0;
-        for (int p = t; p < n; p += P) part += (double)sF[phys(p)];
+        CSum<R> acc;
+        for (int p = t; p < n; p += P) acc.add(sF[phys(p)]);
+        double part = (double)acc.s + (double)acc.c;
         double lsum;
         if (P <= 32) {
             for (int o = 1; o < P; o <<= 1) part += __shfl_xor_sync(0xffffffffu, part, o, P);
@@ -415,14 +457,14 @@ __global__ void __launch_bounds__(512) line_sweep_kernel(LineArgs args)
             __syncthreads();
             lsum = red[P];
         }
-        const double corr = lsum / (double)n;
+        R ch, cl;
+        split_f64(lsum / (double)n, ch, cl);
         if (active) {
             R *out = static_cast<R *>(J.Tout) + (size_t)lc * n;
             R *outl = static_cast<R *>(J.ToutLo) + (size_t)lc * n;
             for (int p = t; p < n; p += P) {
-                const double tot = ((double)rc[p] + (double)rcl[p]) + ((double)sF[phys(p)] - corr);
                 R hi, lo;
-                split_f64(tot, hi, lo);
+                dw_update(rc[p], rcl[p], sF[phys(p)], ch, cl, hi, lo);
                 out[p] = hi;
                 outl[p] = lo;
                 flag_nonfinite(args.err, hi);
@@ -633,31 +675,33 @@ __global__ void __launch_bounds__(512) col_sweep_kernel(ColArgs args)
     const R Xm = sX[((t - 1) & (P - 1)) * Wb + c];
 
     if (K) {
-        // Compensated state: as in line_sweep_kernel, the column's FP64 sum
-        // of delta (zero in exact arithmetic) is removed evenly and
-        // hi + lo + delta is formed in FP64.
+        // Compensated state: as in line_sweep_kernel, the column's compensated
+        // sum of delta (zero in exact arithmetic) is removed evenly and
+        // hi + lo + delta - corr is formed in double-word arithmetic.
         R dprev = Xm;
-        double part = 0.0;
+        CSum<R> acc;
         for (int k = s; k < e; ++k) {
             const R d = sRho[ph(k)] - sAlp[ph(k)] * dprev - sGam[ph(k)] * X;
             sRho[ph(k)] = d;
-            part += (double)d;
+            acc.add(d);
             dprev = d;
         }
         sRho[ph(e)] = X;
-        part += (double)X;
+        acc.add(X);
+        const double part = (double)acc.s + (double)acc.c;
         double *red = reinterpret_cast<double *>(small);  // PCR area, free now
         __syncthreads();
         red[t * Wb + c] = part;
         __syncthreads();
         double csum = 0.0;
         for (int k = 0; k < P; ++k) csum += red[k * Wb + c];  // same order in every thread of the column
-        const double corr = csum / (double)ny;
+        R ch, cl;
+        split_f64(csum / (double)ny, ch, cl);
         if (active) {
             for (int k = s; k <= e; ++k) {
                 const size_t o = (size_t)k * nx + ic;
                 R hi, lo;
-                split_f64(((double)Tin[o] + (double)TinL[o]) + ((double)sRho[ph(k)] - corr), hi, lo);
+                dw_update(Tin[o], TinL[o], sRho[ph(k)], ch, cl, hi, lo);
                 static_cast<R *>(J.Tout)[o] = hi;
                 static_cast<R *>(J.ToutLo)[o] = lo;
                 flag_nonfinite(args.err, hi);
