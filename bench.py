@@ -30,6 +30,16 @@ WORKLOAD = ("batched 512 uneven periodic random-field grids (nx, ny multiples of
             "[64,1024]), FP32, 200 steps per call, one launch per sweep in a captured CUDA graph")
 
 
+def parse_args_for_test(argv):
+    """parse() on an explicit argument list."""
+    old = sys.argv
+    try:
+        sys.argv = ["bench.py"] + list(argv)
+        return parse()
+    finally:
+        sys.argv = old
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -51,6 +61,25 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def reduce_over_ranks(value, op, device):
+    """MAX or SUM of one number over all ranks (identity on one rank)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def job_throughput(cell_steps_local, ms_local, device):
+    """Whole-job Gcell-steps/s: the cell-steps all ranks processed over the
+    slowest rank's time.  Returns (value, max ms, total cell-steps)."""
+    ms = reduce_over_ranks(ms_local, "max", device)
+    units = reduce_over_ranks(cell_steps_local, "sum", device)
+    return units / (ms * 1e-3) / 1e9, ms, units
 
 
 def measured_peak():
@@ -337,13 +366,7 @@ def main():
         sync_all()
     ms = ev0.elapsed_time(ev1)
     kt = {k: P.aniso_kernel_times(batch=batch, kind=k) for k in (0, 1)}
-    ms_step = ms / args.steps
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms_step], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
-    value = cell_steps * world / (ms_step * 1e-3) / 1e9
+    value, ms_step, _ = job_throughput(cell_steps, ms / args.steps, "cuda")
 
     # end to end: host (pinned) T in, one call, host T out, every step
     host = [torch.empty(t.shape, dtype=torch.float32, pin_memory=True) for t in Ts]
@@ -361,7 +384,7 @@ def main():
             hsrc.copy_(t, non_blocking=True)
     e1.record(stream)
     sync_all()
-    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+    e2e_value, e2e_ms, _ = job_throughput(cell_steps, e0.elapsed_time(e1) / e2e_steps, "cuda")
     io_bytes = cells * 4
 
     # roofline of the dominant kernel (live CUDA-event durations over the timed region)
@@ -386,7 +409,7 @@ def main():
                      "algorithmic_bytes_per_launch": BYTES_PER_CELL_SWEEP * cells,
                      "avg_launch_ms": dom_ms / dom_n if dom_n else None,
                      "per_kernel_ms": {names[k]: kt[k][0] / max(1, kt[k][1]) for k in kt}},
-        "e2e": {"value": cell_steps / (e2e_ms * 1e-3) / 1e9, "unit": UNIT,
+        "e2e": {"value": e2e_value, "unit": UNIT,
                 "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes},
         "clocks": clk.summary(),
         "gpu_launches": 2 * STEPS_PER_CALL * args.steps,
