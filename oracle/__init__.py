@@ -28,6 +28,7 @@ from . import build as _build
 
 BC_ZEROFLUX = 0
 BC_PERIODIC = 1
+BC_DIRICHLET = 2   # boundary nodes keep their values (T fixed at the domain edge)
 
 LIM_VANLEER = 0
 LIM_ARITH = 1
@@ -65,7 +66,7 @@ def _load():
         lib.or_ysweep.restype = None
         lib.or_ysweep.argtypes = [i, i, i, _D, _D, d, d, i, _D, _D]
         lib.or_step.restype = i
-        lib.or_step.argtypes = [i, i, i, _D, _D, _D, _D, d, d, d, i, i, ll, i, _D]
+        lib.or_step.argtypes = [i, i, i, _D, _D, _D, _D, d, d, d, i, i, ll, i, _D, ctypes.c_void_p, d]
         lib.or_explicit_step.restype = i
         lib.or_explicit_step.argtypes = [i, i, i, _D, _D, _D, _D, d, d, d, i, i, _D]
         lib.or_totals.restype = None
@@ -151,7 +152,7 @@ def xsweep_row(Tm, T0, Tp, cxx_row, cxy_row, lamx, mu, periodic, limiter=LIM_VAN
     Tm, T0, Tp, g, e = (_f64(v) for v in (Tm, T0, Tp, cxx_row, cxy_row))
     n = len(T0)
     out, w = np.empty(n), np.empty(9 * n)
-    _load().or_xsweep_row(n, int(bool(periodic)), _p(Tm), _p(T0), _p(Tp), _p(g), _p(e),
+    _load().or_xsweep_row(n, int(periodic), _p(Tm), _p(T0), _p(Tp), _p(g), _p(e),
                           float(lamx), float(mu), int(limiter), _p(out), _p(w))
     return out
 
@@ -161,7 +162,7 @@ def ysweep_col(Tl, T0, Tr, cyy_col, cyx_col, lamy, mu, periodic, limiter=LIM_VAN
     Tl, T0, Tr, g, e = (_f64(v) for v in (Tl, T0, Tr, cyy_col, cyx_col))
     n = len(T0)
     out, w = np.empty(n), np.empty(9 * n)
-    _load().or_ysweep_col(n, int(bool(periodic)), _p(Tl), _p(T0), _p(Tr), _p(g), _p(e),
+    _load().or_ysweep_col(n, int(periodic), _p(Tl), _p(T0), _p(Tr), _p(g), _p(e),
                           float(lamy), float(mu), int(limiter), _p(out), _p(w))
     return out
 
@@ -187,14 +188,17 @@ def ysweep(T, co: Coeffs, bc, lamy, mu, limiter=LIM_VANLEER):
 
 
 def step(T, co: Coeffs, bc, dt, dx, dy, chi_par, nsteps=1, step0=0,
-         order=ORDER_XY, limiter=LIM_VANLEER):
+         order=ORDER_XY, limiter=LIM_VANLEER, Q=None):
     """nsteps steps of Eq. op_2step starting at step counter step0; returns a
-    new FP64 array."""
+    new FP64 array.  Q (optional, [ny][nx]): a source term, added as
+    T += dt Q before each step."""
     T = _f64(T).copy()
     ny, nx = T.shape
     lamx, lamy, mu = lambdas(dt, dx, dy, chi_par)
+    q = None if Q is None else _f64(Q)
     rc = _load().or_step(nx, ny, int(bc), _p(co.cxx), _p(co.cxy), _p(co.cyy), _p(co.cyx),
-                         lamx, lamy, mu, int(limiter), int(order), int(step0), int(nsteps), _p(T))
+                         lamx, lamy, mu, int(limiter), int(order), int(step0), int(nsteps), _p(T),
+                         None if q is None else q.ctypes.data_as(ctypes.c_void_p), float(dt))
     if rc:
         raise MemoryError("oracle scratch allocation failed")
     return T

@@ -48,6 +48,7 @@
 
 #define OR_BC_ZEROFLUX 0
 #define OR_BC_PERIODIC 1
+#define OR_BC_DIRICHLET 2 /* boundary nodes hold their values (T fixed at the domain edge) */
 
 #define OR_LIM_VANLEER 0
 #define OR_LIM_ARITH 1 /* arithmetic mean: the linear-analysis reading of Section 2.1 */
@@ -198,10 +199,13 @@ int or_cyclic(int n, const double *a, const double *b, const double *c, const do
  * passes T0 for a mirrored ghost row).  cxx_row, cxy_row: x-face coefficients
  * of row j (face i+1/2 at index i).  lamx = chi dt/dx^2, mu = chi dt/(dx dy).
  * out: T* of row j.  w: scratch of 9*nx doubles. */
-void or_xsweep_row(int nx, int periodic, const double *Tm, const double *T0, const double *Tp,
+void or_xsweep_row(int nx, int mode, const double *Tm, const double *T0, const double *Tp,
                    const double *cxx_row, const double *cxy_row, double lamx, double mu, int lim,
                    double *out, double *w)
 {
+    /* mode: OR_BC_ZEROFLUX, OR_BC_PERIODIC, or OR_BC_DIRICHLET (the first and
+     * last cell keep their values: identity rows) */
+    int periodic = mode == OR_BC_PERIODIC, pinned = mode == OR_BC_DIRICHLET;
     double *flux = w;          /* transverse term at face i+1/2 (index i)  */
     double *a = w + nx, *b = w + 2 * nx, *c = w + 3 * nx, *d = w + 4 * nx;
     double *tw = w + 5 * nx;   /* 4*nx for the cyclic solver */
@@ -231,6 +235,12 @@ void or_xsweep_row(int nx, int periodic, const double *Tm, const double *T0, con
         b[i] = 1.0 + lamx * (cm + cp);
         d[i] = T0[i] + mu * (fplus - fminus);
     }
+    if (pinned) {
+        a[0] = c[0] = a[nx - 1] = c[nx - 1] = 0.0;
+        b[0] = b[nx - 1] = 1.0;
+        d[0] = T0[0];
+        d[nx - 1] = T0[nx - 1];
+    }
     if (periodic) or_cyclic(nx, a, b, c, d, out, tw);
     else or_thomas(nx, a, b, c, d, out, tw);
 }
@@ -240,10 +250,11 @@ void or_xsweep_row(int nx, int periodic, const double *Tm, const double *T0, con
 /* Eq. yup for one column i.  Tl, T0, Tr: columns i-1, i, i+1 of T* stored
  * contiguously (index j).  cyy_col, cyx_col: y-face coefficients of column i
  * (face j+1/2 at index j).  lamy = chi dt/dy^2.  out: T^{n+1} of column i. */
-void or_ysweep_col(int ny, int periodic, const double *Tl, const double *T0, const double *Tr,
+void or_ysweep_col(int ny, int mode, const double *Tl, const double *T0, const double *Tr,
                    const double *cyy_col, const double *cyx_col, double lamy, double mu, int lim,
                    double *out, double *w)
 {
+    int periodic = mode == OR_BC_PERIODIC, pinned = mode == OR_BC_DIRICHLET;
     double *flux = w;
     double *a = w + ny, *b = w + 2 * ny, *c = w + 3 * ny, *d = w + 4 * ny;
     double *tw = w + 5 * ny;
@@ -272,6 +283,12 @@ void or_ysweep_col(int ny, int periodic, const double *Tl, const double *T0, con
         b[j] = 1.0 + lamy * (cm + cp);
         d[j] = T0[j] + mu * (fplus - fminus);
     }
+    if (pinned) {
+        a[0] = c[0] = a[ny - 1] = c[ny - 1] = 0.0;
+        b[0] = b[ny - 1] = 1.0;
+        d[0] = T0[0];
+        d[ny - 1] = T0[ny - 1];
+    }
     if (periodic) or_cyclic(ny, a, b, c, d, out, tw);
     else or_thomas(ny, a, b, c, d, out, tw);
 }
@@ -289,10 +306,14 @@ void or_xsweep(int nx, int ny, int bc, const double *cxx, const double *cxy, dou
         double *w = (double *)malloc(sizeof(double) * 9 * (size_t)nx);
 #pragma omp for schedule(static)
         for (int j = 0; j < ny; ++j) {
+            if (bc == OR_BC_DIRICHLET && (j == 0 || j == ny - 1)) {  /* boundary row: fixed */
+                memcpy(Tout + (size_t)j * nx, Tin + (size_t)j * nx, sizeof(double) * (size_t)nx);
+                continue;
+            }
             int jm = j - 1, jp = j + 1;
             if (jm < 0) jm = periodic ? ny - 1 : 0;      /* mirrored ghost row */
             if (jp >= ny) jp = periodic ? 0 : ny - 1;
-            or_xsweep_row(nx, periodic, Tin + (size_t)jm * nx, Tin + (size_t)j * nx,
+            or_xsweep_row(nx, bc, Tin + (size_t)jm * nx, Tin + (size_t)j * nx,
                           Tin + (size_t)jp * nx, cxx + (size_t)j * nx, cxy + (size_t)j * nx, lamx,
                           mu, lim, Tout + (size_t)j * nx, w);
         }
@@ -312,6 +333,10 @@ void or_ysweep(int nx, int ny, int bc, const double *cyy, const double *cyx, dou
                *ey = buf + 4 * ny, *o = buf + 5 * ny, *w = buf + 6 * ny;
 #pragma omp for schedule(static)
         for (int i = 0; i < nx; ++i) {
+            if (bc == OR_BC_DIRICHLET && (i == 0 || i == nx - 1)) {  /* boundary column: fixed */
+                for (int j = 0; j < ny; ++j) Tout[(size_t)j * nx + i] = Tin[(size_t)j * nx + i];
+                continue;
+            }
             int il = i - 1, ir = i + 1;
             if (il < 0) il = periodic ? nx - 1 : 0;      /* mirrored ghost column */
             if (ir >= nx) ir = periodic ? 0 : nx - 1;
@@ -323,7 +348,7 @@ void or_ysweep(int nx, int ny, int bc, const double *cyy, const double *cyx, dou
                 gy[j] = cyy[r + i];
                 ey[j] = cyx[r + i];
             }
-            or_ysweep_col(ny, periodic, Tl, T0, Tr, gy, ey, lamy, mu, lim, o, w);
+            or_ysweep_col(ny, bc, Tl, T0, Tr, gy, ey, lamy, mu, lim, o, w);
             for (int j = 0; j < ny; ++j) Tout[(size_t)j * nx + i] = o[j];
         }
         free(buf);
@@ -338,11 +363,15 @@ void or_ysweep(int nx, int ny, int bc, const double *cyy, const double *cyx, dou
  * Returns 0, or -1 if scratch could not be allocated. */
 int or_step(int nx, int ny, int bc, const double *cxx, const double *cxy, const double *cyy,
             const double *cyx, double lamx, double lamy, double mu, int lim, int order,
-            long long step0, int nsteps, double *T)
+            long long step0, int nsteps, double *T, const double *Q, double dt)
 {
     double *Ts = (double *)malloc(sizeof(double) * (size_t)nx * ny);
     if (!Ts) return -1;
     for (int n = 0; n < nsteps; ++n) {
+        /* optional source term, applied as an explicit stage before the
+         * updates (the convergence test of Section 3.2 adds Q to Eq. 1) */
+        if (Q)
+            for (size_t k = 0; k < (size_t)nx * ny; ++k) T[k] += dt * Q[k];
         long long s = step0 + n;
         int x_first = (order == OR_ORDER_XY) || (order == OR_ORDER_ALTERNATE && (s % 2) == 0);
         if (x_first) {
@@ -413,6 +442,8 @@ int or_explicit_step(int nx, int ny, int bc, const double *cxx, const double *cx
                 double fym = j > 0 ? ex_fy(nx, ny, per, cyy, cyx, lamy, mu, lim, T, i, j - 1)
                                    : (per ? ex_fy(nx, ny, per, cyy, cyx, lamy, mu, lim, T, i, ny - 1) : 0.0);
                 Tn[(size_t)j * nx + i] = T[(size_t)j * nx + i] + (fxp - fxm) + (fyp - fym);
+                if (bc == OR_BC_DIRICHLET && (i == 0 || j == 0 || i == nx - 1 || j == ny - 1))
+                    Tn[(size_t)j * nx + i] = T[(size_t)j * nx + i];  /* boundary node: fixed */
             }
         }
         memcpy(T, Tn, sizeof(double) * (size_t)nx * ny);

@@ -480,3 +480,103 @@ def test_explicit_ring_minimum_matches_paper():
         lows[lim] = lo
     assert abs(lows[O.LIM_ARITH] - g["min_T_without_limiter"]) < g["min_T_tolerance"]
     assert lows[O.LIM_VANLEER] >= g["T_cold"] * (1 - 1e-12)
+
+
+# ----------------------------------- fixed boundary nodes and source term
+
+def _pinned_nodes(nx, ny):
+    return [j * nx + i for j in range(ny) for i in range(nx) if i in (0, nx - 1) or j in (0, ny - 1)]
+
+
+@pytest.mark.parametrize("nx,ny", [(6, 7), (7, 5)])
+def test_fixed_boundary_step_matches_dense_operator(nx, ny):
+    """bc 2 (the convergence test's T = 0 on the boundary): the outer ring of
+    nodes are identity rows of every directional operator, and the source is
+    an explicit stage: T1 = M (T0 + dt Q) with M = Eq. op_2step assembled
+    densely (arithmetic-mean transverse average) with those identity rows."""
+    rng = np.random.default_rng(nx + 10 * ny)
+    ang = rng.uniform(0, 2 * math.pi, (ny, nx))
+    co = O.face_coeffs(np.cos(ang), np.sin(ang), O.BC_DIRICHLET, chi_par=1.0, chi_perp=0.1)
+    dx, dy, chi = 1.0 / (nx - 1), 1.0 / (ny - 1), 0.6
+    dt = 25 * W.cfl_dt(dx, dy, chi)
+    lamx, lamy, mu = O.lambdas(dt, dx, dy, chi)
+    T0 = rng.normal(size=(ny, nx))
+    Q = rng.normal(size=(ny, nx))
+    pins = _pinned_nodes(nx, ny)
+    Q.ravel()[pins] = 0.0
+    # the zero-flux assembly gives the interior rows; boundary rows become identity
+    M = {}
+    for xf in (True, False):
+        per = False
+        N = nx * ny
+        mats = []
+        for which in ("x", "y"):
+            A, E = np.zeros((N, N)), np.zeros((N, N))
+            for j in range(ny):
+                for i in range(nx):
+                    k = j * nx + i
+                    if which == "x":
+                        gp = co.cxx[j, i] if i < nx - 1 else 0.0
+                        gm = co.cxx[j, i - 1] if i > 0 else 0.0
+                        ep = co.cxy[j, i] if i < nx - 1 else 0.0
+                        em = co.cxy[j, i - 1] if i > 0 else 0.0
+                        A[k, k] += 1 + lamx * (gp + gm)
+                        if gp: A[k, _cell(i + 1, j, nx, ny, per)] -= lamx * gp
+                        if gm: A[k, _cell(i - 1, j, nx, ny, per)] -= lamx * gm
+                        E[k, k] += 1
+                        for (ii, sg, e) in ((i, 1, ep), (i - 1, -1, em)):
+                            if not e:
+                                continue
+                            for (ci, cj, sv) in ((ii + 1, j + 1, 1), (ii + 1, j - 1, -1), (ii, j + 1, 1), (ii, j - 1, -1)):
+                                E[k, _cell(ci, cj, nx, ny, per)] += sg * mu * e * 0.25 * sv
+                    else:
+                        gp = co.cyy[j, i] if j < ny - 1 else 0.0
+                        gm = co.cyy[j - 1, i] if j > 0 else 0.0
+                        ep = co.cyx[j, i] if j < ny - 1 else 0.0
+                        em = co.cyx[j - 1, i] if j > 0 else 0.0
+                        A[k, k] += 1 + lamy * (gp + gm)
+                        if gp: A[k, _cell(i, j + 1, nx, ny, per)] -= lamy * gp
+                        if gm: A[k, _cell(i, j - 1, nx, ny, per)] -= lamy * gm
+                        E[k, k] += 1
+                        for (jj, sg, e) in ((j, 1, ep), (j - 1, -1, em)):
+                            if not e:
+                                continue
+                            for (ci, cj, sv) in ((i + 1, jj + 1, 1), (i - 1, jj + 1, -1), (i + 1, jj, 1), (i - 1, jj, -1)):
+                                E[k, _cell(ci, cj, nx, ny, per)] += sg * mu * e * 0.25 * sv
+            for k in pins:
+                A[k, :] = 0.0
+                E[k, :] = 0.0
+                A[k, k] = E[k, k] = 1.0
+            mats.append(np.linalg.solve(A, E))
+        Mx, My = mats
+        M[xf] = My @ Mx if xf else Mx @ My
+    for order, xf in ((O.ORDER_XY, True), (O.ORDER_YX, False)):
+        T1 = O.step(T0, co, O.BC_DIRICHLET, dt, dx, dy, chi, order=order, limiter=O.LIM_ARITH, Q=Q)
+        np.testing.assert_allclose(T1.ravel(), M[xf] @ (T0 + dt * Q).ravel(), atol=1e-12)
+        np.testing.assert_array_equal(T1.ravel()[pins], (T0 + dt * Q).ravel()[pins])
+
+
+def _steady_center(inst, co, tol=1e-11):
+    T, prev, c = inst.T0.copy(), 0.0, inst.nx // 2
+    for _ in range(2000):
+        T = O.step(T, co, O.BC_DIRICHLET, inst.dt, inst.dx, inst.dy, inst.chi_par, nsteps=100, Q=inst.Q)
+        v = T[c, c]
+        if abs(v - prev) < tol * abs(v):
+            return v, T
+        prev = v
+    raise AssertionError("no steady state")
+
+
+def test_fixed_boundary_isotropic_steady_state_is_second_order():
+    """chi_perp = chi_par makes the operator isotropic: the steady state of
+    the convergence test (Q = 2 pi^2 cos(pi x) cos(pi y), T = 0 on the
+    boundary) is cos(pi x) cos(pi y), so T(0,0) -> 1; the error falls by 4
+    per halving of the spacing (second order) at a fixed ncfl."""
+    errs = []
+    for n in (9, 17, 33):
+        inst = W.sovinec_instance(n, ncfl=1.0, chi_perp=1.0)
+        co = O.face_coeffs(inst.bx, inst.by, O.BC_DIRICHLET, inst.chi_par, inst.chi_perp)
+        v, T = _steady_center(inst, co)
+        errs.append(abs(v - 1.0))
+        assert np.all(T[0, :] == 0.0) and np.all(T[:, -1] == 0.0)
+    assert 3.5 < errs[0] / errs[1] < 4.5 and 3.5 < errs[1] / errs[2] < 4.5

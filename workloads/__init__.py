@@ -24,5 +24,6 @@ from .generators import (  # noqa: F401
     ring_instance,
     random_instance,
     batch_instances,
+    sovinec_instance,
     cfl_dt,
 )

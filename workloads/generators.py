@@ -56,7 +56,7 @@ class Instance:
     ny: int
     dx: float
     dy: float
-    bc: int            # 0 zero-flux, 1 periodic
+    bc: int            # 0 zero-flux, 1 periodic, 2 fixed boundary nodes
     chi_par: float
     chi_perp: float
     dt: float
@@ -64,6 +64,7 @@ class Instance:
     bx: np.ndarray = field(repr=False)
     by: np.ndarray = field(repr=False)
     T0: np.ndarray = field(repr=False)
+    Q: np.ndarray = field(default=None, repr=False)  # source term, or None
 
     @property
     def cells(self) -> int:
@@ -74,7 +75,8 @@ class Instance:
         precision run sees; the oracle widens the same values)."""
         return Instance(self.name, self.nx, self.ny, self.dx, self.dy, self.bc, self.chi_par,
                         self.chi_perp, self.dt, self.nsteps, self.bx.astype(dtype),
-                        self.by.astype(dtype), self.T0.astype(dtype))
+                        self.by.astype(dtype), self.T0.astype(dtype),
+                        None if self.Q is None else self.Q.astype(dtype))
 
 
 def cfl_dt(dx: float, dy: float, chi_par: float) -> float:
@@ -102,6 +104,33 @@ def ring_instance(n: int, t_hot: float = 12.0, t_cold: float = 10.0, chi_par: fl
     dt = dt_factor * cfl_dt(dx, dy, chi_par)
     return Instance("ring%dx%d" % (nx, ny), nx, ny, dx, dy, 0, chi_par, 0.0, dt, nsteps,
                     bx, by, T0)
+
+
+def sovinec_instance(n: int, chi_par: float = 1.0, ncfl: float = 1000.0, chi_perp: float = 0.0,
+                     nsteps: int = 0) -> Instance:
+    """Convergence test of Section 3.2 (after Sovinec et al.): [-1/2,1/2]^2
+    with T = 0 on the boundary, T(0) = 0, source Q = 2 pi^2 cos(pi x) cos(pi y),
+    b along the contours of phi = cos(pi x) cos(pi y), i.e. b = z x grad(phi)
+    / |grad phi| (b = (1, 0) where |grad phi| < 1e-8).  Nodes x_i = -1/2 +
+    i/(n-1): the outer ring sits on the boundary and keeps T = 0 (bc 2); an odd
+    n puts a node at the origin, where the steady state is 1/chi_perp,num.
+    dt = ncfl dx^2 / (4 chi_par) (Eq. ncfl)."""
+    h = 1.0 / (n - 1)
+    x = -0.5 + np.arange(n) * h
+    X, Y = np.meshgrid(x, x)                       # [ny, nx]
+    gx = -math.pi * np.sin(math.pi * X) * np.cos(math.pi * Y)
+    gy = -math.pi * np.cos(math.pi * X) * np.sin(math.pi * Y)
+    mag = np.hypot(gx, gy)
+    small = mag < 1e-8
+    safe = np.where(small, 1.0, mag)
+    bx = np.where(small, 1.0, -gy / safe)
+    by = np.where(small, 0.0, gx / safe)
+    Q = 2.0 * math.pi ** 2 * np.cos(math.pi * X) * np.cos(math.pi * Y)
+    Q[0, :] = Q[-1, :] = 0.0
+    Q[:, 0] = Q[:, -1] = 0.0
+    dt = ncfl * h * h / (4.0 * chi_par)
+    return Instance("sovinec%d" % n, n, n, h, h, 2, chi_par, chi_perp, dt, nsteps, bx, by,
+                    np.zeros((n, n)), Q)
 
 
 def _random_field(rng: SplitMix64, nx: int, ny: int, kmax: int, chunk_rows: int = 1024):
