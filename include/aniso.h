@@ -58,7 +58,11 @@ enum {
 /* Boundary conditions (both directions). */
 enum {
     ANISO_BC_ZEROFLUX = 0, /* reflective (Section 3.1): no flux through boundary faces */
-    ANISO_BC_PERIODIC = 1  /* wrap-around; line systems become cyclic */
+    ANISO_BC_PERIODIC = 1, /* wrap-around; line systems become cyclic */
+    ANISO_BC_DIRICHLET = 2 /* fixed values on the domain edge (the convergence test of Section
+                              3.2): the outer ring of cells holds boundary nodes whose values
+                              never change; single handles only (not batches, not with the
+                              compensated state) */
 };
 
 /* Option keys for aniso_set_option and their values. */
@@ -144,6 +148,14 @@ int aniso_set_option(aniso_t h, int key, long long value);
  * call returns and the stream has passed it.  Errors: ANISO_ERR_ARG (null),
  * ANISO_ERR_OOM, ANISO_ERR_CUDA. */
 int aniso_set_field(aniso_t h, const void *bx, const void *by);
+
+/* Source term Q (device pointer, nx*ny, handle precision, row-major; the
+ * convergence test of Section 3.2 adds Q to Eq. 1): copied into the handle and
+ * applied in every later step as an explicit stage T += dt Q before the
+ * directional updates.  NULL removes it.  ANISO_ERR_STATE before
+ * aniso_set_field; ANISO_ERR_UNSUPPORTED with the compensated state.  A
+ * handle with a source cannot join a batch. */
+int aniso_set_source(aniso_t h, const void *Q);
 
 /* Advance T by nsteps steps of size dt (Eq. op_2step), in place.
  *   T      : device array nx*ny in the handle's precision.

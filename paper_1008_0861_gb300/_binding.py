@@ -20,6 +20,7 @@ ANISO_ERR_UNSUPPORTED = 7
 # boundary conditions
 ANISO_BC_ZEROFLUX = 0
 ANISO_BC_PERIODIC = 1
+ANISO_BC_DIRICHLET = 2
 # options
 ANISO_OPT_PRECISION = 0
 ANISO_OPT_FIELD_FP16 = 1
@@ -55,7 +56,7 @@ EXPORTED = ("aniso_create", "aniso_set_option", "aniso_set_field", "aniso_step",
             "aniso_total", "aniso_get_state", "aniso_set_state", "aniso_sync",
             "aniso_kernel_times", "aniso_destroy", "aniso_last_error", "aniso_batch_create",
             "aniso_step_batched", "aniso_batch_destroy", "aniso_step_noalloc",
-            "aniso_batch_autotune", "aniso_autotune_candidate")
+            "aniso_batch_autotune", "aniso_autotune_candidate", "aniso_set_source")
 
 
 class AnisoError(RuntimeError):
@@ -97,6 +98,7 @@ def load():
         "aniso_step_noalloc": (i, [i, i, d, d, d, d, i, i, vp, vp, vp, d, i, vp]),
         "aniso_batch_autotune": (i, [vp, P(vp), P(d), i, i, P(i), P(d)]),
         "aniso_autotune_candidate": (i, [i, P(i), P(i), P(i)]),
+        "aniso_set_source": (i, [vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -215,6 +217,12 @@ def aniso_autotune_candidate(index):
     f, w, s = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     _check(load().aniso_autotune_candidate(int(index), ctypes.byref(f), ctypes.byref(w), ctypes.byref(s)))
     return f.value, w.value, s.value
+
+
+def aniso_set_source(h, Q):
+    """Source term Q (device tensor [ny][nx], handle precision) applied as
+    T += dt Q before every step; None removes it."""
+    _check(load().aniso_set_source(h, _ptr(Q)))
 
 
 def aniso_batch_destroy(batch):

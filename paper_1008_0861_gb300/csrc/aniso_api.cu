@@ -100,6 +100,7 @@ struct aniso_ctx {
     int prec = PREC_FP64, field_fp16 = 0, kahan = 0, limiter = LIM_VANLEER, order = ANISO_ORDER_XY;
     int use_graph = 1, profile = 0, fast = 3, seg_chunks = 0, l4_warps = 0, scheme = 0;
     void *t4 = nullptr;  // intermediate of the 4-step scheme
+    void *q = nullptr;   // source term (aniso_set_source), handle precision
     cudaStream_t stream = 0;
     long long step_counter = 0;
     bool field_set = false;
@@ -126,6 +127,10 @@ struct aniso_ctx {
     size_t csz() const { return prec == PREC_FP64 ? 8 : (field_fp16 ? 2 : 4); }
     int coef_kind() const { return prec == PREC_FP64 ? 0 : (field_fp16 ? 2 : 1); }
     bool long_cols() const { return ny > MAX_COL; }
+    // columns solved as transposed rows: long columns, and fixed-boundary grids
+    // (only the general row kernel knows fixed boundary nodes)
+    bool col_transpose() const { return long_cols() || bc == ANISO_BC_DIRICHLET; }
+    bool dirichlet() const { return bc == ANISO_BC_DIRICHLET; }
     int vec() const { return prec == PREC_FP64 ? 2 : 4; }
     // Grid shapes the vectorised x-then-y path handles: both line lengths a
     // multiple of the 16-byte vector and short enough for transposed output.
@@ -153,7 +158,8 @@ struct aniso_ctx {
 static void free_buffers(aniso_ctx *h)
 {
     void **bufs[] = {&h->cxx, &h->cxy, &h->cyy,      &h->cyx,  &h->cyyT, &h->cyxT, &h->tstar,
-                     &h->tA,  &h->tB,  &h->tlo, &h->tstar_lo, &h->tAlo, &h->tBlo, &h->t4};
+                     &h->tA,  &h->tB,  &h->tlo, &h->tstar_lo, &h->tAlo, &h->tBlo, &h->t4,
+                     &h->q};
     for (void **b : bufs) {
         if (*b) cudaFree(*b);
         *b = nullptr;
@@ -183,7 +189,7 @@ extern "C" int aniso_create(int nx, int ny, double dx, double dy, double chi_par
     if (!(chi_par > 0)) return fail(ANISO_ERR_ARG, "aniso_create: chi_par must be > 0");
     if (!(chi_perp >= 0) || chi_perp > chi_par)
         return fail(ANISO_ERR_ARG, "aniso_create: need 0 <= chi_perp <= chi_par");
-    if (bc != ANISO_BC_ZEROFLUX && bc != ANISO_BC_PERIODIC)
+    if (bc != ANISO_BC_ZEROFLUX && bc != ANISO_BC_PERIODIC && bc != ANISO_BC_DIRICHLET)
         return fail(ANISO_ERR_ARG, "aniso_create: unknown boundary condition %d", bc);
     aniso_ctx *h = new aniso_ctx;
     h->nx = nx;
@@ -275,6 +281,8 @@ extern "C" int aniso_set_field(aniso_t h, const void *bx, const void *by)
         return fail(ANISO_ERR_ARG, "aniso_set_field: FP16 field storage needs FP32 precision");
     if (h->kahan && h->prec != PREC_FP32)
         return fail(ANISO_ERR_ARG, "aniso_set_field: the compensated state needs FP32 precision");
+    if (h->kahan && h->dirichlet())
+        return fail(ANISO_ERR_UNSUPPORTED, "aniso_set_field: the compensated state needs a conserving boundary");
     if (h->nx > h->max_line() || (h->long_cols() && h->ny > h->max_line()))
         return fail(ANISO_ERR_UNSUPPORTED, "grid %dx%d exceeds the on-chip line limit %d", h->nx, h->ny,
                     h->max_line());
@@ -285,11 +293,11 @@ extern "C" int aniso_set_field(aniso_t h, const void *bx, const void *by)
         CU(cudaMalloc(&h->cyy, n * h->csz()));
         CU(cudaMalloc(&h->cyx, n * h->csz()));
         CU(cudaMalloc(&h->tstar, n * h->esz()));
-        if (h->long_cols() || h->fast_shape()) {
+        if (h->col_transpose() || h->fast_shape()) {
             CU(cudaMalloc(&h->cyyT, n * h->csz()));
             CU(cudaMalloc(&h->cyxT, n * h->csz()));
         }
-        if (h->long_cols()) {
+        if (h->col_transpose()) {
             CU(cudaMalloc(&h->tA, n * h->esz()));
             CU(cudaMalloc(&h->tB, n * h->esz()));
         }
@@ -297,7 +305,7 @@ extern "C" int aniso_set_field(aniso_t h, const void *bx, const void *by)
             CU(cudaMalloc(&h->tlo, n * h->esz()));
             CU(cudaMalloc(&h->tstar_lo, n * h->esz()));
             CU(cudaMemsetAsync(h->tlo, 0, n * h->esz(), h->stream));
-            if (h->long_cols()) {
+            if (h->col_transpose()) {
                 CU(cudaMalloc(&h->tAlo, n * h->esz()));
                 CU(cudaMalloc(&h->tBlo, n * h->esz()));
             }
@@ -417,7 +425,7 @@ static int enqueue_line3(aniso_ctx *h, const void *in, void *out, const void *g,
 // transposed y coefficients) and writes T back row-major.
 static bool use_fast(const aniso_ctx *h, const void *T)
 {
-    return h->fast && !h->kahan && h->order == ANISO_ORDER_XY && h->cyyT && aligned16(T) &&
+    return h->fast && !h->kahan && !h->dirichlet() && h->order == ANISO_ORDER_XY && h->cyyT && aligned16(T) &&
            aligned16(h->tstar) && h->fast_shape();
 }
 
@@ -493,6 +501,7 @@ static int enqueue_sweep(aniso_ctx *h, int dir, const void *in, void *out, doubl
         J.nlines = nlines;
         J.per_line = per_line;
         J.per_cross = per_cross;
+        J.pin_ends = J.pin_lines = h->dirichlet() ? 1 : 0;
         int nthreads;
         line_config(h->prec, n, &J.team, &J.lines_per_block, &nthreads);
         J.block0 = 0;
@@ -507,21 +516,21 @@ static int enqueue_sweep(aniso_ctx *h, int dir, const void *in, void *out, doubl
     if (dir == ANISO_DIR_X) {
         int t1, t2, t3;
         size_t t4;
-        if (!kahan && h->fast == 2 && aligned16(in) && aligned16(out) &&
+        if (!kahan && !h->dirichlet() && h->fast == 2 && aligned16(in) && aligned16(out) &&
             line3_config(h->prec, h->field_fp16, h->nx, false, h->seg_chunks, &t1, &t2, &t3, &t4))
             return enqueue_line3(h, in, out, h->cxx, h->cxy, h->nx, h->ny, per, per, lamx, mu, false,
                                  ANISO_KERNEL_XSWEEP, s, pairs);
-        if (!kahan && h->fast == 3 && aligned16(in) && aligned16(out) &&
+        if (!kahan && !h->dirichlet() && h->fast == 3 && aligned16(in) && aligned16(out) &&
             line4_config(h->prec, h->nx, false, h->l4_warps, h->seg_chunks, &t1, &t2, &t3, &t4))
             return enqueue_line2(h, in, out, h->cxx, h->cxy, h->nx, h->ny, per, per, lamx, mu, false,
                                  ANISO_KERNEL_XSWEEP, s, pairs, true);
-        if (!kahan && h->fast && aligned16(in) && aligned16(out) &&
+        if (!kahan && !h->dirichlet() && h->fast && aligned16(in) && aligned16(out) &&
             line2_config(h->prec, h->nx, false, &t1, &t2, &t3, &t4, h->seg_chunks))
             return enqueue_line2(h, in, out, h->cxx, h->cxy, h->nx, h->ny, per, per, lamx, mu, false,
                                  ANISO_KERNEL_XSWEEP, s, pairs);
         return line(in, out, h->cxx, h->cxy, h->nx, h->ny, per, per, lamx, ANISO_KERNEL_XSWEEP, in_lo, out_lo);
     }
-    if (!h->long_cols()) {
+    if (!h->col_transpose()) {
         ColArgs a{};
         a.jobs = nullptr;
         a.njobs = 1;
@@ -558,11 +567,11 @@ static int enqueue_sweep(aniso_ctx *h, int dir, const void *in, void *out, doubl
         // the columns are contiguous lines now: the vectorised kernels take them when they can
         int t1, t2, t3;
         size_t t4;
-        if (!kahan && h->fast == 3 && aligned16(h->tA) && aligned16(h->tB) &&
+        if (!kahan && !h->dirichlet() && h->fast == 3 && aligned16(h->tA) && aligned16(h->tB) &&
             line4_config(h->prec, h->ny, false, h->l4_warps, h->seg_chunks, &t1, &t2, &t3, &t4))
             rc = enqueue_line2(h, h->tA, h->tB, h->cyyT, h->cyxT, h->ny, h->nx, per, per, lamy, mu, false,
                                ANISO_KERNEL_YSWEEP, s, pairs, true);
-        else if (!kahan && h->fast && aligned16(h->tA) && aligned16(h->tB) &&
+        else if (!kahan && !h->dirichlet() && h->fast && aligned16(h->tA) && aligned16(h->tB) &&
                  line2_config(h->prec, h->ny, false, &t1, &t2, &t3, &t4, h->seg_chunks))
             rc = enqueue_line2(h, h->tA, h->tB, h->cyyT, h->cyxT, h->ny, h->nx, per, per, lamy, mu, false,
                                ANISO_KERNEL_YSWEEP, s, pairs);
@@ -601,6 +610,7 @@ static int enqueue_steps(aniso_ctx *h, void *T, double dt, int nsteps, long long
         a.ny = h->ny;
         a.per = h->bc == ANISO_BC_PERIODIC;
         a.limiter = h->limiter;
+        a.pin = h->dirichlet() ? 1 : 0;
         a.err = h->err;
         // rows per thread: enough threads to fill the GPU, longer strips on big grids
         const long long cols = ((h->nx + 31) / 32) * 32LL;
@@ -609,6 +619,7 @@ static int enqueue_steps(aniso_ctx *h, void *T, double dt, int nsteps, long long
         for (int k = 0; k < nsteps; ++k) {
             a.Tin = (k & 1) ? h->tstar : T;
             a.Tout = (k & 1) ? T : h->tstar;
+            if (h->q) CU(launch_source(h->prec, const_cast<void *>(a.Tin), h->q, dt, h->cells(), s));
             int pidx = -1;
             if (h->profile) {
                 pidx = h->prof.take(ANISO_KERNEL_XSWEEP);
@@ -632,6 +643,7 @@ static int enqueue_steps(aniso_ctx *h, void *T, double dt, int nsteps, long long
             const bool xf = x_first(h->order, counter0 + k);
             const int d1 = xf ? ANISO_DIR_X : ANISO_DIR_Y, d2 = xf ? ANISO_DIR_Y : ANISO_DIR_X;
             int rc;
+            if (h->q) CU(launch_source(h->prec, T, h->q, dt, h->cells(), s));
             if ((rc = enqueue_sweep(h, d1, T, h->t4, dt, s, pairs, nullptr, nullptr, 0.5, 1.0))) return rc;
             if ((rc = enqueue_sweep(h, d1, h->t4, h->tstar, dt, s, pairs, nullptr, nullptr, 0.5, 0.0))) return rc;
             if ((rc = enqueue_sweep(h, d2, h->tstar, h->t4, dt, s, pairs, nullptr, nullptr, 0.5, 1.0))) return rc;
@@ -641,6 +653,7 @@ static int enqueue_steps(aniso_ctx *h, void *T, double dt, int nsteps, long long
     }
     if (use_fast(h, T)) {
         for (int k = 0; k < nsteps; ++k) {
+            if (h->q) CU(launch_source(h->prec, T, h->q, dt, h->cells(), s));
             int rc = enqueue_fast_step(h, T, dt, s, pairs);
             if (rc) return rc;
         }
@@ -648,6 +661,7 @@ static int enqueue_steps(aniso_ctx *h, void *T, double dt, int nsteps, long long
     }
     for (int k = 0; k < nsteps; ++k) {
         const bool xf = x_first(h->order, counter0 + k);
+        if (h->q) CU(launch_source(h->prec, T, h->q, dt, h->cells(), s));
         int rc = enqueue_sweep(h, xf ? ANISO_DIR_X : ANISO_DIR_Y, T, h->tstar, dt, s, pairs, h->tlo, h->tstar_lo);
         if (rc) return rc;
         rc = enqueue_sweep(h, xf ? ANISO_DIR_Y : ANISO_DIR_X, h->tstar, T, dt, s, pairs, h->tstar_lo, h->tlo);
@@ -660,6 +674,26 @@ static int check_ready(aniso_ctx *h, const char *who)
 {
     if (!h) return fail(ANISO_ERR_ARG, "%s: null handle", who);
     if (!h->field_set) return fail(ANISO_ERR_STATE, "%s: aniso_set_field has not been called", who);
+    return ANISO_OK;
+}
+
+extern "C" int aniso_set_source(aniso_t h, const void *Q)
+{
+    if (!h) return fail(ANISO_ERR_ARG, "aniso_set_source: null handle");
+    if (!h->field_set) return fail(ANISO_ERR_STATE, "aniso_set_source: set the field first");
+    if (!Q) {
+        if (h->q) {
+            CU(cudaStreamSynchronize(h->stream));
+            cudaFree(h->q);
+            h->q = nullptr;
+        }
+        drop_graph(h);
+        return ANISO_OK;
+    }
+    if (h->kahan) return fail(ANISO_ERR_UNSUPPORTED, "aniso_set_source: not with the compensated state");
+    if (!h->q) CU(cudaMalloc(&h->q, h->cells() * h->esz()));
+    CU(cudaMemcpyAsync(h->q, Q, h->cells() * h->esz(), cudaMemcpyDeviceToDevice, h->stream));
+    drop_graph(h);
     return ANISO_OK;
 }
 
@@ -836,6 +870,8 @@ extern "C" int aniso_batch_create(int n, const aniso_t *hs, aniso_batch_t *out)
             return fail(ANISO_ERR_ARG, "aniso_batch_create: handle %d differs in precision/field/limiter/state", k);
         if (h->scheme != ANISO_SCHEME_2STEP)
             return fail(ANISO_ERR_UNSUPPORTED, "aniso_batch_create: handle %d runs another scheme than Eq. op_2step", k);
+        if (h->dirichlet() || h->q)
+            return fail(ANISO_ERR_UNSUPPORTED, "aniso_batch_create: handle %d has fixed boundaries or a source", k);
     }
     aniso_batch *b = new aniso_batch;
     b->hs.assign(hs, hs + n);

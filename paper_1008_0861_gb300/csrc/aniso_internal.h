@@ -32,6 +32,9 @@ struct LineJob {
     int per_line, per_cross;  // periodic along the line / across lines
     int team, lines_per_block;
     int block0, nblocks;      // this job's block range in the launch
+    // fixed-value (Dirichlet) boundary nodes: the first and last cell of every
+    // line, and every cell of the first and last line, keep their values
+    int pin_ends, pin_lines;
 };
 
 // One column update (Eq. yup) in the natural row-major layout: blocks own
@@ -141,9 +144,12 @@ struct ExpArgs {
     int nx, ny, per;
     int rows;  // rows per thread strip
     int limiter;
+    int pin;  // fixed boundary nodes (Dirichlet): the grid's outer ring keeps its values
     unsigned *err;
 };
 cudaError_t launch_explicit(int prec, int coef_fp16, const ExpArgs &a, cudaStream_t s);
+
+cudaError_t launch_source(int prec, void *T, const void *Q, double dt, size_t n, cudaStream_t s);
 
 // line4 (warp per line): returns false when the line cannot use it.
 // warps: warps per block (0 = default of 4); seg_chunks: target 16-byte

@@ -77,7 +77,8 @@ __global__ void __launch_bounds__(256) explicit_kernel(ExpArgs a)
         if (lane == 0 || !col_ok) Fxm = fx(il, j, rm.l, rc.l, rp.l, rm.c, rc.c, rp.c);
         if (!per && ic == 0) Fxm = R(0);
         const R Fyp = fy(j, rc, rp);
-        const R Tn = rc.c + (Fxp - Fxm) + (Fyp - Fym);
+        R Tn = rc.c + (Fxp - Fxm) + (Fyp - Fym);
+        if (a.pin && (i == 0 || i == nx - 1 || j == 0 || j == ny - 1)) Tn = rc.c;  // fixed boundary node
         if (col_ok) {
             out[(size_t)j * nx + i] = Tn;
             bad |= !(fabs(Tn) < R(INFINITY));

@@ -364,16 +364,21 @@ __global__ void __launch_bounds__(512) line_sweep_kernel(LineArgs args)
     const int s = (int)(((long long)t * n) / P), e = (int)(((long long)(t + 1) * n) / P) - 1;
     const int em1 = e - 1 < 0 ? e - 1 + n : e - 1;
     const R ge = sG[phys(e)], gem = sG[phys(em1)];
-    const R re = sF[phys(e)] - sF[phys(em1)];
-    const R ae = -lam * gem, ce = -lam * ge, be = R(1) - ae - ce;
+    // fixed boundary nodes: identity rows (delta = 0) for the line's end cells,
+    // or for every cell of a fixed line
+    const bool ident = J.pin_lines && (lc == 0 || lc == J.nlines - 1);
+    const bool pin_e = ident || (J.pin_ends && (e == 0 || e == n - 1));
+    const R re = pin_e ? R(0) : sF[phys(e)] - sF[phys(em1)];
+    const R ae = pin_e ? R(0) : -lam * gem, ce = pin_e ? R(0) : -lam * ge, be = R(1) - ae - ce;
     R rho1 = R(0), alp1 = R(0), gam1 = R(-1);  // map of the virtual row e: delta_e = delta_e
     R qp = R(0), qq = R(1), qw = R(0);          // composite map, starts as the identity
     R gk = gem, Fk = sF[phys(em1)];  // values at k = e-1, carried down the loop
     for (int k = e - 1; k >= s; --k) {
         const int km = k - 1 < 0 ? k - 1 + n : k - 1;
         const R gkm = sG[phys(km)], Fkm = sF[phys(km)];
-        const R rk = Fk - Fkm;
-        const R a = -lam * gkm, c = -lam * gk, b = R(1) - a - c;
+        const bool pin_k = ident || (J.pin_ends && k == 0);
+        const R rk = pin_k ? R(0) : Fk - Fkm;
+        const R a = pin_k ? R(0) : -lam * gkm, c = pin_k ? R(0) : -lam * gk, b = R(1) - a - c;
         gk = gkm;
         Fk = Fkm;
         const R inv = Num<R>::div(R(1), b - c * alp1);
@@ -761,14 +766,15 @@ __global__ void face_coeffs_kernel(const B *__restrict__ bx, const B *__restrict
     const size_t o = (size_t)j * nx + i;
     const double omk = __dsub_rn(1.0, kappa);
     double vxx = 0.0, vxy = 0.0, vyy = 0.0, vyx = 0.0;
-    if (!(bc == 0 && i == nx - 1)) {
+    const bool per = bc == 1;  // otherwise the boundary faces carry no flux
+    if (per || i != nx - 1) {
         const size_t o1 = (size_t)j * nx + ((i + 1) % nx);
         const double fbx = __dmul_rn(0.5, __dadd_rn((double)bx[o], (double)bx[o1]));
         const double fby = __dmul_rn(0.5, __dadd_rn((double)by[o], (double)by[o1]));
         vxx = __dadd_rn(kappa, __dmul_rn(omk, __dmul_rn(fbx, fbx)));
         vxy = __dmul_rn(omk, __dmul_rn(fbx, fby));
     }
-    if (!(bc == 0 && j == ny - 1)) {
+    if (per || j != ny - 1) {
         const size_t o1 = (size_t)((j + 1) % ny) * nx + i;
         const double fbx = __dmul_rn(0.5, __dadd_rn((double)bx[o], (double)bx[o1]));
         const double fby = __dmul_rn(0.5, __dadd_rn((double)by[o], (double)by[o1]));

@@ -209,6 +209,24 @@ bool line4_config(int prec, int n, bool transposed, int warps, int seg_chunks, i
     return true;
 }
 
+// Source stage of a step: T += dt Q, elementwise.
+template <typename R> __global__ void source_kernel(R *T, const R *Q, R dt, size_t n)
+{
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x)
+        T[k] += dt * Q[k];
+}
+
+cudaError_t launch_source(int prec, void *T, const void *Q, double dt, size_t n, cudaStream_t s)
+{
+    const int threads = 256;
+    const int blocks = (int)std::min<size_t>((n + threads - 1) / threads, 152 * 8);
+    if (prec == PREC_FP64)
+        source_kernel<double><<<blocks, threads, 0, s>>>(static_cast<double *>(T), static_cast<const double *>(Q), dt, n);
+    else
+        source_kernel<float><<<blocks, threads, 0, s>>>(static_cast<float *>(T), static_cast<const float *>(Q), (float)dt, n);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_line3(int prec, int coef_fp16, const Line3Args &a, int nthreads, size_t smem, cudaStream_t s)
 {
     if (prec == PREC_FP64) return launch_line3_f64(a, nthreads, smem, s);
