@@ -328,7 +328,8 @@ static bool aligned16(const void *p) { return ((uintptr_t)p & 15) == 0; }
 // One vectorised line update (line2_kernel) of `nlines` lines of n cells.
 static int enqueue_line2(aniso_ctx *h, const void *in, void *out, const void *g, const void *e, int n,
                          int nlines, int per_line, int per_cross, double lam, double mu, bool transposed,
-                         int kind, cudaStream_t s, std::vector<int> *pairs, bool v4 = false)
+                         int kind, cudaStream_t s, std::vector<int> *pairs, bool v4 = false,
+                         const void *in_lo = nullptr, void *out_lo = nullptr)
 {
     Line2Args a{};
     a.jobs = nullptr;
@@ -338,6 +339,8 @@ static int enqueue_line2(aniso_ctx *h, const void *in, void *out, const void *g,
     Line2Job &J = a.one;
     J.Tin = in;
     J.Tout = out;
+    J.TinLo = in_lo;
+    J.ToutLo = out_lo;
     J.g = g;
     J.e = e;
     J.lam = lam;
@@ -364,7 +367,7 @@ static int enqueue_line2(aniso_ctx *h, const void *in, void *out, const void *g,
         CU(cudaEventRecordWithFlags(h->prof.pool[pidx].a, s, rec_flags));
     }
     CU(v4 ? launch_line4(h->prec, h->field_fp16, a, J.nblocks, nthreads, smem, s)
-          : launch_line2(h->prec, h->field_fp16, a, J.nblocks, nthreads, smem, s));
+          : launch_line2(h->prec, h->field_fp16, a, J.nblocks, nthreads, smem, s, in_lo != nullptr));
     if (h->profile) {
         CU(cudaEventRecordWithFlags(h->prof.pool[pidx].b, s, rec_flags));
         if (pairs) pairs->push_back(pidx);
@@ -524,10 +527,12 @@ static int enqueue_sweep(aniso_ctx *h, int dir, const void *in, void *out, doubl
             line4_config(h->prec, h->nx, false, h->l4_warps, h->seg_chunks, &t1, &t2, &t3, &t4))
             return enqueue_line2(h, in, out, h->cxx, h->cxy, h->nx, h->ny, per, per, lamx, mu, false,
                                  ANISO_KERNEL_XSWEEP, s, pairs, true);
-        if (!kahan && !h->dirichlet() && h->fast && aligned16(in) && aligned16(out) &&
+        // (the block-synchronous kernel also takes the compensated state)
+        if (!h->dirichlet() && h->fast && aligned16(in) && aligned16(out) &&
+            (!kahan || (aligned16(in_lo) && aligned16(out_lo))) &&
             line2_config(h->prec, h->nx, false, &t1, &t2, &t3, &t4, h->seg_chunks))
             return enqueue_line2(h, in, out, h->cxx, h->cxy, h->nx, h->ny, per, per, lamx, mu, false,
-                                 ANISO_KERNEL_XSWEEP, s, pairs);
+                                 ANISO_KERNEL_XSWEEP, s, pairs, false, in_lo, out_lo);
         return line(in, out, h->cxx, h->cxy, h->nx, h->ny, per, per, lamx, ANISO_KERNEL_XSWEEP, in_lo, out_lo);
     }
     if (!h->col_transpose()) {
@@ -571,10 +576,12 @@ static int enqueue_sweep(aniso_ctx *h, int dir, const void *in, void *out, doubl
             line4_config(h->prec, h->ny, false, h->l4_warps, h->seg_chunks, &t1, &t2, &t3, &t4))
             rc = enqueue_line2(h, h->tA, h->tB, h->cyyT, h->cyxT, h->ny, h->nx, per, per, lamy, mu, false,
                                ANISO_KERNEL_YSWEEP, s, pairs, true);
-        else if (!kahan && !h->dirichlet() && h->fast && aligned16(h->tA) && aligned16(h->tB) &&
+        else if (!h->dirichlet() && h->fast && aligned16(h->tA) && aligned16(h->tB) &&
+                 (!kahan || (aligned16(h->tAlo) && aligned16(h->tBlo))) &&
                  line2_config(h->prec, h->ny, false, &t1, &t2, &t3, &t4, h->seg_chunks))
             rc = enqueue_line2(h, h->tA, h->tB, h->cyyT, h->cyxT, h->ny, h->nx, per, per, lamy, mu, false,
-                               ANISO_KERNEL_YSWEEP, s, pairs);
+                               ANISO_KERNEL_YSWEEP, s, pairs, false, kahan ? h->tAlo : nullptr,
+                               kahan ? h->tBlo : nullptr);
         else
             rc = line(h->tA, h->tB, h->cyyT, h->cyxT, h->ny, h->nx, per, per, lamy, ANISO_KERNEL_YSWEEP,
                       kahan ? h->tAlo : nullptr, kahan ? h->tBlo : nullptr);

@@ -77,6 +77,8 @@ struct ColArgs {
 struct Line2Job {
     const void *Tin;
     void *Tout;
+    const void *TinLo;  // compensated low parts (line2, line-major output only), or nullptr
+    void *ToutLo;
     const void *g;
     const void *e;
     double lam, mu;
@@ -172,7 +174,7 @@ cudaError_t launch_line(int prec, int coef_fp16, const LineArgs &a, int nblocks,
 cudaError_t launch_col(int prec, int coef_fp16, const ColArgs &a, int nblocks, int nthreads,
                        size_t smem, cudaStream_t s, bool kahan = false);
 cudaError_t launch_line2(int prec, int coef_fp16, const Line2Args &a, int nblocks, int nthreads,
-                         size_t smem, cudaStream_t s);
+                         size_t smem, cudaStream_t s, bool kahan = false);
 // Face coefficients from cell-centred b (FP64 arithmetic, one rounding to the
 // storage type).  bprec: element type of bx, by.  coef: 0 fp64, 1 fp32, 2 fp16.
 // cyyT/cyxT (optional) receive transposed copies [nx][ny].

@@ -53,18 +53,23 @@ cudaError_t launch_col_f32(int coef_fp16, bool kahan, const ColArgs &a, int nblo
                  : goc(col_sweep_kernel<float, float, false>, nblocks, nthreads, smem, s, a);
 }
 
-cudaError_t launch_line2_f32(int coef_fp16, const Line2Args &a, int nblocks, int nthreads, size_t smem,
-                             cudaStream_t s)
+template <typename K> static cudaError_t go2(K kern, int nblocks, int nthreads, size_t smem, cudaStream_t s,
+                                               const Line2Args &a)
 {
-    cudaError_t err;
-    if (coef_fp16) {
-        if ((err = prep(line2_kernel<float, __half>, smem)) != cudaSuccess) return err;
-        line2_kernel<float, __half><<<nblocks, nthreads, smem, s>>>(a);
-    } else {
-        if ((err = prep(line2_kernel<float, float>, smem)) != cudaSuccess) return err;
-        line2_kernel<float, float><<<nblocks, nthreads, smem, s>>>(a);
-    }
+    cudaError_t err = prep(kern, smem);
+    if (err != cudaSuccess) return err;
+    kern<<<nblocks, nthreads, smem, s>>>(a);
     return cudaGetLastError();
+}
+
+cudaError_t launch_line2_f32(int coef_fp16, const Line2Args &a, int nblocks, int nthreads, size_t smem,
+                             cudaStream_t s, bool kahan)
+{
+    if (coef_fp16)
+        return kahan ? go2(line2_kernel<float, __half, true>, nblocks, nthreads, smem, s, a)
+                     : go2(line2_kernel<float, __half, false>, nblocks, nthreads, smem, s, a);
+    return kahan ? go2(line2_kernel<float, float, true>, nblocks, nthreads, smem, s, a)
+                 : go2(line2_kernel<float, float, false>, nblocks, nthreads, smem, s, a);
 }
 
 template <typename C> static cudaError_t launch3(const Line3Args &a, int nthreads, size_t smem, cudaStream_t s)

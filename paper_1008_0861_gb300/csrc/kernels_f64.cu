@@ -35,9 +35,9 @@ cudaError_t launch_col_f64(const ColArgs &a, int nblocks, int nthreads, size_t s
 
 cudaError_t launch_line2_f64(const Line2Args &a, int nblocks, int nthreads, size_t smem, cudaStream_t s)
 {
-    cudaError_t err = prep(line2_kernel<double, double>, smem);
+    cudaError_t err = prep(line2_kernel<double, double, false>, smem);
     if (err != cudaSuccess) return err;
-    line2_kernel<double, double><<<nblocks, nthreads, smem, s>>>(a);
+    line2_kernel<double, double, false><<<nblocks, nthreads, smem, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -116,7 +116,11 @@ template <> __device__ __forceinline__ float limit4_v2<float>(int lim, float a, 
     return limit4<float>(lim, a, b, c, d);
 }
 
-template <typename R, typename C>
+// K: compensated state (hi in Tin/Tout, lo in TinLo/ToutLo; line-major output
+// only): differences are formed as (hi_a - hi_b) + (lo_a - lo_b), and each
+// line's compensated sum of delta (zero in exact arithmetic) is removed before
+// the double-word update hi + lo + delta.
+template <typename R, typename C, bool K>
 __global__ void __launch_bounds__(512, 2) line2_kernel(Line2Args args)
 {
     typedef typename V16<R>::T VT;
@@ -139,6 +143,9 @@ __global__ void __launch_bounds__(512, 2) line2_kernel(Line2Args args)
     if (ld < 0) ld = J.per_cross ? nl - 1 : 0;
     const R *Tin = static_cast<const R *>(J.Tin);
     const R *rc = Tin + (size_t)lc * n, *ru = Tin + (size_t)lu * n, *rd = Tin + (size_t)ld * n;
+    const R *TinL = static_cast<const R *>(J.TinLo);  // K only
+    const R *rcl = K ? TinL + (size_t)lc * n : nullptr, *rul = K ? TinL + (size_t)lu * n : nullptr,
+            *rdl = K ? TinL + (size_t)ld * n : nullptr;
     const C *G = static_cast<const C *>(J.g) + (size_t)lc * n;
     const C *E = static_cast<const C *>(J.e) + (size_t)lc * n;
     const R lam = (R)J.lam, mu = (R)J.mu;
@@ -161,18 +168,32 @@ __global__ void __launch_bounds__(512, 2) line2_kernel(Line2Args args)
         const int lane_in = t & (width - 1);
         const VT *vd = reinterpret_cast<const VT *>(rd), *vc = reinterpret_cast<const VT *>(rc),
                  *vu = reinterpret_cast<const VT *>(ru);
+        const VT *wd = reinterpret_cast<const VT *>(rdl), *wc = reinterpret_cast<const VT *>(rcl),
+                 *wu = reinterpret_cast<const VT *>(rul);
         for (int c0 = 0; c0 < m; c0 += P) {
             const int c = c0 + t;
             const int cl = c < m ? c : m - 1;
             R Td[N], Tc[N], Tu[N], Gv[N], Ev[N];
+            R Ld[N] = {}, Lc[N] = {}, Lu[N] = {};  // low parts (K only)
             V16<R>::unpack(vd[cl], Td);
             V16<R>::unpack(vc[cl], Tc);
             V16<R>::unpack(vu[cl], Tu);
+            if (K) {
+                V16<R>::unpack(wd[cl], Ld);
+                V16<R>::unpack(wc[cl], Lc);
+                V16<R>::unpack(wu[cl], Lu);
+            }
             ld_coef_chunk(G + cl * N, Gv);
             ld_coef_chunk(E + cl * N, Ev);
             R nd = __shfl_down_sync(full, Td[0], 1, width);
             R nc = __shfl_down_sync(full, Tc[0], 1, width);
             R nu = __shfl_down_sync(full, Tu[0], 1, width);
+            R ndl = R(0), ncl = R(0), nul = R(0);
+            if (K) {
+                ndl = __shfl_down_sync(full, Ld[0], 1, width);
+                ncl = __shfl_down_sync(full, Lc[0], 1, width);
+                nul = __shfl_down_sync(full, Lu[0], 1, width);
+            }
             if (c < m) {
                 if (lane_in == width - 1 || c + 1 >= m) {
                     int p1 = (c + 1) * N;
@@ -180,15 +201,22 @@ __global__ void __launch_bounds__(512, 2) line2_kernel(Line2Args args)
                     nd = rd[p1];
                     nc = rc[p1];
                     nu = ru[p1];
+                    if (K) {
+                        ndl = rdl[p1];
+                        ncl = rcl[p1];
+                        nul = rul[p1];
+                    }
                 }
                 R Fo[N];
 #pragma unroll
                 for (int v = 0; v < N; ++v) {
-                    const R d1 = v + 1 < N ? Td[v + 1] : nd;
-                    const R c1 = v + 1 < N ? Tc[v + 1] : nc;
-                    const R u1 = v + 1 < N ? Tu[v + 1] : nu;
-                    const R dT = limit4_v2<R>(lim, u1 - c1, c1 - d1, Tu[v] - Tc[v], Tc[v] - Td[v]);
-                    Fo[v] = lam * Gv[v] * (c1 - Tc[v]) + mu * Ev[v] * dT;
+                    const R d1 = v + 1 < N ? Td[v + 1] : nd, d1l = v + 1 < N ? Ld[v + 1] : ndl;
+                    const R c1 = v + 1 < N ? Tc[v + 1] : nc, c1l = v + 1 < N ? Lc[v + 1] : ncl;
+                    const R u1 = v + 1 < N ? Tu[v + 1] : nu, u1l = v + 1 < N ? Lu[v + 1] : nul;
+                    const R dT = limit4_v2<R>(lim, dif<R, K>(u1, u1l, c1, c1l), dif<R, K>(c1, c1l, d1, d1l),
+                                              dif<R, K>(Tu[v], Lu[v], Tc[v], Lc[v]),
+                                              dif<R, K>(Tc[v], Lc[v], Td[v], Ld[v]));
+                    Fo[v] = lam * Gv[v] * dif<R, K>(c1, c1l, Tc[v], Lc[v]) + mu * Ev[v] * dT;
                 }
                 vF[swz(c)] = V16<R>::pack(Fo);
                 vG[swz(c)] = V16<R>::pack(Gv);
@@ -323,7 +351,57 @@ __global__ void __launch_bounds__(512, 2) line2_kernel(Line2Args args)
     __syncthreads();
 
     // ---- C: T_new = T_old + delta
-    if (!J.transpose_out) {
+    if (K) {
+        // compensated state (line-major output): remove the line's residual
+        // sum of delta, then the double-word update of (hi, lo)
+        CSum<R> acc;
+        for (int c = t; c < m; c += P) {
+            R d[N];
+            V16<R>::unpack(vF[swz(c)], d);
+#pragma unroll
+            for (int v = 0; v < N; ++v) acc.add(d[v]);
+        }
+        double part = (double)acc.s + (double)acc.c;
+        double lsum;
+        if (P <= 32) {
+            for (int o = 1; o < P; o <<= 1) part += __shfl_xor_sync(full, part, o, P);
+            lsum = part;
+        } else {
+            // the PCR area of this line (8P words, 8-byte aligned), free since B2
+            double *red = reinterpret_cast<double *>(reinterpret_cast<R *>(smem_raw) + LPB * LS + tm * 8 * P);
+            red[t] = part;
+            __syncthreads();
+            if (t == 0) {
+                double a = 0.0;
+                for (int k = 0; k < P; ++k) a += red[k];
+                red[P] = a;
+            }
+            __syncthreads();
+            lsum = red[P];
+        }
+        R ch, cl;
+        split_f64(lsum / (double)n, ch, cl);
+        if (active) {
+            const VT *vo = reinterpret_cast<const VT *>(rc), *wo = reinterpret_cast<const VT *>(rcl);
+            VT *out = reinterpret_cast<VT *>(static_cast<R *>(J.Tout) + (size_t)lc * n);
+            VT *outl = reinterpret_cast<VT *>(static_cast<R *>(J.ToutLo) + (size_t)lc * n);
+            for (int c = t; c < m; c += P) {
+                R to[N], tw[N], d[N], oh[N], ol[N];
+                V16<R>::unpack(vo[c], to);
+                V16<R>::unpack(wo[c], tw);
+                V16<R>::unpack(vF[swz(c)], d);
+                R sum = R(0);
+#pragma unroll
+                for (int v = 0; v < N; ++v) {
+                    dw_update(to[v], tw[v], d[v], ch, cl, oh[v], ol[v]);
+                    sum += oh[v];
+                }
+                bad |= !(fabs(sum) < R(INFINITY));
+                out[c] = V16<R>::pack(oh);
+                outl[c] = V16<R>::pack(ol);
+            }
+        }
+    } else if (!J.transpose_out) {
         if (active) {
             const VT *vo = reinterpret_cast<const VT *>(rc);
             VT *out = reinterpret_cast<VT *>(static_cast<R *>(J.Tout) + (size_t)lc * n);

@@ -10,7 +10,7 @@ cudaError_t launch_col_f32(int coef_fp16, bool kahan, const ColArgs &a, int nblo
 cudaError_t launch_line_f64(const LineArgs &a, int nblocks, int nthreads, size_t smem, cudaStream_t s);
 cudaError_t launch_col_f64(const ColArgs &a, int nblocks, int nthreads, size_t smem, cudaStream_t s);
 cudaError_t launch_line2_f32(int coef_fp16, const Line2Args &a, int nblocks, int nthreads, size_t smem,
-                             cudaStream_t s);
+                             cudaStream_t s, bool kahan);
 cudaError_t launch_line2_f64(const Line2Args &a, int nblocks, int nthreads, size_t smem, cudaStream_t s);
 cudaError_t launch_line3_f32(int coef_fp16, const Line3Args &a, int nthreads, size_t smem, cudaStream_t s);
 cudaError_t launch_line3_f64(const Line3Args &a, int nthreads, size_t smem, cudaStream_t s);
@@ -234,10 +234,10 @@ cudaError_t launch_line3(int prec, int coef_fp16, const Line3Args &a, int nthrea
 }
 
 cudaError_t launch_line2(int prec, int coef_fp16, const Line2Args &a, int nblocks, int nthreads,
-                         size_t smem, cudaStream_t s)
+                         size_t smem, cudaStream_t s, bool kahan)
 {
     if (prec == PREC_FP64) return launch_line2_f64(a, nblocks, nthreads, smem, s);
-    return launch_line2_f32(coef_fp16, a, nblocks, nthreads, smem, s);
+    return launch_line2_f32(coef_fp16, a, nblocks, nthreads, smem, s, kahan);
 }
 
 template <typename B, typename C>

@@ -105,7 +105,8 @@ def test_kahan_batched_matches_single(lib):
     import torch
     insts = W.batch_instances(6, nsteps=5, size_cap=384)
     pairs = [_kahan_grid(lib, i) for i in insts]
-    singles = [_kahan_grid(lib, i) for i in insts]
+    # batches run the compensated state on the general kernels; so do these singles
+    singles = [_kahan_grid(lib, i, fast=0) for i in insts]
     try:
         b = lib.aniso_batch_create([h for h, _ in pairs])
         lib.aniso_step_batched(b, [T for _, T in pairs], [i.dt for i in insts], [5] * len(insts))
@@ -131,3 +132,25 @@ def test_kahan_option_rules(lib):
         assert ei.value.code == lib.ANISO_ERR_ARG
     finally:
         lib.aniso_destroy(h)
+
+
+@pytest.mark.parametrize("nx,ny", [(256, 96), (96, 2048), (4096, 16)])
+def test_kahan_vectorised_and_general_kernels_agree(lib, nx, ny):
+    """The block-synchronous vectorised kernel and the general kernels both
+    run the compensated state: same step within FP32 rounding, both
+    conserving the sum of hi + lo to 1e-12 (columns above 1024 rows go
+    through the transposed path on both)."""
+    inst = W.random_instance(nx, ny, seed=13, chi_par=1.0, dt_factor=500.0)
+    a, Ta = _kahan_grid(lib, inst, fp16=True, fast=1)
+    b, Tb = _kahan_grid(lib, inst, fp16=True, fast=0)
+    try:
+        s0 = float(np.sum(inst.T0.astype(np.float32).astype(np.float64)))
+        lib.aniso_step(a, Ta, inst.dt, 20)
+        lib.aniso_step(b, Tb, inst.dt, 20)
+        ga, gb = _hi_lo(lib, a, Ta), _hi_lo(lib, b, Tb)
+        assert rel_linf(ga, gb) < 2e-5
+        for h, T in ((a, Ta), (b, Tb)):
+            assert abs(lib.aniso_total(h, T)[0] - s0) / s0 < 1e-12
+    finally:
+        lib.aniso_destroy(a)
+        lib.aniso_destroy(b)
