@@ -16,7 +16,7 @@
  * limited face differences (the two DeltaT-bar equations after Eq. yup).
  * The operator form of one step is Eq. op_2step.
  *
- * Readings where the paper is silent (each also listed in the design doc):
+ * Readings where the paper is silent:
  *  - b is averaged to faces by the plain mean of the two adjacent cell
  *    centres (Section 2, text after Eq. yup); the implicit coefficient is the
  *    square of the averaged component, as Eq. xup writes it.
