@@ -10,8 +10,16 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/aniso.h"
 #include "aniso_internal.h"
+
+// NVTX range around a public call, for timeline tools (a no-op without one).
+struct TraceRange {
+    explicit TraceRange(const char *name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+};
 
 using namespace aniso;
 
@@ -275,6 +283,7 @@ extern "C" int aniso_set_option(aniso_t h, int key, long long v)
 
 extern "C" int aniso_set_field(aniso_t h, const void *bx, const void *by)
 {
+    TraceRange trace("aniso_set_field");
     if (!h) return fail(ANISO_ERR_ARG, "aniso_set_field: null handle");
     if (!bx || !by) return fail(ANISO_ERR_ARG, "aniso_set_field: null field pointer");
     if (h->field_fp16 && h->prec != PREC_FP32)
@@ -706,6 +715,7 @@ extern "C" int aniso_set_source(aniso_t h, const void *Q)
 
 extern "C" int aniso_step(aniso_t h, void *T, double dt, int nsteps)
 {
+    TraceRange trace("aniso_step");
     int rc = check_ready(h, "aniso_step");
     if (rc) return rc;
     if (!T) return fail(ANISO_ERR_ARG, "aniso_step: T is NULL");
@@ -766,6 +776,7 @@ extern "C" int aniso_step(aniso_t h, void *T, double dt, int nsteps)
 
 extern "C" int aniso_sweep(aniso_t h, int dir, const void *Tin, void *Tout, double dt)
 {
+    TraceRange trace("aniso_sweep");
     int rc = check_ready(h, "aniso_sweep");
     if (rc) return rc;
     if (!Tin || !Tout || Tin == Tout) return fail(ANISO_ERR_ARG, "aniso_sweep: need distinct Tin, Tout");
@@ -1313,6 +1324,7 @@ static int batch_build(aniso_batch *b, void *const *T, const double *dt, const i
 
 extern "C" int aniso_step_batched(aniso_batch_t b, void *const *T, const double *dt, const int *nsteps)
 {
+    TraceRange trace("aniso_step_batched");
     if (!b) return fail(ANISO_ERR_ARG, "aniso_step_batched: null batch");
     if (!T || !dt || !nsteps) return fail(ANISO_ERR_ARG, "aniso_step_batched: null array");
     const int n = (int)b->hs.size();
@@ -1371,6 +1383,7 @@ static const int kTuneCount = (int)(sizeof(kTuneCands) / sizeof(kTuneCands[0]));
 extern "C" int aniso_batch_autotune(aniso_batch_t b, void *const *T, const double *dt, int nsteps, int reps,
                                     int *choice, double *best_ms)
 {
+    TraceRange trace("aniso_batch_autotune");
     if (!b) return fail(ANISO_ERR_ARG, "aniso_batch_autotune: null batch");
     if (!T || !dt) return fail(ANISO_ERR_ARG, "aniso_batch_autotune: null array");
     if (nsteps < 1 || reps < 1) return fail(ANISO_ERR_ARG, "aniso_batch_autotune: nsteps and reps must be >= 1");
