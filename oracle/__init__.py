@@ -6,7 +6,8 @@ the GPU library (``paper_1008_0861_gb300``) and imports nothing from it.
 
 The arithmetic lives in ``aniso_oracle.c`` (plain C, FP64, written from
 Section 2 of Sharma & Hammett, arXiv:1008.0861: Eqs. xup and yup, the limited
-face differences after them, Eq. vanLeer and Eq. op_2step).  This module
+face differences after them, Eq. vanLeer and Eq. op_2step) and, for the
+three-dimensional form of Section 2.1, ``aniso3d_oracle.c``.  This module
 marshals numpy arrays to it, composes those sweeps into the 4-step scheme of
 Eq. 4step (step4), runs the explicit limited scheme built from the same face
 fluxes (explicit_step), and does the one encoding step the paper leaves
@@ -73,6 +74,13 @@ def _load():
         lib.or_totals.argtypes = [sz, _D, _D, _D, _D]
         lib.or_num_threads.restype = i
         lib.or_num_threads.argtypes = []
+        _D9 = _D * 9
+        lib.or3_face_coeffs.restype = None
+        lib.or3_face_coeffs.argtypes = [i, i, i, i, d, _D, _D, _D, _D9]
+        lib.or3_sweep.restype = None
+        lib.or3_sweep.argtypes = [i, i, i, i, i, _D, _D, _D, d, d, d, i, _D, _D]
+        lib.or3_step.restype = i
+        lib.or3_step.argtypes = [i, i, i, i, _D9, _D, _D, i, i, i, _D]
         _lib = lib
     return _lib
 
@@ -237,6 +245,80 @@ def explicit_step(T, co: Coeffs, bc, dt, dx, dy, chi_par, nsteps=1, limiter=LIM_
     lamx, lamy, mu = lambdas(dt, dx, dy, chi_par)
     rc = _load().or_explicit_step(nx, ny, int(bc), _p(co.cxx), _p(co.cxy), _p(co.cyy), _p(co.cyx),
                                   lamx, lamy, mu, int(limiter), int(nsteps), _p(T))
+    if rc:
+        raise MemoryError("oracle scratch allocation failed")
+    return T
+
+
+# ------------------------------------------------------------ three dimensions
+
+SCHEME_2STEP = 0   # Eq. op_2step with a third factor: x, y, z updates
+SCHEME_4STEP = 1   # Eq. 4step with a third pair of factors
+
+
+class Coeffs3:
+    """The nine face coefficients of a 3-D grid in units of chi_par, each
+    [nz, ny, nx] with face f+1/2 along an axis stored at cell f:
+    x faces cxx, cxy, cxz; y faces cyy, cyz, cyx; z faces czz, czx, czy."""
+
+    NAMES = ("cxx", "cxy", "cxz", "cyy", "cyz", "cyx", "czz", "czx", "czy")
+
+    def __init__(self, arrays):
+        self.arrays = [_f64(a) for a in arrays]
+        for name, a in zip(self.NAMES, self.arrays):
+            setattr(self, name, a)
+
+    def _ptrs(self):
+        return (_D * 9)(*(_p(a) for a in self.arrays))
+
+
+def face_coeffs3(bx, by, bz, bc, chi_par=1.0, chi_perp=0.0) -> Coeffs3:
+    """Average the cell-centred unit field to the faces of a 3-D grid and form
+    the normal and the two transverse coefficients of each face."""
+    bx, by, bz = _f64(bx), _f64(by), _f64(bz)
+    nz, ny, nx = bx.shape
+    kappa = float(chi_perp) / float(chi_par)
+    out = [np.empty((nz, ny, nx)) for _ in range(9)]
+    c = Coeffs3(out)
+    _load().or3_face_coeffs(nx, ny, nz, int(bc), kappa, _p(bx), _p(by), _p(bz), c._ptrs())
+    return c
+
+
+def lambdas3(dt, dx, dy, dz, chi_par):
+    """(lam, mu): lam[d] = chi dt / Delta_d^2; mu[2d], mu[2d+1] = chi dt /
+    (Delta_d Delta_{d+1}), chi dt / (Delta_d Delta_{d+2}), axes cyclic."""
+    D = (dx, dy, dz)
+    lam = [chi_par * dt / (D[a] * D[a]) for a in range(3)]
+    mu = []
+    for a in range(3):
+        mu += [chi_par * dt / (D[a] * D[(a + 1) % 3]), chi_par * dt / (D[a] * D[(a + 2) % 3])]
+    return lam, mu
+
+
+def sweep3(T, co: Coeffs3, bc, axis, lam, mua, mub, limiter=LIM_VANLEER):
+    """One directional update along `axis` (0 = x, 1 = y, 2 = z) of T
+    [nz, ny, nx]: implicit in the face-normal flux, explicit and limited in
+    the two transverse ones."""
+    T = _f64(T)
+    nz, ny, nx = T.shape
+    out = np.empty_like(T)
+    cn, ca, cb = co.arrays[3 * axis: 3 * axis + 3]
+    _load().or3_sweep(nx, ny, nz, int(bc), int(axis), _p(cn), _p(ca), _p(cb), float(lam),
+                      float(mua), float(mub), int(limiter), _p(T), _p(out))
+    return out
+
+
+def step3(T, co: Coeffs3, bc, dt, dx, dy, dz, chi_par, nsteps=1, limiter=LIM_VANLEER,
+          scheme=SCHEME_2STEP):
+    """nsteps 3-D steps (x, y, z updates; SCHEME_4STEP takes each axis as a
+    half-coefficient update with the transverse terms followed by a purely
+    implicit half-coefficient update); returns a new FP64 array."""
+    T = _f64(T).copy()
+    nz, ny, nx = T.shape
+    lam, mu = lambdas3(dt, dx, dy, dz, chi_par)
+    lam_a, mu_a = np.array(lam, dtype=np.float64), np.array(mu, dtype=np.float64)
+    rc = _load().or3_step(nx, ny, nz, int(bc), co._ptrs(), _p(lam_a), _p(mu_a), int(limiter),
+                          int(scheme), int(nsteps), _p(T))
     if rc:
         raise MemoryError("oracle scratch allocation failed")
     return T

@@ -94,9 +94,9 @@ double or_limit4(int lim, double a, double b, double c, double d)
 
 /* ------------------------------------------------------ face coefficients */
 
-/* Cell-centred unit field b -> face coefficients (Section 2: "magnetic field
- * unit vectors are interpolated at the appropriate cell faces (simple
- * averaging)").  Arrays are [ny][nx], row-major, x fastest. */
+/* Cell-centred unit field b -> face coefficients (Section 2: the unit vector
+ * at a face is the plain mean of its two neighbouring cell centres).  Arrays
+ * are [ny][nx], row-major, x fastest. */
 void or_face_coeffs(int nx, int ny, int bc, double kappa, const double *bx, const double *by,
                     double *cxx, double *cxy, double *cyy, double *cyx)
 {

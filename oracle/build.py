@@ -10,21 +10,21 @@ import subprocess
 import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SRC = os.path.join(HERE, "aniso_oracle.c")
+SRCS = [os.path.join(HERE, "aniso_oracle.c"), os.path.join(HERE, "aniso3d_oracle.c")]
 LIB = os.path.join(HERE, "liboracle.so")
 
 
 def build(force: bool = False) -> str:
     if (not force and os.path.exists(LIB)
-            and os.path.getmtime(LIB) >= os.path.getmtime(SRC)):
+            and all(os.path.getmtime(LIB) >= os.path.getmtime(s) for s in SRCS)):
         return LIB
     base = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
             "-fno-fast-math", "-Wall"]
     tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = base + ["-fopenmp", SRC, "-o", tmp, "-lm"]
+    cmd = base + ["-fopenmp"] + SRCS + ["-o", tmp, "-lm"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:  # no OpenMP runtime: build single-threaded
-        cmd = base + [SRC, "-o", tmp, "-lm"]
+        cmd = base + SRCS + ["-o", tmp, "-lm"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("oracle build failed:\n" + r.stderr)
