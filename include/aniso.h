@@ -270,6 +270,47 @@ int aniso_step_noalloc(int nx, int ny, double dx, double dy, double chi_par, dou
                        int precision, const void *bx, const void *by, void *T, double dt, int nsteps,
                        void *stream);
 
+/* ------------------------------------------------------ three dimensions
+ *
+ * The split step on an nx * ny * nz grid (Section 2.1: three updates per
+ * step, each implicit in its face-normal flux and explicit in the two limited
+ * transverse fluxes, whose 2-step form is stable for chi dt / dx^2 up to
+ * about 8.25 with equal spacings; the 4-step form of Eq. 4step, with six
+ * half-coefficient line solves per step, at any timestep).
+ * Arrays are [nz][ny][nx], x fastest, device memory, element type of the
+ * handle's precision.  Every line length must be a multiple of the 16-byte
+ * vector (4 cells in FP32, 2 in FP64), at least two vectors, and at most
+ * 2048 cells in FP32 or 1024 in FP64 (with the default segment option);
+ * other shapes give ANISO_ERR_UNSUPPORTED at aniso3_set_field.
+ * Boundaries: ANISO_BC_ZEROFLUX or ANISO_BC_PERIODIC on all six faces.
+ * Status codes and aniso_last_error() as for the 2-D calls. */
+typedef struct aniso3_ctx *aniso3_t;
+
+/* Create a handle; arguments as aniso_create plus nz and dz.  Allocates
+ * nothing on the device.  Errors: ANISO_ERR_ARG. */
+int aniso3_create(int nx, int ny, int nz, double dx, double dy, double dz, double chi_par, double chi_perp,
+                  int bc, aniso3_t *out);
+/* Options: ANISO_OPT_PRECISION (before aniso3_set_field), LIMITER, SCHEME
+ * (ANISO_SCHEME_2STEP or _4STEP), STREAM, BLOCK_WARPS, SEGMENT.  The other
+ * keys accept only their default 0 (ANISO_ERR_UNSUPPORTED otherwise). */
+int aniso3_set_option(aniso3_t h, int key, long long value);
+/* Cell-centred unit field (device arrays, [nz][ny][nx]); the library averages
+ * it to the faces and keeps nine coefficient arrays plus two intermediates
+ * (11 arrays of the grid's size).  Errors: ANISO_ERR_ARG, _UNSUPPORTED
+ * (shape), _OOM, _CUDA. */
+int aniso3_set_field(aniso3_t h, const void *bx, const void *by, const void *bz);
+/* nsteps steps in place on T (device, [nz][ny][nx], 16-byte aligned), the
+ * updates in the order x, y, z.  Asynchronous on the handle's stream.
+ * Errors: ANISO_ERR_ARG, ANISO_ERR_STATE (no field), ANISO_ERR_CUDA. */
+int aniso3_step(aniso3_t h, void *T, double dt, int nsteps);
+/* FP64 sum, min, max and non-finite count of T; synchronises.  Also returns
+ * ANISO_ERR_NONFINITE if a step since the last check produced a NaN or
+ * infinity. */
+int aniso3_total(aniso3_t h, const void *T, double *sum, double *tmin, double *tmax, long long *nonfinite);
+/* Wait for the handle's stream; ANISO_ERR_NONFINITE as aniso3_total. */
+int aniso3_sync(aniso3_t h);
+void aniso3_destroy(aniso3_t h);
+
 #ifdef __cplusplus
 }
 #endif

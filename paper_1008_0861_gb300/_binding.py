@@ -56,7 +56,9 @@ EXPORTED = ("aniso_create", "aniso_set_option", "aniso_set_field", "aniso_step",
             "aniso_total", "aniso_get_state", "aniso_set_state", "aniso_sync",
             "aniso_kernel_times", "aniso_destroy", "aniso_last_error", "aniso_batch_create",
             "aniso_step_batched", "aniso_batch_destroy", "aniso_step_noalloc",
-            "aniso_batch_autotune", "aniso_autotune_candidate", "aniso_set_source")
+            "aniso_batch_autotune", "aniso_autotune_candidate", "aniso_set_source",
+            "aniso3_create", "aniso3_set_option", "aniso3_set_field", "aniso3_step",
+            "aniso3_total", "aniso3_sync", "aniso3_destroy")
 
 
 class AnisoError(RuntimeError):
@@ -99,6 +101,13 @@ def load():
         "aniso_batch_autotune": (i, [vp, P(vp), P(d), i, i, P(i), P(d)]),
         "aniso_autotune_candidate": (i, [i, P(i), P(i), P(i)]),
         "aniso_set_source": (i, [vp, vp]),
+        "aniso3_create": (i, [i, i, i, d, d, d, d, d, i, P(vp)]),
+        "aniso3_set_option": (i, [vp, i, ll]),
+        "aniso3_set_field": (i, [vp, vp, vp, vp]),
+        "aniso3_step": (i, [vp, vp, d, i]),
+        "aniso3_total": (i, [vp, vp, P(d), P(d), P(d), P(ll)]),
+        "aniso3_sync": (i, [vp]),
+        "aniso3_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -238,3 +247,41 @@ def aniso_step_noalloc(nx, ny, dx, dy, chi_par, chi_perp, bc, precision, bx, by,
     _check(load().aniso_step_noalloc(int(nx), int(ny), float(dx), float(dy), float(chi_par),
                                      float(chi_perp), int(bc), int(precision), _ptr(bx), _ptr(by),
                                      _ptr(T), float(dt), int(nsteps), _ptr(stream)))
+
+
+# ------------------------------------------------------ three dimensions
+
+def aniso3_create(nx, ny, nz, dx, dy, dz, chi_par, chi_perp=0.0, bc=ANISO_BC_PERIODIC):
+    h = ctypes.c_void_p()
+    _check(load().aniso3_create(int(nx), int(ny), int(nz), float(dx), float(dy), float(dz),
+                                float(chi_par), float(chi_perp), int(bc), ctypes.byref(h)))
+    return h
+
+
+def aniso3_set_option(h, key, value):
+    _check(load().aniso3_set_option(h, int(key), int(value)))
+
+
+def aniso3_set_field(h, bx, by, bz):
+    _check(load().aniso3_set_field(h, _ptr(bx), _ptr(by), _ptr(bz)))
+
+
+def aniso3_step(h, T, dt, nsteps=1):
+    _check(load().aniso3_step(h, _ptr(T), float(dt), int(nsteps)))
+
+
+def aniso3_total(h, T):
+    """(sum, min, max, nonfinite count) of T, FP64 sum."""
+    s, lo, hi, nf = ctypes.c_double(), ctypes.c_double(), ctypes.c_double(), ctypes.c_longlong()
+    _check(load().aniso3_total(h, _ptr(T), ctypes.byref(s), ctypes.byref(lo), ctypes.byref(hi),
+                               ctypes.byref(nf)))
+    return s.value, lo.value, hi.value, nf.value
+
+
+def aniso3_sync(h):
+    _check(load().aniso3_sync(h))
+
+
+def aniso3_destroy(h):
+    if h:
+        load().aniso3_destroy(h)

@@ -87,6 +87,13 @@ struct Line2Job {
     int team, lines_per_block;
     int transpose_out;
     int block0, nblocks;
+    // Three-dimensional lines (line4_kernel with D3): line l = kb * na + ka,
+    // its neighbours along the first transverse axis are l -+ 1 (ka -+ 1),
+    // along the second l -+ na (kb -+ 1); e2 and mu2 weight the limited
+    // difference along the second axis.  na = 0 for two-dimensional grids.
+    int na;
+    const void *e2;
+    double mu2;
 };
 struct Line2Args {
     const Line2Job *jobs;
@@ -161,6 +168,14 @@ bool line4_config(int prec, int n, bool transposed, int warps, int seg_chunks, i
                   int *nthreads, size_t *smem);
 cudaError_t launch_line4(int prec, int coef_fp16, const Line2Args &a, int nblocks, int nthreads,
                          size_t smem, cudaStream_t s);
+// Three-dimensional grids (kernels_3d.cu).  c[0..2] = x faces (normal, with
+// y, with z) in layout [nz][ny][nx]; c[3..5] = y faces (normal, with z, with
+// x) in [nx][nz][ny]; c[6..8] = z faces (normal, with x, with y) in
+// [ny][nx][nz].  bx, by, bz are [nz][ny][nx] in precision prec, as is c.
+cudaError_t launch_face_coeffs3(int prec, const void *bx, const void *by, const void *bz, int nx, int ny, int nz,
+                                int bc, double kappa, void *const c[9], cudaStream_t s);
+// line4_kernel with the second transverse term (jobs with na > 0).
+cudaError_t launch_line4_3d(int prec, const Line2Args &a, int nblocks, int nthreads, size_t smem, cudaStream_t s);
 void line_config(int prec, int n, int *team, int *lines_per_block, int *nthreads);
 size_t line_smem_bytes(int prec, int n, int team, int lines_per_block);
 void col_config(int prec, int ny, int *P, int *Wb, int *nthreads);

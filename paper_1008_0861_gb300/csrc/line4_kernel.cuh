@@ -28,6 +28,14 @@
 // FP32 reciprocals use the hardware approximation (rcp.approx.ftz.f32,
 // within 1 ulp); FP64 divides exactly.  Each block first asks for its input
 // rows to be brought into L2 with bulk prefetches.
+//
+// D3: the lines of a three-dimensional grid (Section 2.1).  The face flux
+// gains a second limited transverse term, mu2 * e2 * DeltaT-bar along the
+// second transverse axis, from the lines -+ na away; everything after the
+// flux is unchanged.  With lines along x indexed (z, y), the transposed
+// output is indexed (x, z, y): the next update's lines run along y, its
+// transverse axes are z then x, and its output (y, x, z) serves the
+// z-update, whose output is (z, y, x) again.
 #pragma once
 #include "line2_kernel.cuh"
 
@@ -114,7 +122,7 @@ template <typename R> __device__ __forceinline__ R pcr_team(Reduced<R> q, int t,
     return Fast<R>::div(q.Rr, q.L + q.D + q.U);
 }
 
-template <typename R, typename C, bool VL>
+template <typename R, typename C, bool VL, bool D3 = false>
 __global__ void __launch_bounds__(256, 2) line4_kernel(Line2Args args)
 {
     typedef typename V16<R>::T VT;
@@ -138,11 +146,21 @@ __global__ void __launch_bounds__(256, 2) line4_kernel(Line2Args args)
     int lu = lc + 1, ld = lc - 1;
     if (lu >= nl) lu = J.per_cross ? 0 : nl - 1;  // mirrored ghost line
     if (ld < 0) ld = J.per_cross ? nl - 1 : 0;
+    int lbu = lc, lbd = lc;  // neighbours along the second transverse axis (D3)
+    if constexpr (D3) {
+        const int na = J.na, nb = nl / na, ka = lc % na, kb = lc / na;
+        ld = ka > 0 ? lc - 1 : (J.per_cross ? lc + na - 1 : lc);
+        lu = ka < na - 1 ? lc + 1 : (J.per_cross ? lc - (na - 1) : lc);
+        lbd = kb > 0 ? lc - na : (J.per_cross ? lc + (nb - 1) * na : lc);
+        lbu = kb < nb - 1 ? lc + na : (J.per_cross ? lc - (nb - 1) * na : lc);
+    }
     const R *Tin = static_cast<const R *>(J.Tin);
     const R *rc = Tin + (size_t)lc * n, *ru = Tin + (size_t)lu * n, *rd = Tin + (size_t)ld * n;
+    const R *rbu = Tin + (size_t)lbu * n, *rbd = Tin + (size_t)lbd * n;
     const C *G = static_cast<const C *>(J.g) + (size_t)lc * n;
     const C *E = static_cast<const C *>(J.e) + (size_t)lc * n;
-    const R lam = (R)J.lam, mu = (R)J.mu;
+    const C *E2 = D3 ? static_cast<const C *>(J.e2) + (size_t)lc * n : E;
+    const R lam = (R)J.lam, mu = (R)J.mu, mu2 = (R)J.mu2;
     const unsigned full = 0xffffffffu;
 
     // The block's input rows (its lines and the two neighbouring lines of T,
@@ -154,6 +172,12 @@ __global__ void __launch_bounds__(256, 2) line4_kernel(Line2Args args)
         l2_prefetch(Tin + (size_t)f0 * n, (size_t)(f1 - f0) * n * sizeof(R));
         l2_prefetch(static_cast<const C *>(J.g) + (size_t)line0 * n, (size_t)(g1 - line0) * n * sizeof(C));
         l2_prefetch(static_cast<const C *>(J.e) + (size_t)line0 * n, (size_t)(g1 - line0) * n * sizeof(C));
+        if constexpr (D3) {
+            l2_prefetch(static_cast<const C *>(J.e2) + (size_t)line0 * n, (size_t)(g1 - line0) * n * sizeof(C));
+            // the block's neighbours along the second transverse axis, where not wrapped
+            if (line0 >= J.na) l2_prefetch(Tin + (size_t)(line0 - J.na) * n, (size_t)(g1 - line0) * n * sizeof(R));
+            if (g1 + J.na <= nl) l2_prefetch(Tin + (size_t)(line0 + J.na) * n, (size_t)(g1 - line0) * n * sizeof(R));
+        }
     }
 
     // segment of lane t: chunks [c_lo, c_lo + Ut); the first rr lanes one more
@@ -173,19 +197,33 @@ __global__ void __launch_bounds__(256, 2) line4_kernel(Line2Args args)
     {
         const VT *vd = reinterpret_cast<const VT *>(rd), *vc = reinterpret_cast<const VT *>(rc),
                  *vu = reinterpret_cast<const VT *>(ru);
+        const VT *vbd = reinterpret_cast<const VT *>(rbd), *vbu = reinterpret_cast<const VT *>(rbu);
         R Tcar = R(0), vcar = R(0);  // cell 0 of chunk (v+1)P, from the team's lane 0
+        R wcar = R(0);               // the same for the second transverse axis (D3)
         // the next round's loads are issued before this round's arithmetic
         int cl = min(((V - 1) << logP) + t, m - 1);
         VT xd = vd[cl], xc = vc[cl], xu = vu[cl];
         auto xg = ld_raw(G + cl * N), xe = ld_raw(E + cl * N);
+        VT xbd = xc, xbu = xc;
+        auto xe2 = xe;
+        if constexpr (D3) {
+            xbd = vbd[cl];
+            xbu = vbu[cl];
+            xe2 = ld_raw(E2 + cl * N);
+        }
         for (int v = V - 1; v >= 0; --v) {
             const int c = (v << logP) + t;
-            R Td[N], Tc[N], Tu[N], Gv[N], Ev[N];
+            R Td[N], Tc[N], Tu[N], Gv[N], Ev[N], Tbd[N], Tbu[N], E2v[N];
             V16<R>::unpack(xd, Td);
             V16<R>::unpack(xc, Tc);
             V16<R>::unpack(xu, Tu);
             unpack_raw(xg, Gv);
             unpack_raw(xe, Ev);
+            if constexpr (D3) {
+                V16<R>::unpack(xbd, Tbd);
+                V16<R>::unpack(xbu, Tbu);
+                unpack_raw(xe2, E2v);
+            }
             const int cur = cl;
             if (v > 0) {
                 cl = ((v - 1) << logP) + t;  // always < m
@@ -194,22 +232,36 @@ __global__ void __launch_bounds__(256, 2) line4_kernel(Line2Args args)
                 xu = vu[cl];
                 xg = ld_raw(G + cl * N);
                 xe = ld_raw(E + cl * N);
+                if constexpr (D3) {
+                    xbd = vbd[cl];
+                    xbu = vbu[cl];
+                    xe2 = ld_raw(E2 + cl * N);
+                }
             }
-            R vv[N];
+            R vv[N], ww[N];
 #pragma unroll
             for (int j = 0; j < N; ++j) vv[j] = level<R, VL>(lim, Tu[j] - Tc[j], Tc[j] - Td[j]);
+            if constexpr (D3) {
+#pragma unroll
+                for (int j = 0; j < N; ++j) ww[j] = level<R, VL>(lim, Tbu[j] - Tc[j], Tc[j] - Tbd[j]);
+            }
             R nT = __shfl_down_sync(full, Tc[0], 1, P), nv = __shfl_down_sync(full, vv[0], 1, P);
+            R nw = R(0);
+            if constexpr (D3) nw = __shfl_down_sync(full, ww[0], 1, P);
             if (t == P - 1) {
                 nT = Tcar;
                 nv = vcar;
+                nw = wcar;
             }
             if (cur == m - 1) {  // the cell after the line: periodic wrap or mirrored ghost
                 const int p1 = J.per_line ? 0 : n - 1;
                 nT = rc[p1];
                 nv = level<R, VL>(lim, ru[p1] - nT, nT - rd[p1]);
+                if constexpr (D3) nw = level<R, VL>(lim, rbu[p1] - nT, nT - rbd[p1]);
             }
             Tcar = __shfl_sync(full, Tc[0], 0, P);
             vcar = __shfl_sync(full, vv[0], 0, P);
+            if constexpr (D3) wcar = __shfl_sync(full, ww[0], 0, P);
             R F[N], lg[N];
 #pragma unroll
             for (int j = 0; j < N; ++j) {
@@ -217,6 +269,10 @@ __global__ void __launch_bounds__(256, 2) line4_kernel(Line2Args args)
                 const R vnx = j + 1 < N ? vv[j + 1] : nv;
                 lg[j] = lam * Gv[j];
                 F[j] = lg[j] * (Tnx - Tc[j]) + mu * Ev[j] * level<R, VL>(lim, vv[j], vnx);
+                if constexpr (D3) {
+                    const R wnx = j + 1 < N ? ww[j + 1] : nw;
+                    F[j] += mu2 * E2v[j] * level<R, VL>(lim, ww[j], wnx);
+                }
             }
             if (c < m) {
                 sA[swz(c)] = V16<R>::pack(F);

@@ -12,7 +12,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def _declared():
     src = open(os.path.join(ROOT, "include", "aniso.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(aniso_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(aniso3?_[a-z_]+)\s*\(", src)))
 
 
 @pytest.fixture(scope="module")
@@ -61,6 +61,40 @@ def test_create_validates_arguments(built):
         assert P.aniso_get_state(h) == 5
     finally:
         P.aniso_destroy(h)
+
+
+def test_create3_validates_arguments(built):
+    import paper_1008_0861_gb300 as P
+    bad = [dict(nx=2), dict(ny=2), dict(nz=2), dict(dx=0.0), dict(dz=-1.0), dict(chi_par=0.0),
+           dict(chi_perp=2.0), dict(bc=P.ANISO_BC_DIRICHLET)]
+    for kw in bad:
+        args = dict(nx=8, ny=8, nz=8, dx=1.0, dy=1.0, dz=1.0, chi_par=1.0, chi_perp=0.0, bc=1)
+        args.update(kw)
+        with pytest.raises(P.AnisoError) as ei:
+            P.aniso3_create(**args)
+        assert ei.value.code == P.ANISO_ERR_ARG, kw
+    h = P.aniso3_create(8, 12, 10, 1.0, 1.0, 1.0, 1.0)
+    try:
+        with pytest.raises(P.AnisoError) as ei:
+            P.aniso3_step(h, 0x1000, 1.0, 1)
+        assert ei.value.code == P.ANISO_ERR_STATE
+        with pytest.raises(P.AnisoError) as ei:
+            P.aniso3_set_option(h, P.ANISO_OPT_SCHEME, P.ANISO_SCHEME_EXPLICIT)
+        assert ei.value.code == P.ANISO_ERR_UNSUPPORTED
+        with pytest.raises(P.AnisoError) as ei:
+            P.aniso3_set_option(h, P.ANISO_OPT_KAHAN, 1)
+        assert ei.value.code == P.ANISO_ERR_UNSUPPORTED
+        with pytest.raises(P.AnisoError) as ei:
+            P.aniso3_set_option(h, 99, 0)
+        assert ei.value.code == P.ANISO_ERR_ARG
+        P.aniso3_set_option(h, P.ANISO_OPT_SCHEME, P.ANISO_SCHEME_4STEP)
+        P.aniso3_set_option(h, P.ANISO_OPT_PRECISION, P.ANISO_PREC_FP32)
+        # nz = 10 is not a multiple of the 4-cell FP32 vector: refused before any allocation
+        with pytest.raises(P.AnisoError) as ei:
+            P.aniso3_set_field(h, 0x1000, 0x1000, 0x1000)
+        assert ei.value.code == P.ANISO_ERR_UNSUPPORTED and "nz=10" in str(ei.value)
+    finally:
+        P.aniso3_destroy(h)
 
 
 def test_library_does_not_reference_the_oracle(built):

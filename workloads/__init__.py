@@ -16,6 +16,9 @@ Workloads (grid sizes and parameters are those of the benchmark suite):
              stream function psi with integer wavevectors 1<=|k|<=kmax,
              a_k ~ N(0,1)/|k|^2, phi_k ~ U[0,2pi); T = 1 + 16 Gaussians.
   batch    - many independent `random` instances of uneven sizes.
+  random3d - periodic [0,1)^3, b = B/|B| for B = z-hat + curl A with a random
+             vector potential A (integer wavevectors 1<=|k|<=kmax); T = 1 +
+             16 Gaussians (the paper gives no 3-D workload).
 """
 from .generators import (  # noqa: F401
     BASE_SEED,
@@ -26,4 +29,6 @@ from .generators import (  # noqa: F401
     batch_instances,
     sovinec_instance,
     cfl_dt,
+    Instance3,
+    random_instance3d,
 )

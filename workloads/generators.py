@@ -7,6 +7,10 @@ seed BASE_SEED + q.  Draw order within one instance:
   random field: for kx ascending, ky ascending over 1 <= kx^2+ky^2 <= kmax^2:
     a_k (normal / |k|^2), then phi_k (uniform * 2pi);
   Gaussians: for each of the 16: centre x, centre y, amplitude, width.
+Three-dimensional instances (random_instance3d): vector-potential
+coefficients for kx, ky, kz ascending over 1 <= |k|^2 <= kmax^2: the three
+amplitudes (normal / |k|^2), then phi_k (uniform * 2pi); then 16 Gaussians:
+centre x, y, z, amplitude, width.
 """
 from dataclasses import dataclass, field
 import math
@@ -220,3 +224,112 @@ def batch_instances(count: int = 512, nsteps: int = 200, base_seed: int = BASE_S
         out.append(random_instance(nx, ny, kmax=kmax, chi_par=chi, dt_factor=fac,
                                    nsteps=nsteps, rng=rng, name="batch%03d" % q))
     return out
+
+
+# ------------------------------------------------------------ three dimensions
+
+@dataclass
+class Instance3:
+    """One 3-D grid: cell-centred unit field (bx, by, bz), initial T, all
+    [nz][ny][nx], and parameters."""
+    name: str
+    nx: int
+    ny: int
+    nz: int
+    dx: float
+    dy: float
+    dz: float
+    bc: int            # 0 zero-flux, 1 periodic
+    chi_par: float
+    chi_perp: float
+    dt: float
+    nsteps: int
+    bx: np.ndarray = field(repr=False)
+    by: np.ndarray = field(repr=False)
+    bz: np.ndarray = field(repr=False)
+    T0: np.ndarray = field(repr=False)
+
+    @property
+    def cells(self) -> int:
+        return self.nx * self.ny * self.nz
+
+    def astype(self, dtype):
+        return Instance3(self.name, self.nx, self.ny, self.nz, self.dx, self.dy, self.dz, self.bc,
+                         self.chi_par, self.chi_perp, self.dt, self.nsteps, self.bx.astype(dtype),
+                         self.by.astype(dtype), self.bz.astype(dtype), self.T0.astype(dtype))
+
+
+def _field3d(rng: SplitMix64, nx: int, ny: int, nz: int, kmax: int, guide: float):
+    """b = B / |B| with B = guide * z-hat + curl A, A = sum_k a_k cos(2 pi k.x
+    + phi_k) (a_k a random vector), so B is divergence-free like a magnetic
+    field.  Cell centres ((i+1/2)/nx, ...), evaluated as a separable sum one
+    z-plane at a time."""
+    ks = np.arange(-kmax, kmax + 1)
+    nk = len(ks)
+    C = np.zeros((3, nk, nk, nk), dtype=np.complex128)   # B component, [kz, ky, kx]
+    for ix, kx in enumerate(ks):
+        for iy, ky in enumerate(ks):
+            for iz, kz in enumerate(ks):
+                k2 = kx * kx + ky * ky + kz * kz
+                if k2 < 1 or k2 > kmax * kmax:
+                    continue
+                a = rng.normal(3) / k2
+                phi = rng.uniform(1)[0] * 2.0 * math.pi
+                w = np.exp(1j * phi)
+                k = 2.0 * math.pi * np.array([kx, ky, kz], dtype=np.float64)
+                # curl of a cos(k.x + phi) = -(k x a) sin(k.x + phi) = Im(-(k x a) e^{i(.)})
+                C[:, iz, iy, ix] = -np.cross(k, a) * w
+    x = (np.arange(nx) + 0.5) / nx
+    y = (np.arange(ny) + 0.5) / ny
+    z = (np.arange(nz) + 0.5) / nz
+    X = np.exp(2j * math.pi * np.outer(x, ks))     # [nx, nk]
+    Y = np.exp(2j * math.pi * np.outer(y, ks))     # [ny, nk]
+    Z = np.exp(2j * math.pi * np.outer(z, ks))     # [nz, nk]
+    out = np.empty((3, nz, ny, nx))
+    for c in range(3):
+        CX = np.einsum("zyk,xk->zyx", C[c], X)     # [kz, ky, x]
+        for p in range(nz):
+            Cz = np.tensordot(Z[p], CX, axes=(0, 0))   # [ky, x]
+            out[c, p] = (Y @ Cz).imag                   # [y, x]
+    out[2] += guide
+    mag = np.sqrt(out[0] ** 2 + out[1] ** 2 + out[2] ** 2)
+    small = mag < 1e-8
+    safe = np.where(small, 1.0, mag)
+    bx = np.where(small, 0.0, out[0] / safe)
+    by = np.where(small, 0.0, out[1] / safe)
+    bz = np.where(small, 1.0, out[2] / safe)
+    return bx, by, bz
+
+
+def _gaussians3d(rng: SplitMix64, nx: int, ny: int, nz: int, count: int = 16):
+    """T = 1 + sum of `count` periodic Gaussians A exp(-r^2 / (2 w^2)) on the
+    unit torus (minimum-image distance), A in [0.5, 2], w in [0.02, 0.08]."""
+    x = (np.arange(nx) + 0.5) / nx
+    y = (np.arange(ny) + 0.5) / ny
+    z = (np.arange(nz) + 0.5) / nz
+    T = np.ones((nz, ny, nx))
+    for _ in range(count):
+        cx, cy, cz, ua, uw = rng.uniform(5)
+        amp = 0.5 + 1.5 * ua
+        w = 0.02 + 0.06 * uw
+        g = []
+        for v, c in ((x, cx), (y, cy), (z, cz)):
+            d = v - c
+            d -= np.round(d)
+            g.append(np.exp(-(d * d) / (2.0 * w * w)))
+        T += amp * g[2][:, None, None] * g[1][None, :, None] * g[0][None, None, :]
+    return T
+
+
+def random_instance3d(nx: int, ny: int, nz: int, seed: int = BASE_SEED, kmax: int = 3,
+                      guide: float = 1.0, chi_par: float = 0.05, dt_factor: float = 10.0,
+                      nsteps: int = 20, bc: int = 1, chi_perp: float = 0.0) -> Instance3:
+    """Random divergence-free field and Gaussian blobs on the unit cube;
+    dt = dt_factor * min(dx, dy, dz)^2 / (2 chi_par)."""
+    rng = SplitMix64(seed)
+    bx, by, bz = _field3d(rng, nx, ny, nz, kmax, guide)
+    T0 = _gaussians3d(rng, nx, ny, nz)
+    dx, dy, dz = 1.0 / nx, 1.0 / ny, 1.0 / nz
+    dt = dt_factor * min(dx, dy, dz) ** 2 / (2.0 * chi_par)
+    return Instance3("random3d_%dx%dx%d" % (nx, ny, nz), nx, ny, nz, dx, dy, dz, bc, chi_par,
+                     chi_perp, dt, nsteps, bx, by, bz, T0)
