@@ -53,6 +53,9 @@ def parse():
                     help="16-byte chunks per thread segment (0: library default)")
     ap.add_argument("--fast", type=int, default=-1,
                     help="ANISO_OPT_FAST_PATH value (-1: library default)")
+    ap.add_argument("--workload", default="batch", choices=["batch", "random3d"],
+                    help="batch: the 512-grid 2-D benchmark (default); random3d: one 256^3 "
+                         "grid of the three-dimensional split")
     return ap.parse_args()
 
 
@@ -94,7 +97,8 @@ def measured_peak():
 def kernel_source_hash():
     h = hashlib.sha256()
     for f in ("sweep_kernels.cuh", "line2_kernel.cuh", "line3_kernel.cuh", "line4_kernel.cuh",
-              "aniso_internal.h", "util_kernels.cu", "kernels_f32.cu", "kernels_line4.cu"):
+              "aniso_internal.h", "util_kernels.cu", "kernels_f32.cu", "kernels_line4.cu",
+              "kernels_3d.cu"):
         h.update(open(os.path.join(ROOT, "paper_1008_0861_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -294,10 +298,201 @@ def explicit_speedup(P, torch):
     return out
 
 
+# ------------------------------------------------------ three-dimensional workload
+
+W3_N = 256
+W3_STEPS_PER_CALL = 100
+W3_BYTES_PER_CELL_SWEEP = 20  # FP32: read T (4) + three face coefficients (12) + write T (4)
+WORKLOAD3 = ("one periodic 256^3 grid of the 3-D split (Section 2.1): b = B/|B|, B = z-hat + curl A "
+             "for a random vector potential (1 <= |k| <= 3), T = 1 + 16 Gaussians, FP32, 2-step "
+             "x,y,z updates, dt = 10 x min(dx)^2/(2 chi), 100 steps per call")
+
+
+def make_instance3d(rank=0):
+    import workloads as W
+    return W.random_instance3d(W3_N, W3_N, W3_N, seed=W.BASE_SEED + rank, dt_factor=10.0,
+                               nsteps=W3_STEPS_PER_CALL)
+
+
+def setup_3d(P, torch, inst):
+    h = P.aniso3_create(inst.nx, inst.ny, inst.nz, inst.dx, inst.dy, inst.dz, inst.chi_par,
+                        inst.chi_perp, inst.bc)
+    P.aniso3_set_option(h, P.ANISO_OPT_PRECISION, P.ANISO_PREC_FP32)
+    b = [torch.tensor(a, dtype=torch.float32, device="cuda") for a in (inst.bx, inst.by, inst.bz)]
+    P.aniso3_set_field(h, *b)
+    T = torch.tensor(inst.T0, dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    return h, T
+
+
+def time_3d(P, torch, h, T, inst, steps, warmup, clocks_gpu=None):
+    """Device time of `steps` aniso3_step calls after `warmup` calls.  The
+    step is three launches of the same line kernel over the same number of
+    cells, so a launch's average duration is the step time / 3."""
+    for _ in range(warmup):
+        P.aniso3_step(h, T, inst.dt, inst.nsteps)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clk = Clocks(clocks_gpu) if clocks_gpu is not None else None
+    if clk:
+        clk.__enter__()
+    e0.record(stream)
+    for _ in range(steps):
+        P.aniso3_step(h, T, inst.dt, inst.nsteps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if clk:
+        clk.__exit__()
+    ms_call = e0.elapsed_time(e1) / steps
+    return ms_call, ms_call / (3 * inst.nsteps), (clk.summary() if clk else None)
+
+
+def cpu_baseline_3d(inst, budget_s=12.0):
+    """The FP64 oracle, as it stands, on a bounded sample of the 3-D workload:
+    whole steps of the full grid until the time budget is used."""
+    import numpy as np
+    import oracle as O
+    w = lambda a: a.astype(np.float32).astype(np.float64)  # noqa: E731
+    co = O.face_coeffs3(w(inst.bx), w(inst.by), w(inst.bz), inst.bc, inst.chi_par)
+    T = w(inst.T0)
+    t0 = time.perf_counter()
+    k = 0
+    while True:
+        T = O.step3(T, co, inst.bc, inst.dt, inst.dx, inst.dy, inst.dz, inst.chi_par, nsteps=1)
+        k += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    el = time.perf_counter() - t0
+    return {"value": inst.cells * k / el / 1e9, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+            "sample": "%d full steps of the %dx%dx%d grid, FP64, %.1f s" % (k, inst.nx, inst.ny, inst.nz, el)}
+
+
+def summary_3d(P, torch):
+    """Short live measurement of the 3-D workload for the default line."""
+    inst = make_instance3d()
+    h, T = setup_3d(P, torch, inst)
+    try:
+        ms_call, launch_ms, _ = time_3d(P, torch, h, T, inst, steps=3, warmup=3)
+    finally:
+        P.aniso3_destroy(h)
+    peak, note = measured_peak()
+    achieved = W3_BYTES_PER_CELL_SWEEP * inst.cells / (launch_ms * 1e-3) / 1e9
+    return {"workload": WORKLOAD3, "value": inst.cells * inst.nsteps / (ms_call * 1e-3) / 1e9, "unit": UNIT,
+            "avg_launch_ms": launch_ms, "achieved_GBs": achieved, "frac": achieved / peak,
+            "peak_source": note, "traffic": ncu_traffic("sweep3d"),
+            "algorithmic_bytes_per_launch": W3_BYTES_PER_CELL_SWEEP * inst.cells}
+
+
+def main_3d(args):
+    """bench.py --workload random3d: one JSON line for the 3-D workload (one
+    bench step = one aniso3_step call of 100 steps)."""
+    import numpy as np
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_1008_0861_gb300 as P
+    P.load()
+    inst = make_instance3d(rank)
+    h, T = setup_3d(P, torch, inst)
+    T0 = T.clone()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    ms_call, launch_ms, clocks = time_3d(P, torch, h, T, inst, args.steps, args.warmup, clocks_gpu=local)
+    cell_steps = inst.cells * inst.nsteps
+    value, ms_step, _ = job_throughput(cell_steps, ms_call, "cuda")
+
+    # end to end: pinned host T in, one call, host T out
+    host = torch.empty(T.shape, dtype=torch.float32, pin_memory=True)
+    host.copy_(T)
+    stream = torch.cuda.current_stream()
+    e2e_steps = max(1, min(3, args.steps))
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        T.copy_(host, non_blocking=True)
+        P.aniso3_step(h, T, inst.dt, inst.nsteps)
+        host.copy_(T, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_value, _, _ = job_throughput(cell_steps, e0.elapsed_time(e1) / e2e_steps, "cuda")
+
+    peak, note = measured_peak()
+    achieved = W3_BYTES_PER_CELL_SWEEP * inst.cells / (launch_ms * 1e-3) / 1e9
+    line = {
+        "metric": "Gcell-steps/s, 3-D split step (Section 2.1), FP32; % HBM peak", "value": value,
+        "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD3, "cells_per_gpu": inst.cells, "steps_per_call": inst.nsteps,
+                   "l2": "inputs larger than L2: %.2f GB resident per GPU (T, 2 intermediates, 9 "
+                         "coefficient arrays)" % (inst.cells * 4 * 12 / 1e9),
+                   "parallelism": "one independent grid per GPU (no collective)"},
+        "roofline": {"bound": "hbm", "kernel": "sweep3d", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_source": note, "traffic": ncu_traffic("sweep3d"),
+                     "algorithmic_bytes_per_launch": W3_BYTES_PER_CELL_SWEEP * inst.cells,
+                     "avg_launch_ms": launch_ms},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": inst.cells * 4,
+                "d2h_bytes_per_step": inst.cells * 4},
+        "clocks": clocks,
+        "gpu_launches": 3 * inst.nsteps * args.steps,
+    }
+    if rank == 0:
+        import oracle as O
+        w = lambda a: a.astype(np.float32).astype(np.float64)  # noqa: E731
+        t = T0.clone()
+        P.aniso3_step(h, t, inst.dt, 1)
+        P.aniso3_sync(h)
+        co = O.face_coeffs3(w(inst.bx), w(inst.by), w(inst.bz), inst.bc, inst.chi_par)
+        ref = O.step3(T0.double().cpu().numpy(), co, inst.bc, inst.dt, inst.dx, inst.dy, inst.dz,
+                      inst.chi_par, nsteps=1)
+        got = t.double().cpu().numpy()
+        line["accuracy"] = {"rel_linf_vs_fp64_oracle": float(np.max(np.abs(got - ref)) / np.max(np.abs(ref))),
+                            "sample": "the whole grid after one step"}
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline_3d(inst)
+        print(json.dumps(line), flush=True)
+    P.aniso3_destroy(h)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def run_reference_3d(args):
+    rank, _, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle as O
+    inst = make_instance3d()
+    budget = max(2.0, 150.0 / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        cpu_baseline_3d(inst, budget_s=0.1)
+    runs = [cpu_baseline_3d(inst, budget_s=budget) for _ in range(args.steps)]
+    v = statistics.median(r["value"] for r in runs)
+    line = {"impl": "reference", "metric": "Gcell-steps/s, 3-D split step (Section 2.1), FP32; % HBM peak",
+            "value": v, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": inst.cells * inst.nsteps / (v * 1e9) * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD3},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+                             "sample": runs[0]["sample"]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
-        return run_reference(args)
+        return run_reference_3d(args) if args.workload == "random3d" else run_reference(args)
+    if args.workload == "random3d":
+        return main_3d(args)
     import numpy as np
     import torch
     rank, world, local = dist_env()
@@ -434,6 +629,7 @@ def main():
                             "sample": "instances 0-1, one 200-step call"}
         line["fp64_plain"] = fp64_plain_compare(P, torch)
         line["speedup_vs_explicit"] = explicit_speedup(P, torch)
+        line["three_d"] = summary_3d(P, torch)
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(insts)
         print(json.dumps(line), flush=True)
