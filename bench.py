@@ -131,7 +131,7 @@ class Clocks:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + q, "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
         return self
@@ -301,11 +301,11 @@ def explicit_speedup(P, torch):
 # ------------------------------------------------------ three-dimensional workload
 
 W3_N = 256
-W3_STEPS_PER_CALL = 100
+W3_STEPS_PER_CALL = 200
 W3_BYTES_PER_CELL_SWEEP = 20  # FP32: read T (4) + three face coefficients (12) + write T (4)
 WORKLOAD3 = ("one periodic 256^3 grid of the 3-D split (Section 2.1): b = B/|B|, B = z-hat + curl A "
              "for a random vector potential (1 <= |k| <= 3), T = 1 + 16 Gaussians, FP32, 2-step "
-             "x,y,z updates, dt = 10 x min(dx)^2/(2 chi), 100 steps per call")
+             "x,y,z updates, dt = 10 x min(dx)^2/(2 chi), 200 steps per call")
 
 
 def make_instance3d(rank=0):
@@ -386,7 +386,7 @@ def summary_3d(P, torch):
 
 def main_3d(args):
     """bench.py --workload random3d: one JSON line for the 3-D workload (one
-    bench step = one aniso3_step call of 100 steps)."""
+    bench step = one aniso3_step call of 200 steps)."""
     import numpy as np
     import torch
     rank, world, local = dist_env()

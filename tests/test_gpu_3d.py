@@ -202,3 +202,58 @@ def test_nonfinite_is_reported(lib):
         g.step(1)  # the flag was cleared; a clean step reports nothing
     finally:
         g.close()
+
+
+def test_zero_steps_leave_T_untouched(lib):
+    import torch
+    inst = _inst(8, 8, 8, 1, seed=21, nsteps=0)
+    g = Grid3(lib, inst, FP32)
+    try:
+        before = g.T.clone()
+        lib.aniso3_step(g.h, g.T, inst.dt, 0)
+        lib.aniso3_sync(g.h)
+        assert torch.equal(before, g.T)
+    finally:
+        g.close()
+
+
+@pytest.mark.parametrize("prec", [FP64, FP32])
+def test_constant_T_is_a_fixed_point(lib, prec):
+    """Uniform T: every difference is zero, so every update returns T."""
+    inst = _inst(16, 12, 8, 0, seed=22, nsteps=5)
+    inst.T0 = np.full_like(inst.T0, 3.25)
+    g = Grid3(lib, inst, prec)
+    try:
+        got = g.step(5)
+    finally:
+        g.close()
+    assert np.max(np.abs(got - 3.25)) <= (1e-15 if prec == FP64 else 2e-6) * 3.25
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_axis_aligned_field_fp64(lib, axis):
+    """b exactly along one axis: all transverse coefficients vanish and only
+    that axis diffuses (degenerate case of the limiter terms)."""
+    inst = _inst(12, 10, 8, 1, seed=23 + axis, nsteps=2)
+    b = [np.zeros_like(inst.bx) for _ in range(3)]
+    b[axis][:] = 1.0
+    inst.bx, inst.by, inst.bz = b
+    ref = oracle_run(inst, FP64, 2)
+    g = Grid3(lib, inst, FP64)
+    try:
+        got = g.step(2)
+    finally:
+        g.close()
+    assert rel_linf(got, ref) < 2 * FP64_TOL_PER_STEP
+
+
+def test_isotropic_limit_fp64(lib):
+    """chi_perp = chi_par: the tensor is chi I, the transverse terms vanish."""
+    inst = _inst(16, 8, 12, 0, seed=24, nsteps=3, chi_perp=0.05)
+    ref = oracle_run(inst, FP64, 3)
+    g = Grid3(lib, inst, FP64)
+    try:
+        got = g.step(3)
+    finally:
+        g.close()
+    assert rel_linf(got, ref) < 3 * FP64_TOL_PER_STEP
