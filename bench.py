@@ -607,7 +607,7 @@ def main():
         "e2e": {"value": e2e_value, "unit": UNIT,
                 "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes},
         "clocks": clk.summary(),
-        "gpu_launches": 2 * STEPS_PER_CALL * args.steps,
+        "gpu_launches": P.aniso_batch_kernel_count(batch) * args.steps,
     }
     if rank == 0:
         # accuracy of this workload (FP32) against the FP64 oracle on a sample

@@ -246,6 +246,12 @@ int aniso_batch_autotune(aniso_batch_t b, void *const *T, const double *dt, int 
 /* The autotuner's candidate `index`: fast-path option value, warps per block
  * (0 = default) and chunks per lane.  ANISO_ERR_ARG when out of range. */
 int aniso_autotune_candidate(int index, int *fast, int *warps, int *seg);
+/* Kernel launches in one aniso_step_batched call of the batch's current plan
+ * (the kernel nodes of its captured graph; 0 before the first call).  The
+ * plan splits each sweep's lines by the occupancy their shared memory allows
+ * and runs those launches concurrently, so a sweep can be several kernels.
+ * Errors: ANISO_ERR_ARG (null). */
+int aniso_batch_kernel_count(aniso_batch_t b, long long *kernels);
 
 /* aniso_step without any device allocation.  (No counterpart in the paper: it
  * exists for callers that are not allowed to allocate GPU memory, such as code

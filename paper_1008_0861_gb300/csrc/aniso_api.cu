@@ -872,6 +872,11 @@ struct aniso_batch {
     std::vector<int> g_pairs;
     int profile = 0;
     int use_graph = 1;
+    // concurrent branches of one sweep (line4 occupancy classes)
+    static constexpr int kSide = 4;
+    cudaStream_t side[kSide] = {};
+    cudaEvent_t fork_ev = nullptr, join_ev[kSide] = {};
+    long long kernels_per_call = 0;  // kernel nodes of the captured graph
 };
 
 extern "C" int aniso_batch_create(int n, const aniso_t *hs, aniso_batch_t *out)
@@ -925,6 +930,9 @@ static int batch_build(aniso_batch *b, void *const *T, const double *dt, const i
         int njobs, nblocks, nthreads;
         size_t smem;
         int work_off = 0;
+        // consecutive launches with the same group >= 0 run concurrently
+        // (one branch each) and are joined before the next launch
+        int group = -1;
         // kind 6: one grid's sweep captured on its own (columns above the
         // on-chip limit go through the transpose path)
         int inst = -1, dir = 0;
@@ -1004,9 +1012,15 @@ static int batch_build(aniso_batch *b, void *const *T, const double *dt, const i
         launches.push_back(L);
     };
 
-    // line4 jobs: one launch, NW-warp blocks, per-job team and lines per block;
-    // the block shape (warps, chunks per lane) is the first grid's, for all
+    // line4 jobs: NW-warp blocks, per-job team and lines per block; the block
+    // shape (warps, chunks per lane) is the first grid's, for all.  A launch's
+    // dynamic shared memory is that of its largest line, so short lines in the
+    // same launch would be held to the long lines' occupancy.  The jobs are
+    // therefore split by the resident blocks per SM their own shared memory
+    // allows (CUDA's occupancy calculator), one launch per class, and the
+    // classes of a sweep run concurrently (one graph branch each).
     int shape_rc = ANISO_OK;
+    int next_group = 0;
     auto add_line4 = [&](std::vector<Line2Job> &jobs, int kind_xy) {
         if (jobs.empty()) return;
         const int warps = b->hs[0]->l4_warps, seg = b->hs[0]->seg_chunks;
@@ -1021,24 +1035,47 @@ static int batch_build(aniso_batch *b, void *const *T, const double *dt, const i
             if (line4_config(prec, J.n, true, warps, seg, &J.team, &J.lines_per_block, &nt, &sm))
                 nthreads = std::max(nthreads, nt);
         }
-        int blocks = 0;
-        size_t smem = 0;
-        for (auto &J : jobs) {
+        std::vector<std::pair<int, size_t>> cls(jobs.size());  // (blocks per SM, own shared memory)
+        for (size_t k = 0; k < jobs.size(); ++k) {
+            Line2Job &J = jobs[k];
             int nt = 0;
             size_t sm = 0;
             if (!line4_config(prec, J.n, true, nthreads / 32, seg, &J.team, &J.lines_per_block, &nt, &sm) ||
                 nt != nthreads)
                 shape_rc = fail(ANISO_ERR_UNSUPPORTED, "batch: line length %d does not fit the block shape", J.n);
-            smem = std::max(smem, sm);
-            J.block0 = blocks;
-            J.nblocks = (J.nlines + J.lines_per_block - 1) / J.lines_per_block;
-            blocks += J.nblocks;
+            const int occ = line4_blocks_per_sm(prec, fp16, b->hs[0]->limiter, nthreads, sm);
+            cls[k] = {occ > 0 ? occ : 0, sm};
         }
-        Launch L{kind_xy == 0 ? 7 : 8, blob.size(), (int)jobs.size(), blocks, nthreads, smem};
-        const unsigned char *p = reinterpret_cast<const unsigned char *>(jobs.data());
-        blob.insert(blob.end(), p, p + jobs.size() * sizeof(Line2Job));
-        while (blob.size() % 16) blob.push_back(0);
-        launches.push_back(L);
+        // classes in ascending occupancy (largest lines first); at most
+        // 1 + kSide of them, the highest-occupancy ones merged
+        std::vector<int> occs;
+        for (auto &c : cls) occs.push_back(c.first);
+        std::sort(occs.begin(), occs.end());
+        occs.erase(std::unique(occs.begin(), occs.end()), occs.end());
+        while ((int)occs.size() > 1 + aniso_batch::kSide) occs.erase(occs.end() - 2);
+        const int group = occs.size() > 1 ? next_group++ : -1;
+        for (size_t ci = 0; ci < occs.size(); ++ci) {
+            const int lo = occs[ci], hi = ci + 1 < occs.size() ? occs[ci + 1] : 1 << 30;
+            std::vector<Line2Job> part;
+            size_t smem = 0;
+            int blocks = 0;
+            for (size_t k = 0; k < jobs.size(); ++k) {
+                if (cls[k].first < lo || cls[k].first >= hi) continue;
+                Line2Job J = jobs[k];
+                smem = std::max(smem, cls[k].second);
+                J.block0 = blocks;
+                J.nblocks = (J.nlines + J.lines_per_block - 1) / J.lines_per_block;
+                blocks += J.nblocks;
+                part.push_back(J);
+            }
+            if (part.empty()) continue;
+            Launch L{kind_xy == 0 ? 7 : 8, blob.size(), (int)part.size(), blocks, nthreads, smem};
+            L.group = group;
+            const unsigned char *p = reinterpret_cast<const unsigned char *>(part.data());
+            blob.insert(blob.end(), p, p + part.size() * sizeof(Line2Job));
+            while (blob.size() % 16) blob.push_back(0);
+            launches.push_back(L);
+        }
     };
 
     // line3 jobs: one launch per block size (normally a single launch)
@@ -1233,10 +1270,57 @@ static int batch_build(aniso_batch *b, void *const *T, const double *dt, const i
     if (!b->cap_stream) CU(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
     b->prof.next = b->prof.pool.size();
     b->g_pairs.clear();
+    if (!b->fork_ev) {  // branches of concurrent launches
+        CU(cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming));
+        for (int k = 0; k < aniso_batch::kSide; ++k) {
+            CU(cudaStreamCreateWithFlags(&b->side[k], cudaStreamNonBlocking));
+            CU(cudaEventCreateWithFlags(&b->join_ev[k], cudaEventDisableTiming));
+        }
+    }
     CU(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
     int rc = ANISO_OK;
     unsigned *err = b->hs[0]->err;
-    for (const Launch &L : launches) {
+    auto launch_one = [&](const Launch &L, cudaStream_t st) -> cudaError_t {
+        if (L.kind == 7 || L.kind == 8) {
+            Line2Args a{};
+            a.jobs = reinterpret_cast<const Line2Job *>(static_cast<unsigned char *>(b->d_jobs) + L.offset);
+            a.njobs = L.njobs;
+            a.limiter = b->hs[0]->limiter;
+            a.err = err;
+            return launch_line4(prec, fp16, a, L.nblocks, L.nthreads, L.smem, st);
+        } else if (L.kind >= 4) {
+            Line3Args a{};
+            a.jobs = reinterpret_cast<const Line3Job *>(static_cast<unsigned char *>(b->d_jobs) + L.offset);
+            a.njobs = L.njobs;
+            a.total_groups = L.nblocks;
+            a.work_off = L.work_off;
+            a.limiter = b->hs[0]->limiter;
+            a.err = err;
+            return launch_line3(prec, fp16, a, L.nthreads, L.smem, st);
+        } else if (L.kind >= 2) {
+            Line2Args a{};
+            a.jobs = reinterpret_cast<const Line2Job *>(static_cast<unsigned char *>(b->d_jobs) + L.offset);
+            a.njobs = L.njobs;
+            a.limiter = b->hs[0]->limiter;
+            a.err = err;
+            return launch_line2(prec, fp16, a, L.nblocks, L.nthreads, L.smem, st);
+        } else if (L.kind == 0) {
+            LineArgs a{};
+            a.jobs = reinterpret_cast<const LineJob *>(static_cast<unsigned char *>(b->d_jobs) + L.offset);
+            a.njobs = L.njobs;
+            a.limiter = b->hs[0]->limiter;
+            a.err = err;
+            return launch_line(prec, fp16, a, L.nblocks, L.nthreads, L.smem, st, b->hs[0]->kahan != 0);
+        }
+        ColArgs a{};
+        a.jobs = reinterpret_cast<const ColJob *>(static_cast<unsigned char *>(b->d_jobs) + L.offset);
+        a.njobs = L.njobs;
+        a.limiter = b->hs[0]->limiter;
+        a.err = err;
+        return launch_col(prec, fp16, a, L.nblocks, L.nthreads, L.smem, st, b->hs[0]->kahan != 0);
+    };
+    for (size_t i = 0; i < launches.size();) {
+        const Launch &L = launches[i];
         if (L.kind == 6) {
             aniso_ctx *h = b->hs[L.inst];
             const int saved = h->profile;  // these sweeps are not profiled inside the batch
@@ -1244,8 +1328,11 @@ static int batch_build(aniso_batch *b, void *const *T, const double *dt, const i
             rc = enqueue_sweep(h, L.dir, L.in, L.out, L.dt, b->cap_stream, nullptr, L.in_lo, L.out_lo);
             h->profile = saved;
             if (rc) break;
+            ++i;
             continue;
         }
+        size_t j = i + 1;  // [i, j): one concurrent group
+        while (L.group >= 0 && j < launches.size() && launches[j].group == L.group) ++j;
         int pidx = -1;
         if (b->profile) {
             pidx = b->prof.take((L.kind == 0 || L.kind == 2 || L.kind == 4 || L.kind == 7)
@@ -1257,44 +1344,20 @@ static int batch_build(aniso_batch *b, void *const *T, const double *dt, const i
                 break;
             }
         }
-        cudaError_t ce;
-        if (L.kind == 7 || L.kind == 8) {
-            Line2Args a{};
-            a.jobs = reinterpret_cast<const Line2Job *>(static_cast<unsigned char *>(b->d_jobs) + L.offset);
-            a.njobs = L.njobs;
-            a.limiter = b->hs[0]->limiter;
-            a.err = err;
-            ce = launch_line4(prec, fp16, a, L.nblocks, L.nthreads, L.smem, b->cap_stream);
-        } else if (L.kind >= 4) {
-            Line3Args a{};
-            a.jobs = reinterpret_cast<const Line3Job *>(static_cast<unsigned char *>(b->d_jobs) + L.offset);
-            a.njobs = L.njobs;
-            a.total_groups = L.nblocks;
-            a.work_off = L.work_off;
-            a.limiter = b->hs[0]->limiter;
-            a.err = err;
-            ce = launch_line3(prec, fp16, a, L.nthreads, L.smem, b->cap_stream);
-        } else if (L.kind >= 2) {
-            Line2Args a{};
-            a.jobs = reinterpret_cast<const Line2Job *>(static_cast<unsigned char *>(b->d_jobs) + L.offset);
-            a.njobs = L.njobs;
-            a.limiter = b->hs[0]->limiter;
-            a.err = err;
-            ce = launch_line2(prec, fp16, a, L.nblocks, L.nthreads, L.smem, b->cap_stream);
-        } else if (L.kind == 0) {
-            LineArgs a{};
-            a.jobs = reinterpret_cast<const LineJob *>(static_cast<unsigned char *>(b->d_jobs) + L.offset);
-            a.njobs = L.njobs;
-            a.limiter = b->hs[0]->limiter;
-            a.err = err;
-            ce = launch_line(prec, fp16, a, L.nblocks, L.nthreads, L.smem, b->cap_stream, b->hs[0]->kahan != 0);
+        cudaError_t ce = cudaSuccess;
+        if (j - i == 1) {
+            ce = launch_one(L, b->cap_stream);
         } else {
-            ColArgs a{};
-            a.jobs = reinterpret_cast<const ColJob *>(static_cast<unsigned char *>(b->d_jobs) + L.offset);
-            a.njobs = L.njobs;
-            a.limiter = b->hs[0]->limiter;
-            a.err = err;
-            ce = launch_col(prec, fp16, a, L.nblocks, L.nthreads, L.smem, b->cap_stream, b->hs[0]->kahan != 0);
+            ce = cudaEventRecord(b->fork_ev, b->cap_stream);
+            for (size_t k = i + 1; k < j && ce == cudaSuccess; ++k) {
+                cudaStream_t st = b->side[k - i - 1];
+                ce = cudaStreamWaitEvent(st, b->fork_ev, 0);
+                if (ce == cudaSuccess) ce = launch_one(launches[k], st);
+                if (ce == cudaSuccess) ce = cudaEventRecord(b->join_ev[k - i - 1], st);
+            }
+            if (ce == cudaSuccess) ce = launch_one(L, b->cap_stream);
+            for (size_t k = i + 1; k < j && ce == cudaSuccess; ++k)
+                ce = cudaStreamWaitEvent(b->cap_stream, b->join_ev[k - i - 1], 0);
         }
         if (ce != cudaSuccess) {
             rc = fail(ANISO_ERR_CUDA, "batched launch: %s", cudaGetErrorString(ce));
@@ -1308,6 +1371,7 @@ static int batch_build(aniso_batch *b, void *const *T, const double *dt, const i
             }
             b->g_pairs.push_back(pidx);
         }
+        i = j;
     }
     cudaGraph_t graph = nullptr;
     cudaError_t ce = cudaStreamEndCapture(b->cap_stream, &graph);
@@ -1316,6 +1380,19 @@ static int batch_build(aniso_batch *b, void *const *T, const double *dt, const i
         return rc;
     }
     if (ce != cudaSuccess) return fail(ANISO_ERR_CUDA, "batch capture: %s", cudaGetErrorString(ce));
+    {
+        size_t nn = 0;
+        b->kernels_per_call = 0;
+        if (cudaGraphGetNodes(graph, nullptr, &nn) == cudaSuccess && nn) {
+            std::vector<cudaGraphNode_t> nodes(nn);
+            if (cudaGraphGetNodes(graph, nodes.data(), &nn) == cudaSuccess)
+                for (size_t k = 0; k < nn; ++k) {
+                    cudaGraphNodeType t;
+                    if (cudaGraphNodeGetType(nodes[k], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel)
+                        ++b->kernels_per_call;
+                }
+        }
+    }
     ce = cudaGraphInstantiate(&b->gexec, graph, 0);
     cudaGraphDestroy(graph);
     if (ce != cudaSuccess) return fail(ANISO_ERR_CUDA, "batch instantiate: %s", cudaGetErrorString(ce));
@@ -1511,9 +1588,21 @@ extern "C" void aniso_batch_destroy(aniso_batch_t b)
     cudaStreamSynchronize(b->stream);
     batch_drop(b);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    for (int k = 0; k < aniso_batch::kSide; ++k) {
+        if (b->side[k]) cudaStreamDestroy(b->side[k]);
+        if (b->join_ev[k]) cudaEventDestroy(b->join_ev[k]);
+    }
+    if (b->fork_ev) cudaEventDestroy(b->fork_ev);
     if (b->d_jobs) cudaFree(b->d_jobs);
     b->prof.destroy();
     delete b;
+}
+
+extern "C" int aniso_batch_kernel_count(aniso_batch_t b, long long *kernels)
+{
+    if (!b || !kernels) return fail(ANISO_ERR_ARG, "aniso_batch_kernel_count: null argument");
+    *kernels = b->gexec ? b->kernels_per_call : 0;
+    return ANISO_OK;
 }
 
 extern "C" int aniso_kernel_times(aniso_t h, aniso_batch_t b, int kind, double *ms, long long *launches,

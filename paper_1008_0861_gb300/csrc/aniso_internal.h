@@ -168,6 +168,9 @@ bool line4_config(int prec, int n, bool transposed, int warps, int seg_chunks, i
                   int *nthreads, size_t *smem);
 cudaError_t launch_line4(int prec, int coef_fp16, const Line2Args &a, int nblocks, int nthreads,
                          size_t smem, cudaStream_t s);
+// Resident blocks per SM of the 2-D line4 kernel for that block size and
+// dynamic shared memory (CUDA's occupancy calculator), or -1.
+int line4_blocks_per_sm(int prec, int coef_fp16, int limiter, int nthreads, size_t smem);
 // Three-dimensional grids (kernels_3d.cu).  c[0..2] = x faces (normal, with
 // y, with z) in layout [nz][ny][nx]; c[3..5] = y faces (normal, with z, with
 // x) in [nx][nz][ny]; c[6..8] = z faces (normal, with x, with y) in

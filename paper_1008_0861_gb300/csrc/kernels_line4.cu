@@ -34,6 +34,33 @@ cudaError_t launch_line4(int prec, int coef_fp16, const Line2Args &a, int nblock
               : run4(line4_kernel<float, float, false>, a, nblocks, nthreads, smem, s);
 }
 
+template <typename K> static int occ4(K kern, int nthreads, size_t smem)
+{
+    if (smem > 47 * 1024) {
+        cudaFuncAttributes fa;
+        if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess) return -1;
+        if ((size_t)fa.maxDynamicSharedSizeBytes < smem &&
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+            return -1;
+    }
+    int blocks = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, nthreads, smem) != cudaSuccess) return -1;
+    return blocks;
+}
+
+int line4_blocks_per_sm(int prec, int coef_fp16, int limiter, int nthreads, size_t smem)
+{
+    const bool vl = limiter == LIM_VANLEER;
+    if (prec == PREC_FP64)
+        return vl ? occ4(line4_kernel<double, double, true>, nthreads, smem)
+                  : occ4(line4_kernel<double, double, false>, nthreads, smem);
+    if (coef_fp16)
+        return vl ? occ4(line4_kernel<float, __half, true>, nthreads, smem)
+                  : occ4(line4_kernel<float, __half, false>, nthreads, smem);
+    return vl ? occ4(line4_kernel<float, float, true>, nthreads, smem)
+              : occ4(line4_kernel<float, float, false>, nthreads, smem);
+}
+
 template <typename K> static cudaError_t run_explicit(K kern, const ExpArgs &a, cudaStream_t s)
 {
     const int rows_total = (a.ny + a.rows - 1) / a.rows;

@@ -122,13 +122,15 @@ template <typename R> __device__ __forceinline__ R pcr_team(Reduced<R> q, int t,
     return Fast<R>::div(q.Rr, q.L + q.D + q.U);
 }
 
-// The FP32 3-D form asks for three resident 256-thread blocks' worth of
-// registers per SM (at most 85 per thread instead of its unbounded 112: more
-// resident lines, +3 % measured despite a few spilled values); the others keep
-// two (the 2-D forms' occupancy is bounded by their shared line state, and
-// FP64 would spill more than it gains).
+// Register budgets.  The FP32 2-D form asks for four resident 256-thread
+// blocks' worth of registers per SM (at most 64 per thread, no spills): lines
+// short enough to need little shared memory then keep up to eight 128-thread
+// blocks per SM instead of five (+7 % on the uneven batch, whose launches are
+// split by occupancy).  The FP32 3-D form asks for three (80 registers
+// instead of 112, a few spilled values, +3 %).  FP64 keeps two: it would
+// spill more than it gains.
 template <typename R, typename C, bool VL, bool D3 = false>
-__global__ void __launch_bounds__(256, (D3 && sizeof(R) == 4) ? 3 : 2) line4_kernel(Line2Args args)
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? (D3 ? 3 : 4) : 2) line4_kernel(Line2Args args)
 {
     typedef typename V16<R>::T VT;
     constexpr int N = V16<R>::N;

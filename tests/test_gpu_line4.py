@@ -98,6 +98,38 @@ def test_line4_batched_fp64_matches_oracle(lib):
             g.close()
 
 
+@pytest.mark.parametrize("prec", [FP64, FP32])
+def test_line4_occupancy_split_batch(lib, prec):
+    """Line lengths from 64 to 1024 need very different shared memory, so the
+    plan splits each sweep into several concurrent launches (one per
+    occupancy class).  The kernel count says so, and every grid still matches
+    the oracle (FP64) or its own single-grid run bit for bit (FP32)."""
+    import torch
+    shapes = [(1024, 96), (64, 1024), (512, 128), (800, 160), (256, 64), (992, 32), (128, 256)]
+    insts = [W.random_instance(nx, ny, seed=31 + k, chi_par=0.05, dt_factor=100.0)
+             for k, (nx, ny) in enumerate(shapes)]
+    grids = [GpuGrid(lib, i, prec, fast=LINE4) for i in insts]
+    singles = [GpuGrid(lib, i, prec, fast=LINE4, graph=False) for i in insts]
+    try:
+        b = lib.aniso_batch_create([g.h for g in grids])
+        assert lib.aniso_batch_kernel_count(b) == 0
+        lib.aniso_step_batched(b, [g.T for g in grids], [i.dt for i in insts], [2] * len(insts))
+        torch.cuda.synchronize()
+        kernels = lib.aniso_batch_kernel_count(b)
+        assert 2 * 2 < kernels <= 2 * 2 * 5  # more than one launch per sweep, at most five
+        for g, s, inst in zip(grids, singles, insts):
+            got = g.T.double().cpu().numpy()
+            if prec == FP64:
+                T0, co = oracle_inputs(lib, inst, FP64)
+                assert rel_linf(got, oracle_step(inst, T0, co, 2)) < 2 * FP64_TOL_PER_STEP
+            else:
+                assert np.array_equal(got, s.step(2))
+        lib.aniso_batch_destroy(b)
+    finally:
+        for g in grids + singles:
+            g.close()
+
+
 def test_line4_nonfinite_flag(lib):
     inst = W.random_instance(256, 128, seed=9)
     T0 = inst.T0.copy()
