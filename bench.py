@@ -168,7 +168,7 @@ def make_instances(count, rank):
     return W.batch_instances(count, nsteps=STEPS_PER_CALL, first=rank * count)
 
 
-def cpu_baseline(insts, budget_s=12.0):
+def cpu_baseline(insts, budget_s=12.0, single_thread_s=0.0):
     """The FP64 oracle, as it stands, on a bounded sample of the workload:
     whole instances for their full 200 steps until the time budget is used."""
     import numpy as np
@@ -185,9 +185,28 @@ def cpu_baseline(insts, budget_s=12.0):
         if time.perf_counter() - t0 > budget_s:
             break
     el = time.perf_counter() - t0
-    return {"value": cells / el / 1e9, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
-            "sample": "%d of %d instances (%s..%s), full %d steps each, FP64, %.1f s" % (
-                len(used), len(insts), used[0], used[-1], STEPS_PER_CALL, el)}
+    out = {"value": cells / el / 1e9, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+           "sample": "%d of %d instances (%s..%s), full %d steps each, FP64, %.1f s" % (
+               len(used), len(insts), used[0], used[-1], STEPS_PER_CALL, el)}
+    if single_thread_s > 0:
+        # the same oracle on one thread, on the largest of the first eight instances
+        nt = O.num_threads()
+        O.set_num_threads(1)
+        try:
+            inst = max(insts[:8], key=lambda i: i.cells)
+            co = O.face_coeffs(w(inst.bx), w(inst.by), inst.bc, inst.chi_par)
+            t1 = time.perf_counter()
+            k = 0
+            T = w(inst.T0)
+            while time.perf_counter() - t1 < single_thread_s:
+                T = O.step(T, co, inst.bc, inst.dt, inst.dx, inst.dy, inst.chi_par, nsteps=5)
+                k += 5
+            el1 = time.perf_counter() - t1
+        finally:
+            O.set_num_threads(nt)
+        out["value_1_thread"] = inst.cells * k / el1 / 1e9
+        out["sample_1_thread"] = "%s, %d steps, 1 thread, %.1f s" % (inst.name, k, el1)
+    return out
 
 
 def run_reference(args):
@@ -253,6 +272,46 @@ def fp64_plain_compare(P, torch):
                 "rel_linf_vs_oracle": err}
     finally:
         P.aniso_destroy(h)
+
+
+def fp32_single(P, torch):
+    """The 4096^2 periodic random-field grid (|k| <= 8, 16 Gaussians, chi_par
+    0.05, dt = 100 x the explicit limit), FP32, 100 steps through aniso_step on
+    one handle: rate, rel L-inf against the FP64 oracle's full run, and the
+    drift of the FP64 sum of T."""
+    import numpy as np
+    import oracle as O
+    import workloads as W
+    inst = W.random_instance(4096, 4096, dt_factor=100.0, nsteps=100)
+    h = P.aniso_create(inst.nx, inst.ny, inst.dx, inst.dy, inst.chi_par, 0.0, inst.bc)
+    try:
+        P.aniso_set_option(h, P.ANISO_OPT_PRECISION, P.ANISO_PREC_FP32)
+        bx = torch.tensor(inst.bx, dtype=torch.float32, device="cuda")
+        by = torch.tensor(inst.by, dtype=torch.float32, device="cuda")
+        P.aniso_set_field(h, bx, by)
+        T0 = torch.tensor(inst.T0, dtype=torch.float32, device="cuda")
+        T = T0.clone()
+        P.aniso_step(h, T, inst.dt, inst.nsteps)  # builds the graph; warm-up
+        T.copy_(T0)
+        s0 = P.aniso_total(h, T)[0]
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        P.aniso_step(h, T, inst.dt, inst.nsteps)
+        e1.record()
+        P.aniso_sync(h)
+        ms = e0.elapsed_time(e1)
+        s1 = P.aniso_total(h, T)[0]
+        got = T.double().cpu().numpy()
+    finally:
+        P.aniso_destroy(h)
+    w = lambda a: a.astype(np.float32).astype(np.float64)  # noqa: E731
+    co = O.face_coeffs(w(inst.bx), w(inst.by), inst.bc, inst.chi_par)
+    ref = O.step(w(inst.T0), co, inst.bc, inst.dt, inst.dx, inst.dy, inst.chi_par, nsteps=inst.nsteps)
+    return {"workload": "random field 4096^2, FP32, 100 steps, one handle", "unit": UNIT,
+            "value": inst.cells * inst.nsteps / (ms * 1e-3) / 1e9,
+            "rel_linf_vs_fp64_oracle": float(np.max(np.abs(got - ref)) / np.max(np.abs(ref))),
+            "conservation_drift_fp32": abs(s1 - s0) / abs(s0)}
 
 
 def explicit_speedup(P, torch):
@@ -612,7 +671,7 @@ def main():
     if rank == 0:
         # accuracy of this workload (FP32) against the FP64 oracle on a sample
         import workloads as W  # noqa: F401
-        errs = []
+        errs, drifts = [], []
         for k in range(2):
             inst = insts[k]
             hT = T0_saved[k]
@@ -625,13 +684,17 @@ def main():
                          inst.chi_par, nsteps=STEPS_PER_CALL)
             got = t.double().cpu().numpy()
             errs.append(float(np.max(np.abs(got - ref)) / np.max(np.abs(ref))))
+            s0 = float(hT.double().sum())
+            drifts.append(abs(float(got.sum()) - s0) / abs(s0))
         line["accuracy"] = {"rel_linf_vs_fp64_oracle": max(errs),
+                            "conservation_drift_fp32": max(drifts),
                             "sample": "instances 0-1, one 200-step call"}
         line["fp64_plain"] = fp64_plain_compare(P, torch)
         line["speedup_vs_explicit"] = explicit_speedup(P, torch)
+        line["fp32_single"] = fp32_single(P, torch)
         line["three_d"] = summary_3d(P, torch)
         if not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(insts)
+            line["cpu_baseline"] = cpu_baseline(insts, single_thread_s=4.0)
         print(json.dumps(line), flush=True)
     P.aniso_batch_destroy(batch)
     for h in handles:

@@ -74,6 +74,8 @@ def _load():
         lib.or_totals.argtypes = [sz, _D, _D, _D, _D]
         lib.or_num_threads.restype = i
         lib.or_num_threads.argtypes = []
+        lib.or_set_num_threads.restype = None
+        lib.or_set_num_threads.argtypes = [i]
         _D9 = _D * 9
         lib.or3_face_coeffs.restype = None
         lib.or3_face_coeffs.argtypes = [i, i, i, i, d, _D, _D, _D, _D9]
@@ -96,6 +98,11 @@ def _p(a):
 def num_threads() -> int:
     """OpenMP threads the oracle uses (OMP_NUM_THREADS, else all cores)."""
     return int(_load().or_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    """Use n OpenMP threads from now on (results do not depend on it)."""
+    _load().or_set_num_threads(int(n))
 
 
 def limit4(a, b, c, d, limiter=LIM_VANLEER) -> float:

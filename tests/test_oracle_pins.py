@@ -580,3 +580,20 @@ def test_fixed_boundary_isotropic_steady_state_is_second_order():
         errs.append(abs(v - 1.0))
         assert np.all(T[0, :] == 0.0) and np.all(T[:, -1] == 0.0)
     assert 3.5 < errs[0] / errs[1] < 4.5 and 3.5 < errs[1] / errs[2] < 4.5
+
+
+
+def test_results_do_not_depend_on_the_thread_count():
+    # Every line is solved independently, so the OpenMP thread count cannot
+    # change a bit of the result.
+    inst = W.random_instance(96, 64, seed=4, dt_factor=300.0)
+    co = O.face_coeffs(inst.bx, inst.by, inst.bc, inst.chi_par)
+    nt = O.num_threads()
+    try:
+        O.set_num_threads(1)
+        one = O.step(inst.T0, co, inst.bc, inst.dt, inst.dx, inst.dy, inst.chi_par, nsteps=3)
+        O.set_num_threads(max(2, nt))
+        many = O.step(inst.T0, co, inst.bc, inst.dt, inst.dx, inst.dy, inst.chi_par, nsteps=3)
+    finally:
+        O.set_num_threads(nt)
+    assert np.array_equal(one, many)
