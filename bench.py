@@ -314,6 +314,45 @@ def fp32_single(P, torch):
             "conservation_drift_fp32": abs(s1 - s0) / abs(s0)}
 
 
+def nonlinear_single(P, torch):
+    """The temperature-dependent diffusivity (Section 3.3: chi_par (T/t_ref)^2.5,
+    harmonic face average): one 1024^2 periodic random-field grid, FP32, 100
+    steps at dt = 10 x the explicit limit of chi_par, with its rel L-inf
+    against the FP64 oracle's full run."""
+    import numpy as np
+    import oracle as O
+    import workloads as W
+    inst = W.random_instance(1024, 1024, dt_factor=10.0, nsteps=100)
+    h = P.aniso_create(inst.nx, inst.ny, inst.dx, inst.dy, inst.chi_par, 0.0, inst.bc)
+    try:
+        P.aniso_set_option(h, P.ANISO_OPT_PRECISION, P.ANISO_PREC_FP32)
+        P.aniso_set_nonlinear(h, 2.5, 1.0)
+        bx = torch.tensor(inst.bx, dtype=torch.float32, device="cuda")
+        by = torch.tensor(inst.by, dtype=torch.float32, device="cuda")
+        P.aniso_set_field(h, bx, by)
+        T0 = torch.tensor(inst.T0, dtype=torch.float32, device="cuda")
+        T = T0.clone()
+        P.aniso_step(h, T, inst.dt, inst.nsteps)  # builds the graph; warm-up
+        T.copy_(T0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        P.aniso_step(h, T, inst.dt, inst.nsteps)
+        e1.record()
+        P.aniso_sync(h)
+        ms = e0.elapsed_time(e1)
+        got = T.double().cpu().numpy()
+    finally:
+        P.aniso_destroy(h)
+    w = lambda a: a.astype(np.float32).astype(np.float64)  # noqa: E731
+    co = O.face_coeffs(w(inst.bx), w(inst.by), inst.bc, inst.chi_par)
+    ref = O.step_nl(w(inst.T0), co, inst.bc, inst.dt, inst.dx, inst.dy, inst.chi_par, 2.5, t_ref=1.0,
+                    nsteps=inst.nsteps)
+    return {"workload": "random field 1024^2, chi_par (T/1)^2.5, FP32, 100 steps, one handle", "unit": UNIT,
+            "value": inst.cells * inst.nsteps / (ms * 1e-3) / 1e9,
+            "rel_linf_vs_fp64_oracle": float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))}
+
+
 def explicit_speedup(P, torch):
     """The paper's speed-up claim (Section 3.1: the semi-implicit step at ncfl
     = 1000 against the explicit method at ncfl = 1): time to reach t = 20 on
@@ -692,6 +731,7 @@ def main():
         line["fp64_plain"] = fp64_plain_compare(P, torch)
         line["speedup_vs_explicit"] = explicit_speedup(P, torch)
         line["fp32_single"] = fp32_single(P, torch)
+        line["nonlinear_chi"] = nonlinear_single(P, torch)
         line["three_d"] = summary_3d(P, torch)
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(insts, single_thread_s=4.0)

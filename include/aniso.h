@@ -246,6 +246,19 @@ int aniso_batch_autotune(aniso_batch_t b, void *const *T, const double *dt, int 
 /* The autotuner's candidate `index`: fast-path option value, warps per block
  * (0 = default) and chunks per lane.  ANISO_ERR_ARG when out of range. */
 int aniso_autotune_candidate(int index, int *fast, int *warps, int *seg);
+/* Temperature-dependent diffusivity (Section 3.3 runs the method with chi_par
+ * proportional to T^(5/2)): chi_par becomes chi_par * (max(T,0)/t_ref)^alpha,
+ * taken at each face as the harmonic mean of the two cells' values, from the
+ * input of each directional update (T^n for the x-update, T* for the
+ * y-update); chi_perp scales alike.  alpha = 0 (the default) restores the
+ * constant diffusivity.  aniso_step then needs the 2-step x-then-y scheme on
+ * the line4 fast path (both line lengths multiples of the 16-byte vector and
+ * at most 2048), the plain state, an FP32 or FP64 field, and neither fixed
+ * boundaries nor a source; otherwise it returns ANISO_ERR_UNSUPPORTED, as do
+ * aniso_sweep and aniso_batch_create for such a handle.
+ * Errors: ANISO_ERR_ARG (alpha < 0, t_ref <= 0, not finite). */
+int aniso_set_nonlinear(aniso_t h, double alpha, double t_ref);
+
 /* Kernel launches in one aniso_step_batched call of the batch's current plan
  * (the kernel nodes of its captured graph; 0 before the first call).  The
  * plan splits each sweep's lines by the occupancy their shared memory allows

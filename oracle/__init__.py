@@ -6,7 +6,8 @@ the GPU library (``paper_1008_0861_gb300``) and imports nothing from it.
 
 The arithmetic lives in ``aniso_oracle.c`` (plain C, FP64, written from
 Section 2 of Sharma & Hammett, arXiv:1008.0861: Eqs. xup and yup, the limited
-face differences after them, Eq. vanLeer and Eq. op_2step) and, for the
+face differences after them, Eq. vanLeer and Eq. op_2step; the temperature-
+dependent diffusivity of Section 3.3 in ``or_step_nl``) and, for the
 three-dimensional form of Section 2.1, ``aniso3d_oracle.c``.  This module
 marshals numpy arrays to it, composes those sweeps into the 4-step scheme of
 Eq. 4step (step4), runs the explicit limited scheme built from the same face
@@ -17,9 +18,12 @@ to the implementation: rounding stored face coefficients to FP16 with numpy
 Parity pins: every function here is pinned by ``tests/test_oracle_pins.py``
 against closed forms (Eqs. amp1/amp2, the 1-D backward-Euler factor), dense
 linear algebra on tiny grids, conservation, the extremum property of the
-limiter (Section 3.1) and x/y transposition symmetry.  Unpinned: nothing in
-this module; the ring-test contour shapes and min-T time series of the
-paper's figures are printed only as plots and are not compared.
+limiter (Section 3.1) and x/y transposition symmetry; step3 by
+``tests/test_oracle3d_pins.py`` and step_nl by
+``tests/test_oracle_nonlinear_pins.py``.  Parity unpinned: which temperature
+feeds the y-update's face factor in step_nl (T*, the reading taken, or T^n:
+no pin tells them apart); the ring-test contour shapes and min-T time series
+of the paper's figures are printed only as plots and are not compared.
 """
 import ctypes
 
@@ -76,6 +80,8 @@ def _load():
         lib.or_num_threads.argtypes = []
         lib.or_set_num_threads.restype = None
         lib.or_set_num_threads.argtypes = [i]
+        lib.or_step_nl.restype = i
+        lib.or_step_nl.argtypes = [i, i, i, _D, _D, _D, _D, d, d, d, i, d, d, i, _D]
         _D9 = _D * 9
         lib.or3_face_coeffs.restype = None
         lib.or3_face_coeffs.argtypes = [i, i, i, i, d, _D, _D, _D, _D9]
@@ -240,6 +246,20 @@ def step4(T, co: Coeffs, bc, dt, dx, dy, chi_par, nsteps=1, step0=0,
         k = step0 + s
         x_first = order == ORDER_XY or (order == ORDER_ALTERNATE and k % 2 == 0)
         T = ypart(xpart(T)) if x_first else xpart(ypart(T))
+    return T
+
+
+def step_nl(T, co: Coeffs, bc, dt, dx, dy, chi_par, alpha, t_ref=1.0, nsteps=1, limiter=LIM_VANLEER):
+    """nsteps x-then-y steps with chi_par scaled by (max(T,0)/t_ref)^alpha at
+    each face: the harmonic mean of the two cells' values, from the input of
+    each directional update (Section 3.3 uses alpha = 5/2)."""
+    T = _f64(T).copy()
+    ny, nx = T.shape
+    lamx, lamy, mu = lambdas(dt, dx, dy, chi_par)
+    rc = _load().or_step_nl(nx, ny, int(bc), _p(co.cxx), _p(co.cxy), _p(co.cyy), _p(co.cyx),
+                            lamx, lamy, mu, int(limiter), float(alpha), float(t_ref), int(nsteps), _p(T))
+    if rc:
+        raise MemoryError("oracle scratch allocation failed")
     return T
 
 

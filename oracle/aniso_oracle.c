@@ -386,6 +386,72 @@ int or_step(int nx, int ny, int bc, const double *cxx, const double *cxy, const 
     return 0;
 }
 
+/* ------------------------------------------- temperature-dependent chi */
+
+/* Section 3.3 runs the method with chi_par proportional to T^(5/2), the
+ * diffusivity taken at each face from the current temperature by a harmonic
+ * average of the two cells beside it (the interpolation the paper's earlier
+ * work prescribes, Section 2).  Readings: chi(T) = chi_par (max(T,0)/t_ref)^alpha;
+ * "current" is the input of each directional update (T^n for the x-update,
+ * T* for the y-update), so each update stays linear in its unknown; the face
+ * factor multiplies the normal and the transverse coefficient alike (and so
+ * chi_perp scales with chi_par). */
+static double chi_ratio(double T, double alpha, double t_ref)
+{
+    return T > 0.0 ? pow(T / t_ref, alpha) : 0.0;
+}
+
+static double harmonic(double a, double b)
+{
+    return (a > 0.0 && b > 0.0) ? 2.0 * a * b / (a + b) : 0.0;
+}
+
+/* Face coefficients of one update scaled by the face factor of T: axis 0
+ * scales cxx, cxy at x faces (cells (i,j), (i+1,j)); axis 1 scales cyy, cyx
+ * at y faces (cells (i,j), (i,j+1)).  The neighbour index wraps; zero-flux
+ * boundary faces keep their zero coefficients. */
+void or_nl_coeffs(int nx, int ny, int axis, double alpha, double t_ref, const double *cn, const double *ct,
+                  const double *T, double *gn, double *gt)
+{
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            const size_t o = (size_t)j * nx + i;
+            const size_t o1 = axis == 0 ? (size_t)j * nx + (i + 1) % nx : (size_t)((j + 1) % ny) * nx + i;
+            const double h = harmonic(chi_ratio(T[o], alpha, t_ref), chi_ratio(T[o1], alpha, t_ref));
+            gn[o] = cn[o] * h;
+            gt[o] = ct[o] * h;
+        }
+}
+
+/* nsteps x-then-y steps (Eq. op_2step) in place on T with the face factor
+ * recomputed from each update's input.  Returns 0, or -1 on allocation
+ * failure. */
+int or_step_nl(int nx, int ny, int bc, const double *cxx, const double *cxy, const double *cyy,
+               const double *cyx, double lamx, double lamy, double mu, int lim, double alpha, double t_ref,
+               int nsteps, double *T)
+{
+    const size_t n = (size_t)nx * ny;
+    double *Ts = (double *)malloc(sizeof(double) * n);
+    double *g = (double *)malloc(sizeof(double) * n);
+    double *e = (double *)malloc(sizeof(double) * n);
+    if (!Ts || !g || !e) {
+        free(Ts);
+        free(g);
+        free(e);
+        return -1;
+    }
+    for (int s = 0; s < nsteps; ++s) {
+        or_nl_coeffs(nx, ny, 0, alpha, t_ref, cxx, cxy, T, g, e);
+        or_xsweep(nx, ny, bc, g, e, lamx, mu, lim, T, Ts);
+        or_nl_coeffs(nx, ny, 1, alpha, t_ref, cyy, cyx, Ts, g, e);
+        or_ysweep(nx, ny, bc, g, e, lamy, mu, lim, Ts, T);
+    }
+    free(Ts);
+    free(g);
+    free(e);
+    return 0;
+}
+
 /* ------------------------------------------------ explicit limited step */
 
 /* Flux through x face (i+1/2, j) of the explicit step: the normal part of

@@ -57,7 +57,7 @@ EXPORTED = ("aniso_create", "aniso_set_option", "aniso_set_field", "aniso_step",
             "aniso_kernel_times", "aniso_destroy", "aniso_last_error", "aniso_batch_create",
             "aniso_step_batched", "aniso_batch_destroy", "aniso_step_noalloc",
             "aniso_batch_autotune", "aniso_autotune_candidate", "aniso_set_source",
-            "aniso_batch_kernel_count",
+            "aniso_batch_kernel_count", "aniso_set_nonlinear",
             "aniso3_create", "aniso3_set_option", "aniso3_set_field", "aniso3_step",
             "aniso3_total", "aniso3_sync", "aniso3_destroy")
 
@@ -103,6 +103,7 @@ def load():
         "aniso_autotune_candidate": (i, [i, P(i), P(i), P(i)]),
         "aniso_set_source": (i, [vp, vp]),
         "aniso_batch_kernel_count": (i, [vp, P(ll)]),
+        "aniso_set_nonlinear": (i, [vp, d, d]),
         "aniso3_create": (i, [i, i, i, d, d, d, d, d, i, P(vp)]),
         "aniso3_set_option": (i, [vp, i, ll]),
         "aniso3_set_field": (i, [vp, vp, vp, vp]),
@@ -234,6 +235,11 @@ def aniso_set_source(h, Q):
     """Source term Q (device tensor [ny][nx], handle precision) applied as
     T += dt Q before every step; None removes it."""
     _check(load().aniso_set_source(h, _ptr(Q)))
+
+
+def aniso_set_nonlinear(h, alpha, t_ref=1.0):
+    """chi_par * (max(T,0)/t_ref)^alpha with harmonic face averaging (alpha = 0: off)."""
+    _check(load().aniso_set_nonlinear(h, float(alpha), float(t_ref)))
 
 
 def aniso_batch_kernel_count(batch):

@@ -107,6 +107,7 @@ struct aniso_ctx {
     double dx = 0, dy = 0, chi_par = 0, chi_perp = 0;
     int prec = PREC_FP64, field_fp16 = 0, kahan = 0, limiter = LIM_VANLEER, order = ANISO_ORDER_XY;
     int use_graph = 1, profile = 0, fast = 3, seg_chunks = 0, l4_warps = 0, scheme = 0;
+    double nl_alpha = 0, nl_tref = 1;  // temperature-dependent diffusivity (aniso_set_nonlinear)
     void *t4 = nullptr;  // intermediate of the 4-step scheme
     void *q = nullptr;   // source term (aniso_set_source), handle precision
     cudaStream_t stream = 0;
@@ -359,6 +360,10 @@ static int enqueue_line2(aniso_ctx *h, const void *in, void *out, const void *g,
     J.per_line = per_line;
     J.per_cross = per_cross;
     J.transpose_out = transposed ? 1 : 0;
+    if (v4 && h->nl_alpha != 0.0) {
+        J.chi_alpha = h->nl_alpha;
+        J.chi_itref = 1.0 / h->nl_tref;
+    }
     int nthreads;
     size_t smem;
     const bool ok = v4 ? line4_config(h->prec, n, transposed, h->l4_warps, h->seg_chunks, &J.team,
@@ -713,6 +718,31 @@ extern "C" int aniso_set_source(aniso_t h, const void *Q)
     return ANISO_OK;
 }
 
+extern "C" int aniso_set_nonlinear(aniso_t h, double alpha, double t_ref)
+{
+    if (!h) return fail(ANISO_ERR_ARG, "aniso_set_nonlinear: null handle");
+    if (!(alpha >= 0) || !(alpha < 1e3) || !(t_ref > 0) || !(t_ref < 1e300))
+        return fail(ANISO_ERR_ARG, "aniso_set_nonlinear: need 0 <= alpha and t_ref > 0 (finite)");
+    h->nl_alpha = alpha;
+    h->nl_tref = t_ref;
+    drop_graph(h);
+    return ANISO_OK;
+}
+
+// What the temperature-dependent diffusivity runs on: the line4 fast path of
+// the x-then-y 2-step scheme on the plain state.
+static int check_nonlinear(aniso_ctx *h, const void *T, const char *who)
+{
+    if (h->nl_alpha == 0.0) return ANISO_OK;
+    if (h->scheme != ANISO_SCHEME_2STEP || h->kahan || h->dirichlet() || h->q || h->field_fp16 ||
+        h->order != ANISO_ORDER_XY || !use_fast(h, T) || h->fast_kind() != 4)
+        return fail(ANISO_ERR_UNSUPPORTED,
+                    "%s: the temperature-dependent diffusivity needs the 2-step x-then-y scheme on the "
+                    "line4 fast path (both line lengths multiples of the 16-byte vector, at most 2048; "
+                    "plain state, FP32 or FP64 field, no fixed boundary or source)", who);
+    return ANISO_OK;
+}
+
 extern "C" int aniso_step(aniso_t h, void *T, double dt, int nsteps)
 {
     TraceRange trace("aniso_step");
@@ -721,6 +751,7 @@ extern "C" int aniso_step(aniso_t h, void *T, double dt, int nsteps)
     if (!T) return fail(ANISO_ERR_ARG, "aniso_step: T is NULL");
     if (!(dt > 0)) return fail(ANISO_ERR_ARG, "aniso_step: dt must be > 0");
     if (nsteps < 0) return fail(ANISO_ERR_ARG, "aniso_step: nsteps must be >= 0");
+    if ((rc = check_nonlinear(h, T, "aniso_step"))) return rc;
     if (nsteps == 0) return ANISO_OK;
     const int parity = h->order == ANISO_ORDER_ALTERNATE ? (int)(h->step_counter & 1) : 0;
     if (h->use_graph && nsteps >= 2) {
@@ -782,6 +813,8 @@ extern "C" int aniso_sweep(aniso_t h, int dir, const void *Tin, void *Tout, doub
     if (!Tin || !Tout || Tin == Tout) return fail(ANISO_ERR_ARG, "aniso_sweep: need distinct Tin, Tout");
     if (dir != ANISO_DIR_X && dir != ANISO_DIR_Y) return fail(ANISO_ERR_ARG, "aniso_sweep: bad direction");
     if (!(dt > 0)) return fail(ANISO_ERR_ARG, "aniso_sweep: dt must be > 0");
+    if (h->nl_alpha != 0.0)
+        return fail(ANISO_ERR_UNSUPPORTED, "aniso_sweep: not with the temperature-dependent diffusivity");
     return enqueue_sweep(h, dir, Tin, Tout, dt, h->stream, nullptr);
 }
 
@@ -895,6 +928,8 @@ extern "C" int aniso_batch_create(int n, const aniso_t *hs, aniso_batch_t *out)
             return fail(ANISO_ERR_UNSUPPORTED, "aniso_batch_create: handle %d runs another scheme than Eq. op_2step", k);
         if (h->dirichlet() || h->q)
             return fail(ANISO_ERR_UNSUPPORTED, "aniso_batch_create: handle %d has fixed boundaries or a source", k);
+        if (h->nl_alpha != 0.0)
+            return fail(ANISO_ERR_UNSUPPORTED, "aniso_batch_create: handle %d has a temperature-dependent diffusivity", k);
     }
     aniso_batch *b = new aniso_batch;
     b->hs.assign(hs, hs + n);

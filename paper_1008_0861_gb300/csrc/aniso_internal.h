@@ -94,6 +94,10 @@ struct Line2Job {
     int na;
     const void *e2;
     double mu2;
+    // Temperature-dependent diffusivity (line4_kernel with NL): the face
+    // coefficients are scaled by the harmonic mean of (max(T,0) * chi_itref)^
+    // chi_alpha over the two cells beside the face, T the update's input.
+    double chi_alpha, chi_itref;
 };
 struct Line2Args {
     const Line2Job *jobs;

@@ -24,6 +24,14 @@ cudaError_t launch_line4(int prec, int coef_fp16, const Line2Args &a, int nblock
                          cudaStream_t s)
 {
     const bool vl = a.limiter == LIM_VANLEER;
+    if (!a.jobs && a.one.chi_alpha != 0.0) {  // temperature-dependent diffusivity (single grids)
+        if (coef_fp16) return cudaErrorInvalidValue;
+        if (prec == PREC_FP64)
+            return vl ? run4(line4_kernel<double, double, true, false, true>, a, nblocks, nthreads, smem, s)
+                      : run4(line4_kernel<double, double, false, false, true>, a, nblocks, nthreads, smem, s);
+        return vl ? run4(line4_kernel<float, float, true, false, true>, a, nblocks, nthreads, smem, s)
+                  : run4(line4_kernel<float, float, false, false, true>, a, nblocks, nthreads, smem, s);
+    }
     if (prec == PREC_FP64)
         return vl ? run4(line4_kernel<double, double, true>, a, nblocks, nthreads, smem, s)
                   : run4(line4_kernel<double, double, false>, a, nblocks, nthreads, smem, s);

@@ -129,7 +129,19 @@ template <typename R> __device__ __forceinline__ R pcr_team(Reduced<R> q, int t,
 // split by occupancy).  The FP32 3-D form asks for three (80 registers
 // instead of 112, a few spilled values, +3 %).  FP64 keeps two: it would
 // spill more than it gains.
-template <typename R, typename C, bool VL, bool D3 = false>
+// NL: temperature-dependent diffusivity (Section 3.3): every face's
+// coefficients (normal and transverse) are scaled by the harmonic mean of
+// chi(T) = (max(T,0)/t_ref)^alpha over the face's two cells, from this
+// update's input T.
+template <typename R> __device__ __forceinline__ R chi_pow(R x, R a);
+template <> __device__ __forceinline__ float chi_pow<float>(float x, float a) { return __powf(x, a); }
+template <> __device__ __forceinline__ double chi_pow<double>(double x, double a) { return pow(x, a); }
+template <typename R> __device__ __forceinline__ R face_harmonic(R a, R b)
+{
+    return (a > R(0) && b > R(0)) ? R(2) * a * Fast<R>::div(b, a + b) : R(0);
+}
+
+template <typename R, typename C, bool VL, bool D3 = false, bool NL = false>
 __global__ void __launch_bounds__(256, sizeof(R) == 4 ? (D3 ? 3 : 4) : 2) line4_kernel(Line2Args args)
 {
     typedef typename V16<R>::T VT;
@@ -168,6 +180,8 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? (D3 ? 3 : 4) : 2) line4_
     const C *E = static_cast<const C *>(J.e) + (size_t)lc * n;
     const C *E2 = D3 ? static_cast<const C *>(J.e2) + (size_t)lc * n : E;
     const R lam = (R)J.lam, mu = (R)J.mu, mu2 = (R)J.mu2;
+    const R chi_a = (R)J.chi_alpha, chi_it = (R)J.chi_itref;
+    auto chi_of = [chi_a, chi_it](R T_) { return T_ > R(0) ? chi_pow<R>(T_ * chi_it, chi_a) : R(0); };
     const unsigned full = 0xffffffffu;
 
     // The block's input rows (its lines and the two neighbouring lines of T,
@@ -269,16 +283,25 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? (D3 ? 3 : 4) : 2) line4_
             Tcar = __shfl_sync(full, Tc[0], 0, P);
             vcar = __shfl_sync(full, vv[0], 0, P);
             if constexpr (D3) wcar = __shfl_sync(full, ww[0], 0, P);
-            R F[N], lg[N];
+            R F[N], lg[N], hf[N];
+            if constexpr (NL) {
+                R ch[N + 1];
+#pragma unroll
+                for (int j = 0; j < N; ++j) ch[j] = chi_of(Tc[j]);
+                ch[N] = chi_of(nT);
+#pragma unroll
+                for (int j = 0; j < N; ++j) hf[j] = face_harmonic<R>(ch[j], ch[j + 1]);
+            }
 #pragma unroll
             for (int j = 0; j < N; ++j) {
                 const R Tnx = j + 1 < N ? Tc[j + 1] : nT;
                 const R vnx = j + 1 < N ? vv[j + 1] : nv;
-                lg[j] = lam * Gv[j];
-                F[j] = lg[j] * (Tnx - Tc[j]) + mu * Ev[j] * level<R, VL>(lim, vv[j], vnx);
+                const R gj = NL ? Gv[j] * hf[j] : Gv[j], ej = NL ? Ev[j] * hf[j] : Ev[j];
+                lg[j] = lam * gj;
+                F[j] = lg[j] * (Tnx - Tc[j]) + mu * ej * level<R, VL>(lim, vv[j], vnx);
                 if constexpr (D3) {
                     const R wnx = j + 1 < N ? ww[j + 1] : nw;
-                    F[j] += mu2 * E2v[j] * level<R, VL>(lim, ww[j], wnx);
+                    F[j] += mu2 * (NL ? E2v[j] * hf[j] : E2v[j]) * level<R, VL>(lim, ww[j], wnx);
                 }
             }
             if (c < m) {

@@ -56,6 +56,12 @@ def test_create_validates_arguments(built):
         with pytest.raises(P.AnisoError) as ei:
             P.aniso_set_option(h, 99, 0)
         assert ei.value.code == P.ANISO_ERR_ARG
+        for a, t in ((-1.0, 1.0), (2.5, 0.0), (float("nan"), 1.0), (2.5, float("inf"))):
+            with pytest.raises(P.AnisoError) as ei:
+                P.aniso_set_nonlinear(h, a, t)
+            assert ei.value.code == P.ANISO_ERR_ARG
+        P.aniso_set_nonlinear(h, 2.5, 1.0)
+        P.aniso_set_nonlinear(h, 0.0, 1.0)
         P.aniso_set_option(h, P.ANISO_OPT_ORDER, P.ANISO_ORDER_ALTERNATE)
         P.aniso_set_state(h, 5)
         assert P.aniso_get_state(h) == 5
