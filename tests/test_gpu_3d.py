@@ -257,3 +257,37 @@ def test_isotropic_limit_fp64(lib):
     finally:
         g.close()
     assert rel_linf(got, ref) < 3 * FP64_TOL_PER_STEP
+
+
+def test_stability_limit_on_the_gpu(lib):
+    """The paper's 3-D stability limit of the 2-step scheme (chi dt / dx^2 <=
+    8.25, Section 2.1) on the GPU: with the linear (arithmetic-mean) average,
+    the worst mode of a 28 x 12 x 12 periodic grid grows by the closed-form
+    factor at 8.3 and the L2 norm of a random state does not grow at 8.2."""
+    import math
+    from test_oracle3d_pins import _GRID, _grid_modes, _mode, _worst
+    K = _grid_modes(_GRID)
+    r_hi, b, idx = _worst(8.3, K)
+    nz, ny, nx = _GRID
+    T, _ = _mode(_GRID, (idx[0] + 1, idx[1] + 1, idx[2] + 1))
+    ones = np.ones(_GRID)
+
+    def run(T0, lam, steps):
+        inst = W.Instance3("stability", nx, ny, nz, 1.0, 1.0, 1.0, 1, 1.0, 0.0, lam, steps,
+                           b[0] * ones, b[1] * ones, b[2] * ones, T0)
+        g = Grid3(lib, inst, FP64, limiter=1)
+        try:
+            return g.step(steps)
+        finally:
+            g.close()
+
+    T1 = run(T, 8.3, 1)
+    ratio = float(np.sum(T1 * T) / np.sum(T * T))
+    assert r_hi > 1.0 + 1e-4
+    assert abs(ratio) == pytest.approx(r_hi, rel=1e-10)
+    rng = np.random.default_rng(5)
+    U = rng.normal(size=_GRID)
+    n0 = np.linalg.norm(U)
+    U5 = run(U, 8.2, 5)
+    assert np.linalg.norm(U5) <= n0 * (1 + 1e-12)
+    assert math.isfinite(float(np.linalg.norm(U5)))
