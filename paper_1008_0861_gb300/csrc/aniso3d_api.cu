@@ -16,27 +16,9 @@
 
 #include "../../include/aniso.h"
 #include "aniso_internal.h"
+#include "status.h"
 
 using namespace aniso;
-
-static int fail3(int code, const char *fmt, ...)
-{
-    char buf[512];
-    va_list ap;
-    va_start(ap, fmt);
-    vsnprintf(buf, sizeof buf, fmt, ap);
-    va_end(ap);
-    record_error(buf);
-    return code;
-}
-
-#define CU3(call)                                                                           \
-    do {                                                                                    \
-        cudaError_t e_ = (call);                                                            \
-        if (e_ != cudaSuccess)                                                              \
-            return fail3(e_ == cudaErrorMemoryAllocation ? ANISO_ERR_OOM : ANISO_ERR_CUDA, \
-                         "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
-    } while (0)
 
 struct aniso3_ctx {
     int n[3] = {0, 0, 0};
@@ -77,7 +59,7 @@ static int check_shape(const aniso3_ctx *h, const char *who)
         int team, lpb, nt;
         size_t smem;
         if (!line4_config(h->prec, h->n[a], true, h->warps, h->seg, &team, &lpb, &nt, &smem))
-            return fail3(ANISO_ERR_UNSUPPORTED,
+            return fail(ANISO_ERR_UNSUPPORTED,
                          "%s: n%c=%d is not a line length the 3-D kernel takes (a multiple of %d, from %d to %d)",
                          who, names[a], h->n[a], h->prec == PREC_FP64 ? 2 : 4, h->prec == PREC_FP64 ? 4 : 8,
                          h->prec == PREC_FP64 ? 1024 : MAX_LINE2_TRANSPOSED);
@@ -88,16 +70,16 @@ static int check_shape(const aniso3_ctx *h, const char *who)
 extern "C" int aniso3_create(int nx, int ny, int nz, double dx, double dy, double dz, double chi_par, double chi_perp,
                              int bc, aniso3_t *out)
 {
-    if (!out) return fail3(ANISO_ERR_ARG, "aniso3_create: out is NULL");
+    if (!out) return fail(ANISO_ERR_ARG, "aniso3_create: out is NULL");
     *out = nullptr;
     if (nx < 3 || ny < 3 || nz < 3)
-        return fail3(ANISO_ERR_ARG, "aniso3_create: nx=%d ny=%d nz=%d (need >= 3)", nx, ny, nz);
-    if (!(dx > 0) || !(dy > 0) || !(dz > 0)) return fail3(ANISO_ERR_ARG, "aniso3_create: dx, dy, dz must be > 0");
-    if (!(chi_par > 0)) return fail3(ANISO_ERR_ARG, "aniso3_create: chi_par must be > 0");
+        return fail(ANISO_ERR_ARG, "aniso3_create: nx=%d ny=%d nz=%d (need >= 3)", nx, ny, nz);
+    if (!(dx > 0) || !(dy > 0) || !(dz > 0)) return fail(ANISO_ERR_ARG, "aniso3_create: dx, dy, dz must be > 0");
+    if (!(chi_par > 0)) return fail(ANISO_ERR_ARG, "aniso3_create: chi_par must be > 0");
     if (!(chi_perp >= 0) || chi_perp > chi_par)
-        return fail3(ANISO_ERR_ARG, "aniso3_create: need 0 <= chi_perp <= chi_par");
+        return fail(ANISO_ERR_ARG, "aniso3_create: need 0 <= chi_perp <= chi_par");
     if (bc != ANISO_BC_ZEROFLUX && bc != ANISO_BC_PERIODIC)
-        return fail3(ANISO_ERR_ARG, "aniso3_create: boundary condition %d (zero-flux or periodic)", bc);
+        return fail(ANISO_ERR_ARG, "aniso3_create: boundary condition %d (zero-flux or periodic)", bc);
     aniso3_ctx *h = new aniso3_ctx;
     h->n[0] = nx;
     h->n[1] = ny;
@@ -114,32 +96,32 @@ extern "C" int aniso3_create(int nx, int ny, int nz, double dx, double dy, doubl
 
 extern "C" int aniso3_set_option(aniso3_t h, int key, long long v)
 {
-    if (!h) return fail3(ANISO_ERR_ARG, "aniso3_set_option: null handle");
+    if (!h) return fail(ANISO_ERR_ARG, "aniso3_set_option: null handle");
     switch (key) {
     case ANISO_OPT_PRECISION:
-        if (v != ANISO_PREC_FP64 && v != ANISO_PREC_FP32) return fail3(ANISO_ERR_ARG, "bad precision %lld", v);
-        if (h->field_set && v != h->prec) return fail3(ANISO_ERR_STATE, "precision is fixed once the field is set");
+        if (v != ANISO_PREC_FP64 && v != ANISO_PREC_FP32) return fail(ANISO_ERR_ARG, "bad precision %lld", v);
+        if (h->field_set && v != h->prec) return fail(ANISO_ERR_STATE, "precision is fixed once the field is set");
         h->prec = (int)v;
         return ANISO_OK;
     case ANISO_OPT_LIMITER:
-        if (v < ANISO_LIM_VANLEER || v > ANISO_LIM_MC) return fail3(ANISO_ERR_ARG, "bad limiter %lld", v);
+        if (v < ANISO_LIM_VANLEER || v > ANISO_LIM_MC) return fail(ANISO_ERR_ARG, "bad limiter %lld", v);
         h->limiter = (int)v;
         return ANISO_OK;
     case ANISO_OPT_SCHEME:
         if (v == ANISO_SCHEME_EXPLICIT)
-            return fail3(ANISO_ERR_UNSUPPORTED, "aniso3_set_option: the explicit scheme is two-dimensional only");
-        if (v != ANISO_SCHEME_2STEP && v != ANISO_SCHEME_4STEP) return fail3(ANISO_ERR_ARG, "bad scheme %lld", v);
+            return fail(ANISO_ERR_UNSUPPORTED, "aniso3_set_option: the explicit scheme is two-dimensional only");
+        if (v != ANISO_SCHEME_2STEP && v != ANISO_SCHEME_4STEP) return fail(ANISO_ERR_ARG, "bad scheme %lld", v);
         h->scheme = (int)v;
         return ANISO_OK;
     case ANISO_OPT_STREAM:
         h->stream = reinterpret_cast<cudaStream_t>(v);
         return ANISO_OK;
     case ANISO_OPT_BLOCK_WARPS:
-        if (v < 0 || v > 8) return fail3(ANISO_ERR_ARG, "warps per block %lld (0..8)", v);
+        if (v < 0 || v > 8) return fail(ANISO_ERR_ARG, "warps per block %lld (0..8)", v);
         h->warps = (int)v;
         return h->field_set ? check_shape(h, "aniso3_set_option") : ANISO_OK;
     case ANISO_OPT_SEGMENT:
-        if (v < 0 || v > 64) return fail3(ANISO_ERR_ARG, "segment %lld (0..64)", v);
+        if (v < 0 || v > 64) return fail(ANISO_ERR_ARG, "segment %lld (0..64)", v);
         h->seg = (int)v;
         return h->field_set ? check_shape(h, "aniso3_set_option") : ANISO_OK;
     case ANISO_OPT_FIELD_FP16:
@@ -149,29 +131,29 @@ extern "C" int aniso3_set_option(aniso3_t h, int key, long long v)
     case ANISO_OPT_PROFILE:
     case ANISO_OPT_FAST_PATH:
         if (v == 0) return ANISO_OK;  // the default: nothing to change
-        return fail3(ANISO_ERR_UNSUPPORTED, "aniso3_set_option: option %d is two-dimensional only", key);
+        return fail(ANISO_ERR_UNSUPPORTED, "aniso3_set_option: option %d is two-dimensional only", key);
     default:
-        return fail3(ANISO_ERR_ARG, "aniso3_set_option: unknown key %d", key);
+        return fail(ANISO_ERR_ARG, "aniso3_set_option: unknown key %d", key);
     }
 }
 
 extern "C" int aniso3_set_field(aniso3_t h, const void *bx, const void *by, const void *bz)
 {
-    if (!h) return fail3(ANISO_ERR_ARG, "aniso3_set_field: null handle");
-    if (!bx || !by || !bz) return fail3(ANISO_ERR_ARG, "aniso3_set_field: null field pointer");
+    if (!h) return fail(ANISO_ERR_ARG, "aniso3_set_field: null handle");
+    if (!bx || !by || !bz) return fail(ANISO_ERR_ARG, "aniso3_set_field: null field pointer");
     int rc = check_shape(h, "aniso3_set_field");
     if (rc) return rc;
     if (!h->field_set) {
         const size_t bytes = h->cells() * h->esz();
-        for (auto &p : h->c) CU3(cudaMalloc(&p, bytes));
-        CU3(cudaMalloc(&h->s1, bytes));
-        CU3(cudaMalloc(&h->s2, bytes));
-        CU3(cudaMalloc(&h->partials, 4 * TOTALS_BLOCKS * sizeof(double)));
-        CU3(cudaMalloc(&h->result, 4 * sizeof(double)));
-        CU3(cudaMalloc(&h->err, sizeof(unsigned)));
-        CU3(cudaMemsetAsync(h->err, 0, sizeof(unsigned), h->stream));
+        for (auto &p : h->c) CU(cudaMalloc(&p, bytes));
+        CU(cudaMalloc(&h->s1, bytes));
+        CU(cudaMalloc(&h->s2, bytes));
+        CU(cudaMalloc(&h->partials, 4 * TOTALS_BLOCKS * sizeof(double)));
+        CU(cudaMalloc(&h->result, 4 * sizeof(double)));
+        CU(cudaMalloc(&h->err, sizeof(unsigned)));
+        CU(cudaMemsetAsync(h->err, 0, sizeof(unsigned), h->stream));
     }
-    CU3(launch_face_coeffs3(h->prec, bx, by, bz, h->n[0], h->n[1], h->n[2], h->bc, h->chi_perp / h->chi_par, h->c,
+    CU(launch_face_coeffs3(h->prec, bx, by, bz, h->n[0], h->n[1], h->n[2], h->bc, h->chi_perp / h->chi_par, h->c,
                             h->stream));
     h->field_set = true;
     return ANISO_OK;
@@ -205,21 +187,21 @@ static int enqueue3(aniso3_ctx *h, int d, const void *in, void *out, double lam,
     int nthreads;
     size_t smem;
     if (!line4_config(h->prec, J.n, transposed, h->warps, h->seg, &J.team, &J.lines_per_block, &nthreads, &smem))
-        return fail3(ANISO_ERR_UNSUPPORTED, "3-D line kernel cannot take n=%d", J.n);
+        return fail(ANISO_ERR_UNSUPPORTED, "3-D line kernel cannot take n=%d", J.n);
     J.block0 = 0;
     J.nblocks = (J.nlines + J.lines_per_block - 1) / J.lines_per_block;
-    CU3(launch_line4_3d(h->prec, A, J.nblocks, nthreads, smem, h->stream));
+    CU(launch_line4_3d(h->prec, A, J.nblocks, nthreads, smem, h->stream));
     return ANISO_OK;
 }
 
 extern "C" int aniso3_step(aniso3_t h, void *T, double dt, int nsteps)
 {
-    if (!h) return fail3(ANISO_ERR_ARG, "aniso3_step: null handle");
-    if (!T) return fail3(ANISO_ERR_ARG, "aniso3_step: T is NULL");
-    if (!(dt > 0)) return fail3(ANISO_ERR_ARG, "aniso3_step: dt must be > 0");
-    if (nsteps < 0) return fail3(ANISO_ERR_ARG, "aniso3_step: nsteps < 0");
-    if (!h->field_set) return fail3(ANISO_ERR_STATE, "aniso3_step: call aniso3_set_field first");
-    if (((uintptr_t)T & 15) != 0) return fail3(ANISO_ERR_ARG, "aniso3_step: T must be 16-byte aligned");
+    if (!h) return fail(ANISO_ERR_ARG, "aniso3_step: null handle");
+    if (!T) return fail(ANISO_ERR_ARG, "aniso3_step: T is NULL");
+    if (!(dt > 0)) return fail(ANISO_ERR_ARG, "aniso3_step: dt must be > 0");
+    if (nsteps < 0) return fail(ANISO_ERR_ARG, "aniso3_step: nsteps < 0");
+    if (!h->field_set) return fail(ANISO_ERR_STATE, "aniso3_step: call aniso3_set_field first");
+    if (((uintptr_t)T & 15) != 0) return fail(ANISO_ERR_ARG, "aniso3_step: T must be 16-byte aligned");
     const double c = h->chi_par * dt;
     double lam[3], mu[6];
     for (int d = 0; d < 3; ++d) {
@@ -252,10 +234,10 @@ extern "C" int aniso3_step(aniso3_t h, void *T, double dt, int nsteps)
 static int check_err3(aniso3_ctx *h)
 {
     unsigned flag = 0;
-    CU3(cudaMemcpy(&flag, h->err, sizeof flag, cudaMemcpyDeviceToHost));
+    CU(cudaMemcpy(&flag, h->err, sizeof flag, cudaMemcpyDeviceToHost));
     if (flag) {
-        CU3(cudaMemset(h->err, 0, sizeof(unsigned)));
-        return fail3(ANISO_ERR_NONFINITE, "a 3-D step produced a non-finite temperature");
+        CU(cudaMemset(h->err, 0, sizeof(unsigned)));
+        return fail(ANISO_ERR_NONFINITE, "a 3-D step produced a non-finite temperature");
     }
     return ANISO_OK;
 }
@@ -263,13 +245,13 @@ static int check_err3(aniso3_ctx *h)
 extern "C" int aniso3_total(aniso3_t h, const void *T, double *sum, double *tmin, double *tmax,
                             long long *nonfinite)
 {
-    if (!h) return fail3(ANISO_ERR_ARG, "aniso3_total: null handle");
-    if (!h->field_set) return fail3(ANISO_ERR_STATE, "aniso3_total: call aniso3_set_field first");
-    if (!T) return fail3(ANISO_ERR_ARG, "aniso3_total: T is NULL");
-    CU3(launch_totals(h->prec, T, h->cells(), h->partials, h->result, h->stream));
+    if (!h) return fail(ANISO_ERR_ARG, "aniso3_total: null handle");
+    if (!h->field_set) return fail(ANISO_ERR_STATE, "aniso3_total: call aniso3_set_field first");
+    if (!T) return fail(ANISO_ERR_ARG, "aniso3_total: T is NULL");
+    CU(launch_totals(h->prec, T, h->cells(), h->partials, h->result, h->stream));
     double r[4];
-    CU3(cudaMemcpyAsync(r, h->result, sizeof r, cudaMemcpyDeviceToHost, h->stream));
-    CU3(cudaStreamSynchronize(h->stream));
+    CU(cudaMemcpyAsync(r, h->result, sizeof r, cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
     if (sum) *sum = r[0];
     if (tmin) *tmin = r[1];
     if (tmax) *tmax = r[2];
@@ -279,8 +261,8 @@ extern "C" int aniso3_total(aniso3_t h, const void *T, double *sum, double *tmin
 
 extern "C" int aniso3_sync(aniso3_t h)
 {
-    if (!h) return fail3(ANISO_ERR_ARG, "aniso3_sync: null handle");
-    CU3(cudaStreamSynchronize(h->stream));
+    if (!h) return fail(ANISO_ERR_ARG, "aniso3_sync: null handle");
+    CU(cudaStreamSynchronize(h->stream));
     if (!h->err) return ANISO_OK;
     return check_err3(h);
 }

@@ -14,6 +14,7 @@
 
 #include "../../include/aniso.h"
 #include "aniso_internal.h"
+#include "status.h"
 
 // NVTX range around a public call, for timeline tools (a no-op without one).
 struct TraceRange {
@@ -26,25 +27,6 @@ using namespace aniso;
 // ------------------------------------------------------------- errors
 
 static thread_local std::string g_last_error;
-
-static int fail(int code, const char *fmt, ...)
-{
-    char buf[512];
-    va_list ap;
-    va_start(ap, fmt);
-    vsnprintf(buf, sizeof buf, fmt, ap);
-    va_end(ap);
-    g_last_error = buf;
-    return code;
-}
-
-#define CU(call)                                                                           \
-    do {                                                                                   \
-        cudaError_t e_ = (call);                                                           \
-        if (e_ != cudaSuccess)                                                             \
-            return fail(e_ == cudaErrorMemoryAllocation ? ANISO_ERR_OOM : ANISO_ERR_CUDA, \
-                        "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
-    } while (0)
 
 extern "C" const char *aniso_last_error(void) { return g_last_error.c_str(); }
 
