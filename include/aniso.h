@@ -138,7 +138,7 @@ int aniso_set_option(aniso_t h, int key, long long value);
 
 /* Set the unit field b (Section 2): bx, by are device arrays of nx*ny cell-
  * centred components in the handle's precision.  The library averages b to
- * faces (Section 2, "simple averaging") in FP64 and stores the face
+ * faces (Section 2: the plain mean of the two cells) in FP64 and stores the face
  * coefficients it needs, in units of chi_par (kappa = chi_perp/chi_par):
  *     x faces: kappa + (1-kappa) bx^2,  (1-kappa) bx by
  *     y faces: kappa + (1-kappa) by^2,  (1-kappa) by bx

@@ -13,8 +13,8 @@
 // coefficient (b-bar_x b-bar_y), DeltaTbar the limited transverse difference
 // (the DeltaT-bar equations after Eq. yup, limiter of Eq. vanLeer).
 //
-// Line solve (no counterpart in the paper, which only says the systems are
-// solved "exactly and efficiently"): each line is cut into P segments, one
+// Line solve (no counterpart in the paper, which only notes that the line
+// systems can be solved directly and cheaply): each line is cut into P segments, one
 // per thread.  A thread eliminates its segment bottom-up, storing
 //     delta_k = rho_k - alpha_k delta_{k-1} - gamma_k delta_e       (s <= k < e)
 // and composing those maps into delta_{e-1} = p + q delta_{s-1} + w delta_e.
@@ -747,7 +747,7 @@ __global__ void __launch_bounds__(512) col_sweep_kernel(ColArgs args)
 
 // ======================================================= setup / utility
 
-// Face coefficients of Section 2 ("simple averaging" of b to faces) in FP64
+// Face coefficients of Section 2 (b averaged to faces by the plain mean) in FP64
 // with explicit round-to-nearest operations (no contraction), then one
 // rounding to the storage type.
 template <typename C> __device__ __forceinline__ C to_store(double v);

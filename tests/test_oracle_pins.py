@@ -40,7 +40,7 @@ def test_vanleer_four_argument_is_harmonic_mean_and_symmetric():
         harmonic = 4.0 / np.sum(1.0 / v)        # closed form of the nesting
         assert got == pytest.approx(harmonic, rel=1e-13)
         assert min(v) - 1e-12 <= got <= max(v) + 1e-12
-        # "symmetric in its arguments" (text after Eq. vanLeer)
+        # the limiter is symmetric in its four arguments (text after Eq. vanLeer)
         for perm in ([1, 0, 2, 3], [2, 3, 0, 1], [0, 2, 1, 3], [3, 1, 2, 0]):
             assert O.limit4(*v[perm]) == pytest.approx(got, rel=1e-13)
     # any sign disagreement gives zero
