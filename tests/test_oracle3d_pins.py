@@ -199,12 +199,14 @@ def test_four_step_3d_is_stable_at_large_timesteps():
 # ---------------------------------------------------- exact reductions
 
 @pytest.mark.parametrize("bc", [O.BC_ZEROFLUX, O.BC_PERIODIC])
+@pytest.mark.parametrize("scheme", [O.SCHEME_2STEP, O.SCHEME_4STEP])
 @pytest.mark.parametrize("plane", ["xy", "yz", "zx"])
-def test_plane_field_reduces_to_the_2d_step(bc, plane):
+def test_plane_field_reduces_to_the_2d_step(bc, scheme, plane):
     # b in a coordinate plane and T constant along the third axis: that
     # axis's update is the identity and the other two carry no term along
     # it, so every slice takes the (separately pinned) 2-D step, the two
-    # in-plane updates in the order x, y, z.
+    # in-plane updates in the order x, y, z; likewise for the 4-step form
+    # against the 2-D Eq. 4step.
     rng = np.random.default_rng({"xy": 1, "yz": 2, "zx": 3}[plane] + 10 * bc)
     shape = (5, 6, 7)  # (nz, ny, nx)
     dx, dy, dz, chi, dt = 0.8, 1.3, 1.1, 1.0, 4.0
@@ -242,9 +244,10 @@ def test_plane_field_reduces_to_the_2d_step(bc, plane):
         d2 = (dx, dz)
         take = lambda U: [U[:, j, :] for j in range(shape[1])]  # noqa: E731
     co3 = O.face_coeffs3(bx, by, bz, bc)
-    got = O.step3(T, co3, bc, dt, dx, dy, dz, chi, nsteps=2)
+    got = O.step3(T, co3, bc, dt, dx, dy, dz, chi, nsteps=2, scheme=scheme)
     co2 = O.face_coeffs(b2[0], b2[1], bc)
-    want = O.step(T2, co2, bc, dt, d2[0], d2[1], chi, nsteps=2)
+    two_d = O.step if scheme == O.SCHEME_2STEP else O.step4  # Eq. op_2step / Eq. 4step in 2-D
+    want = two_d(T2, co2, bc, dt, d2[0], d2[1], chi, nsteps=2)
     for s in take(got):
         np.testing.assert_allclose(s, want, rtol=0, atol=1e-14)
 
