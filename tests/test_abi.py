@@ -103,6 +103,31 @@ def test_create3_validates_arguments(built):
         P.aniso3_destroy(h)
 
 
+def test_requests_beyond_the_limits_are_refused_before_any_allocation(built):
+    import paper_1008_0861_gb300 as P
+    with pytest.raises(P.AnisoError) as ei:
+        P.aniso_batch_create([])
+    assert ei.value.code == P.ANISO_ERR_ARG
+    # a row longer than the on-chip line limit (16384 cells in FP32)
+    h = P.aniso_create(16388, 8, 1.0, 1.0, 1.0)
+    try:
+        P.aniso_set_option(h, P.ANISO_OPT_PRECISION, P.ANISO_PREC_FP32)
+        with pytest.raises(P.AnisoError) as ei:
+            P.aniso_set_field(h, 0x1000, 0x1000)
+        assert ei.value.code == P.ANISO_ERR_UNSUPPORTED
+    finally:
+        P.aniso_destroy(h)
+    # a 3-D line longer than the 3-D kernel takes (2048 cells in FP32)
+    h3 = P.aniso3_create(2052, 8, 8, 1.0, 1.0, 1.0, 1.0)
+    try:
+        P.aniso3_set_option(h3, P.ANISO_OPT_PRECISION, P.ANISO_PREC_FP32)
+        with pytest.raises(P.AnisoError) as ei:
+            P.aniso3_set_field(h3, 0x1000, 0x1000, 0x1000)
+        assert ei.value.code == P.ANISO_ERR_UNSUPPORTED
+    finally:
+        P.aniso3_destroy(h3)
+
+
 def test_library_does_not_reference_the_oracle(built):
     data = open(built, "rb").read()
     assert b"or_xsweep" not in data and b"liboracle" not in data
