@@ -96,6 +96,11 @@ template <typename K> static cudaError_t run4_3d(K kern, const Line2Args &a, int
 cudaError_t launch_line4_3d(int prec, const Line2Args &a, int nblocks, int nthreads, size_t smem, cudaStream_t s)
 {
     const bool vl = a.limiter == LIM_VANLEER;
+    if (a.one.mu == 0.0 && a.one.mu2 == 0.0) {  // purely implicit update (4-step halves)
+        if (prec == PREC_FP64)
+            return run4_3d(line4_kernel<double, double, false, true, false, true>, a, nblocks, nthreads, smem, s);
+        return run4_3d(line4_kernel<float, float, false, true, false, true>, a, nblocks, nthreads, smem, s);
+    }
     if (prec == PREC_FP64)
         return vl ? run4_3d(line4_kernel<double, double, true, true>, a, nblocks, nthreads, smem, s)
                   : run4_3d(line4_kernel<double, double, false, true>, a, nblocks, nthreads, smem, s);

@@ -24,6 +24,13 @@ cudaError_t launch_line4(int prec, int coef_fp16, const Line2Args &a, int nblock
                          cudaStream_t s)
 {
     const bool vl = a.limiter == LIM_VANLEER;
+    if (!a.jobs && a.one.mu == 0.0 && a.one.chi_alpha == 0.0) {  // purely implicit update (4-step halves)
+        if (prec == PREC_FP64)
+            return run4(line4_kernel<double, double, false, false, false, true>, a, nblocks, nthreads, smem, s);
+        if (coef_fp16)
+            return run4(line4_kernel<float, __half, false, false, false, true>, a, nblocks, nthreads, smem, s);
+        return run4(line4_kernel<float, float, false, false, false, true>, a, nblocks, nthreads, smem, s);
+    }
     if (!a.jobs && a.one.chi_alpha != 0.0) {  // temperature-dependent diffusivity (single grids)
         if (coef_fp16) return cudaErrorInvalidValue;
         if (prec == PREC_FP64)

@@ -141,7 +141,10 @@ template <typename R> __device__ __forceinline__ R face_harmonic(R a, R b)
     return (a > R(0) && b > R(0)) ? R(2) * a * Fast<R>::div(b, a + b) : R(0);
 }
 
-template <typename R, typename C, bool VL, bool D3 = false, bool NL = false>
+// IMPL: a purely implicit update (no transverse term, mu = mu2 = 0: the second
+// half-update of each axis in the 4-step scheme); neighbouring lines and
+// transverse coefficients are then neither loaded nor limited.
+template <typename R, typename C, bool VL, bool D3 = false, bool NL = false, bool IMPL = false>
 __global__ void __launch_bounds__(256, sizeof(R) == 4 ? (D3 ? 3 : 4) : 2) line4_kernel(Line2Args args)
 {
     typedef typename V16<R>::T VT;
@@ -189,11 +192,13 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? (D3 ? 3 : 4) : 2) line4_
     // warps' loads below find them there.  A hint only: issued when the
     // range is 16-byte aligned.
     if (threadIdx.x == 0) {
-        const int f0 = line0 > 0 ? line0 - 1 : 0, f1 = min(line0 + LPB + 1, nl), g1 = min(line0 + LPB, nl);
+        const int f0 = line0 > 0 && !IMPL ? line0 - 1 : line0, f1 = min(line0 + LPB + (IMPL ? 0 : 1), nl),
+                  g1 = min(line0 + LPB, nl);
         l2_prefetch(Tin + (size_t)f0 * n, (size_t)(f1 - f0) * n * sizeof(R));
         l2_prefetch(static_cast<const C *>(J.g) + (size_t)line0 * n, (size_t)(g1 - line0) * n * sizeof(C));
-        l2_prefetch(static_cast<const C *>(J.e) + (size_t)line0 * n, (size_t)(g1 - line0) * n * sizeof(C));
-        if constexpr (D3) {
+        if constexpr (!IMPL)
+            l2_prefetch(static_cast<const C *>(J.e) + (size_t)line0 * n, (size_t)(g1 - line0) * n * sizeof(C));
+        if constexpr (D3 && !IMPL) {
             l2_prefetch(static_cast<const C *>(J.e2) + (size_t)line0 * n, (size_t)(g1 - line0) * n * sizeof(C));
             // the block's neighbours along the second transverse axis, where not wrapped
             if (line0 >= J.na) l2_prefetch(Tin + (size_t)(line0 - J.na) * n, (size_t)(g1 - line0) * n * sizeof(R));
@@ -223,11 +228,16 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? (D3 ? 3 : 4) : 2) line4_
         R wcar = R(0);               // the same for the second transverse axis (D3)
         // the next round's loads are issued before this round's arithmetic
         int cl = min(((V - 1) << logP) + t, m - 1);
-        VT xd = vd[cl], xc = vc[cl], xu = vu[cl];
-        auto xg = ld_raw(G + cl * N), xe = ld_raw(E + cl * N);
+        VT xc = vc[cl], xd = xc, xu = xc;
+        auto xg = ld_raw(G + cl * N), xe = xg;
+        if constexpr (!IMPL) {
+            xd = vd[cl];
+            xu = vu[cl];
+            xe = ld_raw(E + cl * N);
+        }
         VT xbd = xc, xbu = xc;
         auto xe2 = xe;
-        if constexpr (D3) {
+        if constexpr (D3 && !IMPL) {
             xbd = vbd[cl];
             xbu = vbu[cl];
             xe2 = ld_raw(E2 + cl * N);
@@ -235,12 +245,14 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? (D3 ? 3 : 4) : 2) line4_
         for (int v = V - 1; v >= 0; --v) {
             const int c = (v << logP) + t;
             R Td[N], Tc[N], Tu[N], Gv[N], Ev[N], Tbd[N], Tbu[N], E2v[N];
-            V16<R>::unpack(xd, Td);
             V16<R>::unpack(xc, Tc);
-            V16<R>::unpack(xu, Tu);
             unpack_raw(xg, Gv);
-            unpack_raw(xe, Ev);
-            if constexpr (D3) {
+            if constexpr (!IMPL) {
+                V16<R>::unpack(xd, Td);
+                V16<R>::unpack(xu, Tu);
+                unpack_raw(xe, Ev);
+            }
+            if constexpr (D3 && !IMPL) {
                 V16<R>::unpack(xbd, Tbd);
                 V16<R>::unpack(xbu, Tbu);
                 unpack_raw(xe2, E2v);
@@ -248,27 +260,31 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? (D3 ? 3 : 4) : 2) line4_
             const int cur = cl;
             if (v > 0) {
                 cl = ((v - 1) << logP) + t;  // always < m
-                xd = vd[cl];
                 xc = vc[cl];
-                xu = vu[cl];
                 xg = ld_raw(G + cl * N);
-                xe = ld_raw(E + cl * N);
-                if constexpr (D3) {
+                if constexpr (!IMPL) {
+                    xd = vd[cl];
+                    xu = vu[cl];
+                    xe = ld_raw(E + cl * N);
+                }
+                if constexpr (D3 && !IMPL) {
                     xbd = vbd[cl];
                     xbu = vbu[cl];
                     xe2 = ld_raw(E2 + cl * N);
                 }
             }
             R vv[N], ww[N];
+            if constexpr (!IMPL) {
 #pragma unroll
-            for (int j = 0; j < N; ++j) vv[j] = level<R, VL>(lim, Tu[j] - Tc[j], Tc[j] - Td[j]);
-            if constexpr (D3) {
+                for (int j = 0; j < N; ++j) vv[j] = level<R, VL>(lim, Tu[j] - Tc[j], Tc[j] - Td[j]);
+            }
+            if constexpr (D3 && !IMPL) {
 #pragma unroll
                 for (int j = 0; j < N; ++j) ww[j] = level<R, VL>(lim, Tbu[j] - Tc[j], Tc[j] - Tbd[j]);
             }
-            R nT = __shfl_down_sync(full, Tc[0], 1, P), nv = __shfl_down_sync(full, vv[0], 1, P);
-            R nw = R(0);
-            if constexpr (D3) nw = __shfl_down_sync(full, ww[0], 1, P);
+            R nT = __shfl_down_sync(full, Tc[0], 1, P), nv = R(0), nw = R(0);
+            if constexpr (!IMPL) nv = __shfl_down_sync(full, vv[0], 1, P);
+            if constexpr (D3 && !IMPL) nw = __shfl_down_sync(full, ww[0], 1, P);
             if (t == P - 1) {
                 nT = Tcar;
                 nv = vcar;
@@ -277,12 +293,12 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? (D3 ? 3 : 4) : 2) line4_
             if (cur == m - 1) {  // the cell after the line: periodic wrap or mirrored ghost
                 const int p1 = J.per_line ? 0 : n - 1;
                 nT = rc[p1];
-                nv = level<R, VL>(lim, ru[p1] - nT, nT - rd[p1]);
-                if constexpr (D3) nw = level<R, VL>(lim, rbu[p1] - nT, nT - rbd[p1]);
+                if constexpr (!IMPL) nv = level<R, VL>(lim, ru[p1] - nT, nT - rd[p1]);
+                if constexpr (D3 && !IMPL) nw = level<R, VL>(lim, rbu[p1] - nT, nT - rbd[p1]);
             }
             Tcar = __shfl_sync(full, Tc[0], 0, P);
-            vcar = __shfl_sync(full, vv[0], 0, P);
-            if constexpr (D3) wcar = __shfl_sync(full, ww[0], 0, P);
+            if constexpr (!IMPL) vcar = __shfl_sync(full, vv[0], 0, P);
+            if constexpr (D3 && !IMPL) wcar = __shfl_sync(full, ww[0], 0, P);
             R F[N], lg[N], hf[N];
             if constexpr (NL) {
                 R ch[N + 1];
@@ -295,11 +311,16 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? (D3 ? 3 : 4) : 2) line4_
 #pragma unroll
             for (int j = 0; j < N; ++j) {
                 const R Tnx = j + 1 < N ? Tc[j + 1] : nT;
-                const R vnx = j + 1 < N ? vv[j + 1] : nv;
-                const R gj = NL ? Gv[j] * hf[j] : Gv[j], ej = NL ? Ev[j] * hf[j] : Ev[j];
+                const R gj = NL ? Gv[j] * hf[j] : Gv[j];
                 lg[j] = lam * gj;
-                F[j] = lg[j] * (Tnx - Tc[j]) + mu * ej * level<R, VL>(lim, vv[j], vnx);
-                if constexpr (D3) {
+                if constexpr (IMPL) {
+                    F[j] = lg[j] * (Tnx - Tc[j]);
+                } else {
+                    const R vnx = j + 1 < N ? vv[j + 1] : nv;
+                    const R ej = NL ? Ev[j] * hf[j] : Ev[j];
+                    F[j] = lg[j] * (Tnx - Tc[j]) + mu * ej * level<R, VL>(lim, vv[j], vnx);
+                }
+                if constexpr (D3 && !IMPL) {
                     const R wnx = j + 1 < N ? ww[j + 1] : nw;
                     F[j] += mu2 * (NL ? E2v[j] * hf[j] : E2v[j]) * level<R, VL>(lim, ww[j], wnx);
                 }
