@@ -639,6 +639,34 @@ static int enqueue_steps(aniso_ctx *h, void *T, double dt, int nsteps, long long
         if (nsteps & 1) CU(cudaMemcpyAsync(T, h->tstar, h->cells() * h->esz(), cudaMemcpyDeviceToDevice, s));
         return ANISO_OK;
     }
+    if (h->scheme == ANISO_SCHEME_4STEP && h->order == ANISO_ORDER_XY && h->t4 && aligned16(h->t4) &&
+        use_fast(h, T) && h->fast_kind() == 4) {
+        // Eq. 4step on the line4 path: each direction's first half-update
+        // writes its lines in place order (t4), the purely implicit second
+        // half writes them transposed, so x: T -> t4 -> T* (column-major) and
+        // y: T* -> t4 -> T (row-major), with no transpose pass
+        const double lamx = h->chi_par * dt / (h->dx * h->dx);
+        const double lamy = h->chi_par * dt / (h->dy * h->dy);
+        const double mu = h->chi_par * dt / (h->dx * h->dy);
+        const int per = h->bc == ANISO_BC_PERIODIC;
+        for (int k = 0; k < nsteps; ++k) {
+            int rc;
+            if (h->q) CU(launch_source(h->prec, T, h->q, dt, h->cells(), s));
+            if ((rc = enqueue_line2(h, T, h->t4, h->cxx, h->cxy, h->nx, h->ny, per, per, 0.5 * lamx, mu, false,
+                                    ANISO_KERNEL_XSWEEP, s, pairs, true)))
+                return rc;
+            if ((rc = enqueue_line2(h, h->t4, h->tstar, h->cxx, h->cxy, h->nx, h->ny, per, per, 0.5 * lamx, 0.0,
+                                    true, ANISO_KERNEL_XSWEEP, s, pairs, true)))
+                return rc;
+            if ((rc = enqueue_line2(h, h->tstar, h->t4, h->cyyT, h->cyxT, h->ny, h->nx, per, per, 0.5 * lamy, mu,
+                                    false, ANISO_KERNEL_YSWEEP, s, pairs, true)))
+                return rc;
+            if ((rc = enqueue_line2(h, h->t4, T, h->cyyT, h->cyxT, h->ny, h->nx, per, per, 0.5 * lamy, 0.0, true,
+                                    ANISO_KERNEL_YSWEEP, s, pairs, true)))
+                return rc;
+        }
+        return ANISO_OK;
+    }
     if (h->scheme == ANISO_SCHEME_4STEP) {
         // Eq. 4step: per direction, the semi-implicit update with its implicit
         // part over dt/2, then a fully implicit dt/2 update (no transverse term)
