@@ -47,6 +47,9 @@ def _worker(rank, world, port, out):
         with redirect_stdout(printed):
             rc = b.run_reference(b.parse_args_for_test(["--impl", "reference", "--steps", "1", "--warmup", "0",
                                                         "--instances", "2"])) if rank != 0 else 0
+            if rank != 0:  # the 3-D workload's reference arm as well
+                rc |= b.run_reference_3d(b.parse_args_for_test(["--impl", "reference", "--workload", "random3d",
+                                                                "--steps", "1", "--warmup", "0"]))
         out.put((rank, value, ms, units, everyone, rc, printed.getvalue()))
     finally:
         dist.destroy_process_group()
@@ -75,3 +78,9 @@ def test_two_gloo_ranks_shard_and_reduce():
     assert u0 == u1 == cells0 + cells1                         # sum over ranks
     assert v0 == pytest.approx((cells0 + cells1) / 15e-3 / 1e9)
     assert rc1 == 0 and out1 == ""
+    # the 3-D workload gives each rank its own grid (seed base + rank)
+    import workloads as W
+    assert b.W3_N == 256 and b.make_instance3d.__defaults__ == (0,)
+    i0 = W.random_instance3d(8, 8, 8, seed=W.BASE_SEED + 0)
+    i1 = W.random_instance3d(8, 8, 8, seed=W.BASE_SEED + 1)
+    assert not (i0.bx == i1.bx).all()
