@@ -596,6 +596,53 @@ static bool x_first(int order, long long counter)
     return (counter & 1) == 0;
 }
 
+// Any update order on the line4 path.  An x-update reads rows (a row-major
+// array), a y-update columns (a column-major one); each writes its lines in
+// place order or transposed, whichever layout the next update reads, and the
+// last update leaves T row-major.  A call that starts with a y-update first
+// transposes T once; the updates alternate between T and T*, and a final copy
+// brings the state back to T when it ends in T*.
+static bool fast_any_order(const aniso_ctx *h, const void *T)
+{
+    return h->fast && !h->kahan && !h->dirichlet() && !h->q && h->nl_alpha == 0.0 && h->cyyT && aligned16(T) &&
+           aligned16(h->tstar) && h->fast_kind() == 4;
+}
+
+static int enqueue_steps_any_order(aniso_ctx *h, void *T, double dt, int nsteps, long long counter0,
+                                   cudaStream_t s, std::vector<int> *pairs)
+{
+    const double lamx = h->chi_par * dt / (h->dx * h->dx);
+    const double lamy = h->chi_par * dt / (h->dy * h->dy);
+    const double mu = h->chi_par * dt / (h->dx * h->dy);
+    const int per = h->bc == ANISO_BC_PERIODIC;
+    std::vector<int> dirs;  // the updates of the call, in order
+    for (int k = 0; k < nsteps; ++k) {
+        const bool xf = x_first(h->order, counter0 + k);
+        dirs.push_back(xf ? ANISO_DIR_X : ANISO_DIR_Y);
+        dirs.push_back(xf ? ANISO_DIR_Y : ANISO_DIR_X);
+    }
+    void *cur = T;
+    if (!dirs.empty() && dirs[0] == ANISO_DIR_Y) {  // columns of the row-major T, once
+        CU(launch_transpose((int)h->esz(), T, h->tstar, h->ny, h->nx, s));
+        cur = h->tstar;
+    }
+    for (size_t i = 0; i < dirs.size(); ++i) {
+        const bool x = dirs[i] == ANISO_DIR_X;
+        // the next update (or the caller, after the last) reads rows for x, columns for y
+        const bool next_rows = i + 1 < dirs.size() ? dirs[i + 1] == ANISO_DIR_X : true;
+        const bool transposed = x ? !next_rows : next_rows;
+        void *out = cur == T ? h->tstar : T;
+        const int rc = x ? enqueue_line2(h, cur, out, h->cxx, h->cxy, h->nx, h->ny, per, per, lamx, mu, transposed,
+                                         ANISO_KERNEL_XSWEEP, s, pairs, true)
+                         : enqueue_line2(h, cur, out, h->cyyT, h->cyxT, h->ny, h->nx, per, per, lamy, mu,
+                                         transposed, ANISO_KERNEL_YSWEEP, s, pairs, true);
+        if (rc) return rc;
+        cur = out;
+    }
+    if (cur != T) CU(cudaMemcpyAsync(T, cur, h->cells() * h->esz(), cudaMemcpyDeviceToDevice, s));
+    return ANISO_OK;
+}
+
 static int enqueue_steps(aniso_ctx *h, void *T, double dt, int nsteps, long long counter0,
                          cudaStream_t s, std::vector<int> *pairs)
 {
@@ -690,6 +737,8 @@ static int enqueue_steps(aniso_ctx *h, void *T, double dt, int nsteps, long long
         }
         return ANISO_OK;
     }
+    if (h->scheme == ANISO_SCHEME_2STEP && fast_any_order(h, T))
+        return enqueue_steps_any_order(h, T, dt, nsteps, counter0, s, pairs);
     for (int k = 0; k < nsteps; ++k) {
         const bool xf = x_first(h->order, counter0 + k);
         if (h->q) CU(launch_source(h->prec, T, h->q, dt, h->cells(), s));
