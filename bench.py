@@ -1,4 +1,4 @@
-"""Benchmark: batched uneven grids, FP32, one graph-captured launch per sweep.
+"""Benchmark: batched uneven grids, FP32, all steps of a call in one captured CUDA graph.
 
 Workload (one bench "step" = one aniso_step_batched call): 512 independent
 periodic random-field grids, nx and ny drawn from the multiples of 32 in
@@ -27,7 +27,8 @@ N_INST = 512
 STEPS_PER_CALL = 200
 BYTES_PER_CELL_SWEEP = 16  # FP32: read T (4) + two face coefficients (8) + write T (4)
 WORKLOAD = ("batched 512 uneven periodic random-field grids (nx, ny multiples of 32 in "
-            "[64,1024]), FP32, 200 steps per call, one launch per sweep in a captured CUDA graph")
+            "[64,1024]), FP32, 200 steps per call in a captured CUDA graph, each sweep one launch per "
+            "occupancy class of line lengths (run concurrently)")
 
 
 def parse_args_for_test(argv):

@@ -209,9 +209,10 @@ void aniso_destroy(aniso_t h);
 const char *aniso_last_error(void);
 
 /* Group n handles (same precision, limiter and field storage; each with its
- * field set) so that one launch per sweep advances all of them: the
- * paper's update applied to independent grids of uneven sizes, fields and
- * timesteps.  The batch uses the first handle's stream and options
+ * field set) so that each sweep advances all of them together: one launch per
+ * class of line lengths with the same occupancy (at most five, run
+ * concurrently), the paper's update applied to independent grids of uneven
+ * sizes, fields and timesteps.  The batch uses the first handle's stream and options
  * GRAPH/PROFILE.  The handles must outlive the batch.  Grids with more than
  * 1024 rows take their y-updates through the transpose path, captured into the
  * same graph.  Errors: ANISO_ERR_ARG, ANISO_ERR_STATE. */
