@@ -310,7 +310,8 @@ typedef struct aniso3_ctx *aniso3_t;
  * nothing on the device.  Errors: ANISO_ERR_ARG. */
 int aniso3_create(int nx, int ny, int nz, double dx, double dy, double dz, double chi_par, double chi_perp,
                   int bc, aniso3_t *out);
-/* Options: ANISO_OPT_PRECISION (before aniso3_set_field), LIMITER, SCHEME
+/* Options: ANISO_OPT_PRECISION and FIELD_FP16 (FP16 face coefficients, FP32
+ * precision only; both before aniso3_set_field), LIMITER, SCHEME
  * (ANISO_SCHEME_2STEP or _4STEP), STREAM, BLOCK_WARPS, SEGMENT.  The other
  * keys accept only their default 0 (ANISO_ERR_UNSUPPORTED otherwise). */
 int aniso3_set_option(aniso3_t h, int key, long long value);

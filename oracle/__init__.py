@@ -298,6 +298,11 @@ class Coeffs3:
     def _ptrs(self):
         return (_D * 9)(*(_p(a) for a in self.arrays))
 
+    def rounded(self, dtype):
+        """Coefficients as stored in a reduced-precision field (plain
+        round-to-nearest-even of each stored value), widened back exactly."""
+        return Coeffs3([a.astype(dtype).astype(np.float64) for a in self.arrays])
+
 
 def face_coeffs3(bx, by, bz, bc, chi_par=1.0, chi_perp=0.0) -> Coeffs3:
     """Average the cell-centred unit field to the faces of a 3-D grid and form

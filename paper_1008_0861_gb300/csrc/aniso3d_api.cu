@@ -26,6 +26,7 @@ struct aniso3_ctx {
     double chi_par = 0, chi_perp = 0;
     int bc = 0;
     int prec = PREC_FP64, limiter = LIM_VANLEER, scheme = ANISO_SCHEME_2STEP, warps = 0, seg = 0;
+    int field_fp16 = 0;  // face coefficients stored as FP16 (FP32 precision only)
     cudaStream_t stream = 0;
     bool field_set = false;
     void *c[9] = {};                    // face coefficients, each axis in its update's layout
@@ -35,6 +36,7 @@ struct aniso3_ctx {
 
     size_t cells() const { return (size_t)n[0] * n[1] * n[2]; }
     size_t esz() const { return prec == PREC_FP64 ? 8 : 4; }
+    size_t csz() const { return field_fp16 ? 2 : esz(); }
 };
 
 static void free3(aniso3_ctx *h)
@@ -125,6 +127,10 @@ extern "C" int aniso3_set_option(aniso3_t h, int key, long long v)
         h->seg = (int)v;
         return h->field_set ? check_shape(h, "aniso3_set_option") : ANISO_OK;
     case ANISO_OPT_FIELD_FP16:
+        if (h->field_set && (v != 0) != (h->field_fp16 != 0))
+            return fail(ANISO_ERR_STATE, "field storage is fixed once the field is set");
+        h->field_fp16 = v != 0;
+        return ANISO_OK;
     case ANISO_OPT_KAHAN:
     case ANISO_OPT_ORDER:
     case ANISO_OPT_GRAPH:
@@ -141,11 +147,13 @@ extern "C" int aniso3_set_field(aniso3_t h, const void *bx, const void *by, cons
 {
     if (!h) return fail(ANISO_ERR_ARG, "aniso3_set_field: null handle");
     if (!bx || !by || !bz) return fail(ANISO_ERR_ARG, "aniso3_set_field: null field pointer");
+    if (h->field_fp16 && h->prec != PREC_FP32)
+        return fail(ANISO_ERR_ARG, "aniso3_set_field: FP16 field storage needs FP32 precision");
     int rc = check_shape(h, "aniso3_set_field");
     if (rc) return rc;
     if (!h->field_set) {
         const size_t bytes = h->cells() * h->esz();
-        for (auto &p : h->c) CU(cudaMalloc(&p, bytes));
+        for (auto &p : h->c) CU(cudaMalloc(&p, h->cells() * h->csz()));
         CU(cudaMalloc(&h->s1, bytes));
         CU(cudaMalloc(&h->s2, bytes));
         CU(cudaMalloc(&h->partials, 4 * TOTALS_BLOCKS * sizeof(double)));
@@ -153,8 +161,8 @@ extern "C" int aniso3_set_field(aniso3_t h, const void *bx, const void *by, cons
         CU(cudaMalloc(&h->err, sizeof(unsigned)));
         CU(cudaMemsetAsync(h->err, 0, sizeof(unsigned), h->stream));
     }
-    CU(launch_face_coeffs3(h->prec, bx, by, bz, h->n[0], h->n[1], h->n[2], h->bc, h->chi_perp / h->chi_par, h->c,
-                            h->stream));
+    CU(launch_face_coeffs3(h->prec, h->field_fp16, bx, by, bz, h->n[0], h->n[1], h->n[2], h->bc,
+                           h->chi_perp / h->chi_par, h->c, h->stream));
     h->field_set = true;
     return ANISO_OK;
 }
@@ -190,7 +198,7 @@ static int enqueue3(aniso3_ctx *h, int d, const void *in, void *out, double lam,
         return fail(ANISO_ERR_UNSUPPORTED, "3-D line kernel cannot take n=%d", J.n);
     J.block0 = 0;
     J.nblocks = (J.nlines + J.lines_per_block - 1) / J.lines_per_block;
-    CU(launch_line4_3d(h->prec, A, J.nblocks, nthreads, smem, h->stream));
+    CU(launch_line4_3d(h->prec, h->field_fp16, A, J.nblocks, nthreads, smem, h->stream));
     return ANISO_OK;
 }
 

@@ -178,11 +178,13 @@ int line4_blocks_per_sm(int prec, int coef_fp16, int limiter, int nthreads, size
 // Three-dimensional grids (kernels_3d.cu).  c[0..2] = x faces (normal, with
 // y, with z) in layout [nz][ny][nx]; c[3..5] = y faces (normal, with z, with
 // x) in [nx][nz][ny]; c[6..8] = z faces (normal, with x, with y) in
-// [ny][nx][nz].  bx, by, bz are [nz][ny][nx] in precision prec, as is c.
-cudaError_t launch_face_coeffs3(int prec, const void *bx, const void *by, const void *bz, int nx, int ny, int nz,
-                                int bc, double kappa, void *const c[9], cudaStream_t s);
+// [ny][nx][nz].  bx, by, bz are [nz][ny][nx] in precision prec; c is in that
+// precision too, or FP16 with coef_fp16 (FP32 only).
+cudaError_t launch_face_coeffs3(int prec, int coef_fp16, const void *bx, const void *by, const void *bz, int nx,
+                                int ny, int nz, int bc, double kappa, void *const c[9], cudaStream_t s);
 // line4_kernel with the second transverse term (jobs with na > 0).
-cudaError_t launch_line4_3d(int prec, const Line2Args &a, int nblocks, int nthreads, size_t smem, cudaStream_t s);
+cudaError_t launch_line4_3d(int prec, int coef_fp16, const Line2Args &a, int nblocks, int nthreads, size_t smem,
+                            cudaStream_t s);
 void line_config(int prec, int n, int *team, int *lines_per_block, int *nthreads);
 size_t line_smem_bytes(int prec, int n, int team, int lines_per_block);
 void col_config(int prec, int ny, int *P, int *Wb, int *nthreads);

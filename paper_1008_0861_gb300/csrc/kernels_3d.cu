@@ -22,7 +22,8 @@ namespace aniso {
 // periodic); the normal coefficient is kappa + (1 - kappa) b_d^2 and the two
 // transverse ones (1 - kappa) b_d b_a, (1 - kappa) b_d b_b with (d, a, b) =
 // (x, y, z), (y, z, x), (z, x, y).  Zero-flux boundary faces are zero.  FP64
-// arithmetic, one rounding to the storage type.
+// arithmetic with explicitly rounded operations (no contraction), one rounding
+// to the storage type (FP64, FP32 or FP16).
 template <typename B, typename C>
 __global__ void face_coeffs3_kernel(const B *bx, const B *by, const B *bz, int nx, int ny, int nz, int bc,
                                     double kappa, C *cx0, C *cx1, C *cx2, C *cy0, C *cy1, C *cy2, C *cz0,
@@ -43,25 +44,36 @@ __global__ void face_coeffs3_kernel(const B *bx, const B *by, const B *bz, int n
             if (bc != 0 || ix[d] < n3[d] - 1) {
                 const int nb = ix[d] + 1 < n3[d] ? ix[d] + 1 : 0;
                 const size_t o1 = o - (size_t)ix[d] * st[d] + (size_t)nb * st[d];
-                const double f[3] = {0.5 * ((double)bx[o] + (double)bx[o1]), 0.5 * ((double)by[o] + (double)by[o1]),
-                                     0.5 * ((double)bz[o] + (double)bz[o1])};
-                cn = kappa + (1.0 - kappa) * (f[d] * f[d]);
-                ca = (1.0 - kappa) * (f[d] * f[a]);
-                cb = (1.0 - kappa) * (f[d] * f[b]);
+                const double f[3] = {__dmul_rn(0.5, __dadd_rn((double)bx[o], (double)bx[o1])),
+                                     __dmul_rn(0.5, __dadd_rn((double)by[o], (double)by[o1])),
+                                     __dmul_rn(0.5, __dadd_rn((double)bz[o], (double)bz[o1]))};
+                const double omk = __dsub_rn(1.0, kappa);
+                cn = __dadd_rn(kappa, __dmul_rn(omk, __dmul_rn(f[d], f[d])));
+                ca = __dmul_rn(omk, __dmul_rn(f[d], f[a]));
+                cb = __dmul_rn(omk, __dmul_rn(f[d], f[b]));
             }
-            outs[d][0][dst[d]] = (C)cn;
-            outs[d][1][dst[d]] = (C)ca;
-            outs[d][2][dst[d]] = (C)cb;
+            outs[d][0][dst[d]] = to_store<C>(cn);
+            outs[d][1][dst[d]] = to_store<C>(ca);
+            outs[d][2][dst[d]] = to_store<C>(cb);
         }
     }
 }
 
-cudaError_t launch_face_coeffs3(int prec, const void *bx, const void *by, const void *bz, int nx, int ny, int nz,
-                                int bc, double kappa, void *const c[9], cudaStream_t s)
+cudaError_t launch_face_coeffs3(int prec, int coef_fp16, const void *bx, const void *by, const void *bz, int nx,
+                                int ny, int nz, int bc, double kappa, void *const c[9], cudaStream_t s)
 {
     const size_t cells = (size_t)nx * ny * nz;
     const int threads = 256;
     const int blocks = (int)std::min<size_t>((cells + threads - 1) / threads, 152 * 16);
+    if (coef_fp16) {
+        if (prec == PREC_FP64) return cudaErrorInvalidValue;
+        __half *h[9];
+        for (int k = 0; k < 9; ++k) h[k] = static_cast<__half *>(c[k]);
+        face_coeffs3_kernel<float, __half><<<blocks, threads, 0, s>>>(
+            static_cast<const float *>(bx), static_cast<const float *>(by), static_cast<const float *>(bz), nx, ny, nz,
+            bc, kappa, h[0], h[1], h[2], h[3], h[4], h[5], h[6], h[7], h[8]);
+        return cudaGetLastError();
+    }
     if (prec == PREC_FP64)
         face_coeffs3_kernel<double, double><<<blocks, threads, 0, s>>>(
             static_cast<const double *>(bx), static_cast<const double *>(by), static_cast<const double *>(bz), nx, ny,
@@ -93,14 +105,21 @@ template <typename K> static cudaError_t run4_3d(K kern, const Line2Args &a, int
     return cudaGetLastError();
 }
 
-cudaError_t launch_line4_3d(int prec, const Line2Args &a, int nblocks, int nthreads, size_t smem, cudaStream_t s)
+cudaError_t launch_line4_3d(int prec, int coef_fp16, const Line2Args &a, int nblocks, int nthreads, size_t smem,
+                            cudaStream_t s)
 {
     const bool vl = a.limiter == LIM_VANLEER;
+    if (coef_fp16 && prec == PREC_FP64) return cudaErrorInvalidValue;
     if (a.one.mu == 0.0 && a.one.mu2 == 0.0) {  // purely implicit update (4-step halves)
         if (prec == PREC_FP64)
             return run4_3d(line4_kernel<double, double, false, true, false, true>, a, nblocks, nthreads, smem, s);
+        if (coef_fp16)
+            return run4_3d(line4_kernel<float, __half, false, true, false, true>, a, nblocks, nthreads, smem, s);
         return run4_3d(line4_kernel<float, float, false, true, false, true>, a, nblocks, nthreads, smem, s);
     }
+    if (coef_fp16)
+        return vl ? run4_3d(line4_kernel<float, __half, true, true>, a, nblocks, nthreads, smem, s)
+                  : run4_3d(line4_kernel<float, __half, false, true>, a, nblocks, nthreads, smem, s);
     if (prec == PREC_FP64)
         return vl ? run4_3d(line4_kernel<double, double, true, true>, a, nblocks, nthreads, smem, s)
                   : run4_3d(line4_kernel<double, double, false, true>, a, nblocks, nthreads, smem, s);

@@ -24,13 +24,15 @@ def rel_linf(a, ref):
 class Grid3:
     """One aniso3 handle with its field set and T resident on the device."""
 
-    def __init__(self, P, inst, prec, limiter=0, scheme=0, warps=0, seg=0):
+    def __init__(self, P, inst, prec, limiter=0, scheme=0, warps=0, seg=0, fp16=False):
         import torch
         self.P, self.inst = P, inst
         self.dtype = torch.float64 if prec == FP64 else torch.float32
         self.h = P.aniso3_create(inst.nx, inst.ny, inst.nz, inst.dx, inst.dy, inst.dz, inst.chi_par,
                                  inst.chi_perp, inst.bc)
         P.aniso3_set_option(self.h, P.ANISO_OPT_PRECISION, prec)
+        if fp16:
+            P.aniso3_set_option(self.h, P.ANISO_OPT_FIELD_FP16, 1)
         P.aniso3_set_option(self.h, P.ANISO_OPT_LIMITER, limiter)
         P.aniso3_set_option(self.h, P.ANISO_OPT_SCHEME, scheme)
         if warps:
@@ -50,14 +52,17 @@ class Grid3:
         self.P.aniso3_destroy(self.h)
 
 
-def oracle_run(inst, prec, nsteps, limiter=0, scheme=0, round_each_step=False):
+def oracle_run(inst, prec, nsteps, limiter=0, scheme=0, round_each_step=False, fp16=False):
     """The oracle on the inputs the GPU sees (rounded to its precision,
-    widened exactly).  round_each_step: round the state to FP32 after every
+    widened exactly; with fp16, the face coefficients rounded to FP16 as the
+    GPU stores them).  round_each_step: round the state to FP32 after every
     step (the FP32 noise floor of the problem)."""
     dt = np.float64 if prec == FP64 else np.float32
     b = [a.astype(dt).astype(np.float64) for a in (inst.bx, inst.by, inst.bz)]
     T = inst.T0.astype(dt).astype(np.float64)
     co = O.face_coeffs3(*b, inst.bc, inst.chi_par, inst.chi_perp)
+    if fp16:
+        co = co.rounded(np.float16)
     if not round_each_step:
         return O.step3(T, co, inst.bc, inst.dt, inst.dx, inst.dy, inst.dz, inst.chi_par, nsteps=nsteps,
                        limiter=limiter, scheme=scheme)
@@ -291,3 +296,32 @@ def test_stability_limit_on_the_gpu(lib):
     U5 = run(U, 8.2, 5)
     assert np.linalg.norm(U5) <= n0 * (1 + 1e-12)
     assert math.isfinite(float(np.linalg.norm(U5)))
+
+
+@pytest.mark.parametrize("shape", [(32, 28, 16), (64, 36, 44), (8, 12, 20)])
+@pytest.mark.parametrize("bc", [0, 1])
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_fp16_field_fp32(lib, shape, bc, scheme):
+    """FP16 face coefficients (14 instead of 20 bytes per cell and update)
+    against the oracle run on the same FP16-rounded coefficients."""
+    inst = _inst(*shape, bc, seed=5 * sum(shape) + bc, nsteps=3)
+    ref = oracle_run(inst, FP32, inst.nsteps, scheme=scheme, fp16=True)
+    floor = rel_linf(oracle_run(inst, FP32, inst.nsteps, scheme=scheme, fp16=True, round_each_step=True), ref)
+    g = Grid3(lib, inst, FP32, scheme=scheme, fp16=True)
+    try:
+        got = g.step(inst.nsteps)
+    finally:
+        g.close()
+    assert rel_linf(got, ref) < max(FP32_TOL, 3.0 * floor)
+
+
+def test_fp16_field_needs_fp32(lib):
+    inst = _inst(8, 8, 8, 1, seed=1, nsteps=1)
+    h = lib.aniso3_create(8, 8, 8, inst.dx, inst.dy, inst.dz, inst.chi_par, 0.0, 1)
+    try:
+        lib.aniso3_set_option(h, lib.ANISO_OPT_FIELD_FP16, 1)
+        with pytest.raises(lib.AnisoError) as ei:
+            lib.aniso3_set_field(h, 0x1000, 0x1000, 0x1000)  # FP64 handle: refused before any access
+        assert ei.value.code == lib.ANISO_ERR_ARG
+    finally:
+        lib.aniso3_destroy(h)
