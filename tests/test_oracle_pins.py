@@ -47,6 +47,113 @@ def test_vanleer_four_argument_is_harmonic_mean_and_symmetric():
     assert O.limit4(1.0, 2.0, 3.0, -4.0) == 0.0
 
 
+# The two other limiters the paper names after Eq. vanLeer (minmod and the
+# monotonized central limiter, defined in the limiter literature it cites):
+#   minmod(a, b) = s * min(|a|, |b|)
+#   MC(a, b)     = s * min(2|a|, 2|b|, |a + b| / 2)
+# with s the common sign of a and b, and 0 unless a and b share a strict sign.
+# The expected values below were worked out by hand from those definitions;
+# L(a, b) is read through L(a, b, a, b) = L(L(a,b), L(a,b)) = L(a, b), which
+# holds for all three limiters since L(x, x) = x.
+
+@pytest.mark.parametrize("a,b,want", [
+    (1.0, 3.0, 1.0), (3.0, 1.0, 1.0), (-1.0, -3.0, -1.0), (-3.0, -0.5, -0.5),
+    (2.5, 2.5, 2.5), (1.0, -3.0, 0.0), (-1.0, 3.0, 0.0), (0.0, 2.0, 0.0), (2.0, 0.0, 0.0),
+])
+def test_minmod_two_argument_values(a, b, want):
+    assert O.limit4(a, b, a, b, O.LIM_MINMOD) == want
+
+
+@pytest.mark.parametrize("a,b,want", [
+    (1.0, 3.0, 2.0),      # 2|a| = 2 binds (|a+b|/2 = 2 too)
+    (1.0, 10.0, 2.0),     # 2|a| binds
+    (1.0, 1.2, 1.1),      # |a+b|/2 binds: a dropped /2 gives 2, a dropped factor 2 gives 1
+    (3.0, 1.0, 2.0),      # 2|b| binds
+    (4.0, 6.0, 5.0),
+    (-1.0, -3.0, -2.0), (-4.0, -6.0, -5.0), (-1.0, -1.2, -1.1),
+    (1.0, -3.0, 0.0), (-2.0, 5.0, 0.0), (0.0, 1.0, 0.0), (1.0, 0.0, 0.0),
+])
+def test_mc_two_argument_values(a, b, want):
+    assert O.limit4(a, b, a, b, O.LIM_MC) == pytest.approx(want, rel=1e-15, abs=0.0)
+
+
+def test_mc_nesting_pairs_each_cells_differences():
+    # L(a,b,c,d) = L(L(a,b), L(c,d)) as written after Eq. vanLeer.  For MC
+    # the nesting is not symmetric, so the pairing is visible:
+    #   MC(MC(1,3), MC(4,6)) = MC(2, 5)   = min(4, 10, 3.5)  = 3.5
+    #   MC(MC(1,4), MC(3,6)) = MC(2, 4.5) = min(4, 9, 3.25)  = 3.25
+    #   MC(MC(1,6), MC(3,4)) = MC(2, 3.5) = min(4, 7, 2.75)  = 2.75
+    assert O.limit4(1.0, 3.0, 4.0, 6.0, O.LIM_MC) == pytest.approx(3.5, rel=1e-15)
+    assert O.limit4(1.0, 4.0, 3.0, 6.0, O.LIM_MC) == pytest.approx(3.25, rel=1e-15)
+    assert O.limit4(1.0, 6.0, 3.0, 4.0, O.LIM_MC) == pytest.approx(2.75, rel=1e-15)
+    assert O.limit4(-1.0, -3.0, -4.0, -6.0, O.LIM_MC) == pytest.approx(-3.5, rel=1e-15)
+    # one pair of mixed sign zeroes the inner level, hence the whole value
+    assert O.limit4(1.0, 3.0, 4.0, -6.0, O.LIM_MC) == 0.0
+    # minmod nests to the smallest magnitude of the four when all agree
+    assert O.limit4(1.0, 3.0, 4.0, 6.0, O.LIM_MINMOD) == 1.0
+    assert O.limit4(-6.0, -4.0, -3.0, -2.0, O.LIM_MINMOD) == -2.0
+
+
+# Slopes (up, down) = (T[i,2] - T[i,1], T[i,1] - T[i,0]) of the five columns
+# of a 3-row grid; the middle row is the only one with a non-zero limited
+# difference (rows 0 and 2 see a mirrored ghost, so one inner argument is 0).
+_SLOPES = [(4.0, 6.0), (1.0, 3.0), (-1.0, 2.0), (-2.0, -6.0), (-1.0, -1.0)]
+# Transverse coefficients e at x faces 0..4 of the middle row (face 4 is the
+# zero-flux boundary face, stored as 0).
+_E = [1.0, 1.0, 1.0, 0.5, 0.0]
+# Worked by hand.  Face i+1/2 takes L(L(up_{i+1}, down_{i+1}), L(up_i, down_i))
+# (first DeltaT-bar equation after Eq. yup); column 2 is mixed-sign, so faces
+# 1 and 2 are 0.  With mu = 0.5 and no implicit part, T* - T at cell i is
+# mu (e_i dT_i - e_{i-1} dT_{i-1}):
+#   MC:     dT = [MC(MC(1,3),MC(4,6)) = 3.5, 0, 0, MC(-1,-4) = -2, 0]
+#           delta = 0.5 [3.5, -3.5, 0, -1, 1]
+#   minmod: dT = [minmod(1, 4) = 1, 0, 0, minmod(-1, -2) = -1, 0]
+#           delta = 0.5 [1, -1, 0, -0.5, 0.5]
+_WANT_DELTA = {
+    O.LIM_MC: [1.75, -1.75, 0.0, -0.5, 0.5],
+    O.LIM_MINMOD: [0.5, -0.5, 0.0, -0.25, 0.25],
+}
+
+
+def _slope_grid():
+    T = np.empty((3, 5))
+    for i, (up, down) in enumerate(_SLOPES):
+        T[0, i] = 10.0
+        T[1, i] = 10.0 + down
+        T[2, i] = 10.0 + down + up
+    return T
+
+
+@pytest.mark.parametrize("lim", [O.LIM_MC, O.LIM_MINMOD])
+def test_x_update_transverse_term_on_known_slopes(lim):
+    T = _slope_grid()
+    zero = np.zeros_like(T)
+    e = np.zeros_like(T)
+    e[1, :] = _E
+    e[0, :4] = e[2, :4] = 1.0                # rows 0, 2: limited difference is 0 anyway
+    co = O.Coeffs(zero, e, zero, zero)       # no implicit part: T* = T + mu dF
+    out = O.xsweep(T, co, O.BC_ZEROFLUX, lamx=7.0, mu=0.5, limiter=lim)
+    np.testing.assert_array_equal(out[0], T[0])
+    np.testing.assert_array_equal(out[2], T[2])
+    np.testing.assert_allclose(out[1] - T[1], _WANT_DELTA[lim], rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("lim", [O.LIM_MC, O.LIM_MINMOD])
+def test_y_update_transverse_term_on_known_slopes(lim):
+    # The same numbers through Eq. yup: columns become rows (second
+    # DeltaT-bar equation after Eq. yup, x-differences of rows j and j+1).
+    T = _slope_grid().T.copy()               # [5][3]: column 1 holds the slopes
+    zero = np.zeros_like(T)
+    f = np.zeros_like(T)
+    f[:, 1] = _E
+    f[:4, 0] = f[:4, 2] = 1.0
+    co = O.Coeffs(zero, zero, zero, f)
+    out = O.ysweep(T, co, O.BC_ZEROFLUX, lamy=7.0, mu=0.5, limiter=lim)
+    np.testing.assert_array_equal(out[:, 0], T[:, 0])
+    np.testing.assert_array_equal(out[:, 2], T[:, 2])
+    np.testing.assert_allclose(out[:, 1] - T[:, 1], _WANT_DELTA[lim], rtol=0, atol=1e-14)
+
+
 # ------------------------------------------------------- tridiagonal solves
 
 def _dd_system(rng, n):
