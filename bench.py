@@ -97,7 +97,7 @@ def measured_peak():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("sweep_kernels.cuh", "line2_kernel.cuh", "line3_kernel.cuh", "line4_kernel.cuh",
+    for f in ("sweep_kernels.cuh", "line2_kernel.cuh", "line4_kernel.cuh",
               "aniso_internal.h", "util_kernels.cu", "kernels_f32.cu", "kernels_line4.cu",
               "kernels_3d.cu"):
         h.update(open(os.path.join(ROOT, "paper_1008_0861_gb300", "csrc", f), "rb").read())

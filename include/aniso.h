@@ -78,9 +78,8 @@ enum {
     ANISO_OPT_FAST_PATH = 8,  /* kernels of the x-then-y order with a transposed intermediate:
                                  3 (default): warp-autonomous line kernel (coalesced flux phase,
                                  per-lane segment elimination, shuffle-only line solve);
-                                 1: block-synchronous vectorised line kernel; 2: the same with rows
-                                 staged by bulk asynchronous copies in persistent blocks;
-                                 0: general kernels only */
+                                 1: block-synchronous vectorised line kernel;
+                                 0: general kernels only; 2 is not a valid value */
     ANISO_OPT_SEGMENT = 9,    /* cells per thread segment of the vectorised kernels, in 16-byte
                                  chunks (0 = default 4; larger: fewer threads per line and so a
                                  shallower PCR) */

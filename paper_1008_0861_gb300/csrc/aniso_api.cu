@@ -125,8 +125,7 @@ struct aniso_ctx {
     int vec() const { return prec == PREC_FP64 ? 2 : 4; }
     // Grid shapes the vectorised x-then-y path handles: both line lengths a
     // multiple of the 16-byte vector and short enough for transposed output.
-    // 4: warp-per-line kernel (line4, option value 3), 3: staged persistent
-    // kernel (line3, option value 2), 2: line2, 0: none of them.
+    // 4: warp-per-line kernel (line4, option value 3), 2: line2, 0: none of them.
     int fast_kind() const
     {
         int a, b, c;
@@ -134,9 +133,6 @@ struct aniso_ctx {
         if (fast == 3 && line4_config(prec, nx, true, l4_warps, seg_chunks, &a, &b, &c, &d) &&
             line4_config(prec, ny, true, l4_warps, seg_chunks, &a, &b, &c, &d))
             return 4;
-        if (fast == 2 && line3_config(prec, field_fp16, nx, true, seg_chunks, &a, &b, &c, &d) &&
-            line3_config(prec, field_fp16, ny, true, seg_chunks, &a, &b, &c, &d))
-            return 3;
         if (line2_config(prec, nx, true, &a, &b, &c, &d, seg_chunks) &&
             line2_config(prec, ny, true, &a, &b, &c, &d, seg_chunks))
             return 2;
@@ -243,7 +239,7 @@ extern "C" int aniso_set_option(aniso_t h, int key, long long v)
         h->profile = v != 0;
         break;
     case ANISO_OPT_FAST_PATH:
-        if (v < 0 || v > 3) return fail(ANISO_ERR_ARG, "bad fast-path value %lld", v);
+        if (v < 0 || v > 3 || v == 2) return fail(ANISO_ERR_ARG, "bad fast-path value %lld", v);
         h->fast = (int)v;
         drop_graph(h);
         break;
@@ -372,53 +368,6 @@ static int enqueue_line2(aniso_ctx *h, const void *in, void *out, const void *g,
     return ANISO_OK;
 }
 
-// One staged persistent line update (line3_kernel).
-static int enqueue_line3(aniso_ctx *h, const void *in, void *out, const void *g, const void *e, int n,
-                         int nlines, int per_line, int per_cross, double lam, double mu, bool transposed,
-                         int kind, cudaStream_t s, std::vector<int> *pairs)
-{
-    Line3Args a{};
-    a.jobs = nullptr;
-    a.njobs = 1;
-    a.limiter = h->limiter;
-    a.err = h->err;
-    Line3Job &J = a.one;
-    J.Tin = in;
-    J.Tout = out;
-    J.g = g;
-    J.e = e;
-    J.lam = lam;
-    J.mu = mu;
-    J.n = n;
-    J.nlines = nlines;
-    J.per_line = per_line;
-    J.per_cross = per_cross;
-    J.transpose_out = transposed ? 1 : 0;
-    int nthreads;
-    size_t smem;
-    if (!line3_config(h->prec, h->field_fp16, n, transposed, h->seg_chunks, &J.team, &J.lines_per_block,
-                      &nthreads, &smem))
-        return fail(ANISO_ERR_UNSUPPORTED, "staged line kernel cannot take n=%d", n);
-    J.group0 = 0;
-    J.ngroups = (nlines + J.lines_per_block - 1) / J.lines_per_block;
-    a.total_groups = J.ngroups;
-    a.work_off = (int)line3_stage_bytes(h->prec, h->field_fp16, n, J.team, J.lines_per_block);
-    int pidx = -1;
-    const unsigned rec_flags = pairs ? cudaEventRecordExternal : cudaEventRecordDefault;
-    if (h->profile) {
-        pidx = h->prof.take(kind);
-        if (pidx < 0) return fail(ANISO_ERR_CUDA, "event creation failed");
-        CU(cudaEventRecordWithFlags(h->prof.pool[pidx].a, s, rec_flags));
-    }
-    CU(launch_line3(h->prec, h->field_fp16, a, nthreads, smem, s));
-    if (h->profile) {
-        CU(cudaEventRecordWithFlags(h->prof.pool[pidx].b, s, rec_flags));
-        if (pairs) pairs->push_back(pidx);
-        else h->prof.pending.push_back(pidx);
-    }
-    return ANISO_OK;
-}
-
 // Fast path of one x-then-y step: the x-update reads T row-major and writes T*
 // column-major; the y-update reads T*'s columns as contiguous lines (with the
 // transposed y coefficients) and writes T back row-major.
@@ -435,13 +384,6 @@ static int enqueue_fast_step(aniso_ctx *h, void *T, double dt, cudaStream_t s, s
     const double mu = h->chi_par * dt / (h->dx * h->dy);
     const int per = h->bc == ANISO_BC_PERIODIC;
     const int fk = h->fast_kind();
-    if (fk == 3) {
-        int rc = enqueue_line3(h, T, h->tstar, h->cxx, h->cxy, h->nx, h->ny, per, per, lamx, mu, true,
-                               ANISO_KERNEL_XSWEEP, s, pairs);
-        if (rc) return rc;
-        return enqueue_line3(h, h->tstar, T, h->cyyT, h->cyxT, h->ny, h->nx, per, per, lamy, mu, true,
-                             ANISO_KERNEL_YSWEEP, s, pairs);
-    }
     int rc = enqueue_line2(h, T, h->tstar, h->cxx, h->cxy, h->nx, h->ny, per, per, lamx, mu, true,
                            ANISO_KERNEL_XSWEEP, s, pairs, fk == 4);
     if (rc) return rc;
@@ -515,10 +457,6 @@ static int enqueue_sweep(aniso_ctx *h, int dir, const void *in, void *out, doubl
     if (dir == ANISO_DIR_X) {
         int t1, t2, t3;
         size_t t4;
-        if (!kahan && !h->dirichlet() && h->fast == 2 && aligned16(in) && aligned16(out) &&
-            line3_config(h->prec, h->field_fp16, h->nx, false, h->seg_chunks, &t1, &t2, &t3, &t4))
-            return enqueue_line3(h, in, out, h->cxx, h->cxy, h->nx, h->ny, per, per, lamx, mu, false,
-                                 ANISO_KERNEL_XSWEEP, s, pairs);
         if (!kahan && !h->dirichlet() && h->fast == 3 && aligned16(in) && aligned16(out) &&
             line4_config(h->prec, h->nx, false, h->l4_warps, h->seg_chunks, &t1, &t2, &t3, &t4))
             return enqueue_line2(h, in, out, h->cxx, h->cxy, h->nx, h->ny, per, per, lamx, mu, false,
@@ -1019,11 +957,10 @@ static int batch_build(aniso_batch *b, void *const *T, const double *dt, const i
     // Every (global step, phase) launch is one list of line jobs (x) and one
     // of column jobs (y).  Identical lists are shared.
     struct Launch {
-        int kind;  // 0 line, 1 col, 2/3 line2 (x/y), 4/5 line3 (x/y), 7/8 line4 (x/y)
+        int kind;  // 0 line, 1 col, 2/3 line2 (x/y), 7/8 line4 (x/y)
         size_t offset;
         int njobs, nblocks, nthreads;
         size_t smem;
-        int work_off = 0;
         // consecutive launches with the same group >= 0 run concurrently
         // (one branch each) and are joined before the next launch
         int group = -1;
@@ -1172,82 +1109,15 @@ static int batch_build(aniso_batch *b, void *const *T, const double *dt, const i
         }
     };
 
-    // line3 jobs: one launch per block size (normally a single launch)
-    auto add_line3 = [&](std::vector<Line3Job> &all, std::vector<int> &nts, int phase_xy) {
-        if (all.empty()) return;
-        std::vector<int> sizes(nts);
-        std::sort(sizes.begin(), sizes.end());
-        sizes.erase(std::unique(sizes.begin(), sizes.end()), sizes.end());
-        for (int NT : sizes) {
-            std::vector<Line3Job> jobs;
-            for (size_t k = 0; k < all.size(); ++k)
-                if (nts[k] == NT) jobs.push_back(all[k]);
-            std::stable_sort(jobs.begin(), jobs.end(), [](const Line3Job &a, const Line3Job &c) {
-                return (long long)a.n * a.nlines > (long long)c.n * c.nlines;
-            });
-            // one shared-memory layout for the whole launch: staging sized for the
-            // largest job, working arrays after it
-            int groups = 0;
-            size_t stage = 0, work = 0;
-            for (auto &J : jobs) {
-                J.group0 = groups;
-                J.ngroups = (J.nlines + J.lines_per_block - 1) / J.lines_per_block;
-                groups += J.ngroups;
-                const size_t st = line3_stage_bytes(prec, fp16, J.n, J.team, J.lines_per_block);
-                stage = std::max(stage, st);
-                work = std::max(work, line3_smem_bytes(prec, fp16, J.n, J.team, J.lines_per_block) - st);
-            }
-            Launch L{phase_xy == 0 ? 4 : 5, blob.size(), (int)jobs.size(), groups, NT, stage + work};
-            L.work_off = (int)stage;
-            const unsigned char *p = reinterpret_cast<const unsigned char *>(jobs.data());
-            blob.insert(blob.end(), p, p + jobs.size() * sizeof(Line3Job));
-            while (blob.size() % 16) blob.push_back(0);
-            launches.push_back(L);
-        }
-    };
-
     for (int s = 0; s < max_steps; ++s) {
         for (int phase = 0; phase < 2; ++phase) {
             std::vector<LineJob> xl;
             std::vector<ColJob> yl;
             std::vector<Line2Job> fl, fl4;
-            std::vector<Line3Job> tl;
-            std::vector<int> tl_nt;
             std::vector<Launch> solo;
             for (int k = 0; k < n; ++k) {
                 if (s >= nsteps[k]) continue;
                 aniso_ctx *h = b->hs[k];
-                if (use_fast(h, T[k]) && h->fast_kind() == 3) {
-                    const int per = h->bc == ANISO_BC_PERIODIC;
-                    Line3Job J{};
-                    int nt;
-                    size_t sm;
-                    if (phase == 0) {
-                        J.Tin = T[k];
-                        J.Tout = h->tstar;
-                        J.g = h->cxx;
-                        J.e = h->cxy;
-                        J.lam = h->chi_par * dt[k] / (h->dx * h->dx);
-                        J.n = h->nx;
-                        J.nlines = h->ny;
-                    } else {
-                        J.Tin = h->tstar;
-                        J.Tout = T[k];
-                        J.g = h->cyyT;
-                        J.e = h->cyxT;
-                        J.lam = h->chi_par * dt[k] / (h->dy * h->dy);
-                        J.n = h->ny;
-                        J.nlines = h->nx;
-                    }
-                    J.mu = h->chi_par * dt[k] / (h->dx * h->dy);
-                    J.per_line = per;
-                    J.per_cross = per;
-                    J.transpose_out = 1;
-                    line3_config(prec, fp16, J.n, true, h->seg_chunks, &J.team, &J.lines_per_block, &nt, &sm);
-                    tl.push_back(J);
-                    tl_nt.push_back(nt);
-                    continue;
-                }
                 if (use_fast(h, T[k])) {
                     // x: T (rows) -> T* (column-major); y: T* (columns) -> T (rows)
                     const int per = h->bc == ANISO_BC_PERIODIC;
@@ -1340,7 +1210,6 @@ static int batch_build(aniso_batch *b, void *const *T, const double *dt, const i
                     yl.push_back(J);
                 }
             }
-            add_line3(tl, tl_nt, phase);
             add_line2(fl, phase);
             add_line4(fl4, phase);
             add_line(xl);
@@ -1382,15 +1251,6 @@ static int batch_build(aniso_batch *b, void *const *T, const double *dt, const i
             a.limiter = b->hs[0]->limiter;
             a.err = err;
             return launch_line4(prec, fp16, a, L.nblocks, L.nthreads, L.smem, st);
-        } else if (L.kind >= 4) {
-            Line3Args a{};
-            a.jobs = reinterpret_cast<const Line3Job *>(static_cast<unsigned char *>(b->d_jobs) + L.offset);
-            a.njobs = L.njobs;
-            a.total_groups = L.nblocks;
-            a.work_off = L.work_off;
-            a.limiter = b->hs[0]->limiter;
-            a.err = err;
-            return launch_line3(prec, fp16, a, L.nthreads, L.smem, st);
         } else if (L.kind >= 2) {
             Line2Args a{};
             a.jobs = reinterpret_cast<const Line2Job *>(static_cast<unsigned char *>(b->d_jobs) + L.offset);
@@ -1429,7 +1289,7 @@ static int batch_build(aniso_batch *b, void *const *T, const double *dt, const i
         while (L.group >= 0 && j < launches.size() && launches[j].group == L.group) ++j;
         int pidx = -1;
         if (b->profile) {
-            pidx = b->prof.take((L.kind == 0 || L.kind == 2 || L.kind == 4 || L.kind == 7)
+            pidx = b->prof.take((L.kind == 0 || L.kind == 2 || L.kind == 7)
                                     ? ANISO_KERNEL_XSWEEP
                                     : ANISO_KERNEL_YSWEEP);
             if (pidx < 0 || cudaEventRecordWithFlags(b->prof.pool[pidx].a, b->cap_stream,

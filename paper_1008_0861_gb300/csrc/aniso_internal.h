@@ -108,39 +108,6 @@ struct Line2Args {
 };
 constexpr int MAX_LINE2_TRANSPOSED = 2048;
 
-// Persistent, bulk-copy-staged line update (line3_kernel).  Groups of
-// lines_per_block lines; group0 = first global group index of the job.
-struct Line3Job {
-    const void *Tin;
-    void *Tout;
-    const void *g;
-    const void *e;
-    double lam, mu;
-    int n, nlines;
-    int per_line, per_cross;
-    int team, lines_per_block;
-    int transpose_out;
-    int group0, ngroups;
-};
-struct Line3Args {
-    const Line3Job *jobs;  // device array sorted by group0, or nullptr: use `one`
-    int njobs;
-    int total_groups;
-    int work_off;          // byte offset of the working arrays: past the largest staging area
-                           // of any job in the launch, so prefetches never touch them
-    int limiter;
-    unsigned *err;
-    Line3Job one;
-};
-// Returns false when line3 cannot take the line (alignment, shared memory).
-bool line3_config(int prec, int coef_fp16, int n, bool transposed, int seg_chunks, int *team,
-                  int *lines_per_block, int *nthreads, size_t *smem);
-size_t line3_smem_bytes(int prec, int coef_fp16, int n, int team, int lines_per_block);
-// staging bytes (offset of the working arrays) of one job
-size_t line3_stage_bytes(int prec, int coef_fp16, int n, int team, int lines_per_block);
-cudaError_t launch_line3(int prec, int coef_fp16, const Line3Args &a, int nthreads, size_t smem,
-                         cudaStream_t s);
-
 // Launch configuration helpers (host).
 // line2: returns false when the line cannot use the vectorised kernel.
 // seg_chunks: target 16-byte chunks per segment (0 = default of 4).

@@ -1,5 +1,5 @@
 // FP32 instantiations of the sweep kernels (FP32 or FP16 face coefficients).
-#include "line3_kernel.cuh"
+#include "line2_kernel.cuh"
 
 namespace aniso {
 
@@ -70,38 +70,6 @@ cudaError_t launch_line2_f32(int coef_fp16, const Line2Args &a, int nblocks, int
                      : go2(line2_kernel<float, __half, false>, nblocks, nthreads, smem, s, a);
     return kahan ? go2(line2_kernel<float, float, true>, nblocks, nthreads, smem, s, a)
                  : go2(line2_kernel<float, float, false>, nblocks, nthreads, smem, s, a);
-}
-
-template <typename C> static cudaError_t launch3(const Line3Args &a, int nthreads, size_t smem, cudaStream_t s)
-{
-    cudaError_t err = prep(line3_kernel<float, C>, smem);
-    if (err != cudaSuccess) return err;
-    int per_sm = 0, dev = 0, sms = 0;
-    if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, line3_kernel<float, C>, nthreads, smem)) != cudaSuccess)
-        return err;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int grid = (per_sm > 0 ? per_sm : 1) * sms;
-    if (grid > a.total_groups) grid = a.total_groups;
-    line3_kernel<float, C><<<grid, nthreads, smem, s>>>(a);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_line3_f32(int coef_fp16, const Line3Args &a, int nthreads, size_t smem, cudaStream_t s)
-{
-    return coef_fp16 ? launch3<__half>(a, nthreads, smem, s) : launch3<float>(a, nthreads, smem, s);
-}
-
-size_t line3_smem_f32(int coef_fp16, int n, int team, int lpb)
-{
-    return coef_fp16 ? (size_t)line3_plan<float, __half>(n, team, lpb).bytes
-                     : (size_t)line3_plan<float, float>(n, team, lpb).bytes;
-}
-
-size_t line3_stage_f32(int coef_fp16, int n, int team, int lpb)
-{
-    return coef_fp16 ? (size_t)line3_plan<float, __half>(n, team, lpb).work
-                     : (size_t)line3_plan<float, float>(n, team, lpb).work;
 }
 
 }  // namespace aniso

@@ -1,5 +1,5 @@
 // FP64 instantiations of the sweep kernels.
-#include "line3_kernel.cuh"
+#include "line2_kernel.cuh"
 
 namespace aniso {
 
@@ -40,25 +40,5 @@ cudaError_t launch_line2_f64(const Line2Args &a, int nblocks, int nthreads, size
     line2_kernel<double, double, false><<<nblocks, nthreads, smem, s>>>(a);
     return cudaGetLastError();
 }
-
-cudaError_t launch_line3_f64(const Line3Args &a, int nthreads, size_t smem, cudaStream_t s)
-{
-    cudaError_t err = prep(line3_kernel<double, double>, smem);
-    if (err != cudaSuccess) return err;
-    int per_sm = 0, dev = 0, sms = 0;
-    if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, line3_kernel<double, double>, nthreads, smem)) !=
-        cudaSuccess)
-        return err;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int grid = (per_sm > 0 ? per_sm : 1) * sms;
-    if (grid > a.total_groups) grid = a.total_groups;
-    line3_kernel<double, double><<<grid, nthreads, smem, s>>>(a);
-    return cudaGetLastError();
-}
-
-size_t line3_smem_f64(int n, int team, int lpb) { return (size_t)line3_plan<double, double>(n, team, lpb).bytes; }
-
-size_t line3_stage_f64(int n, int team, int lpb) { return (size_t)line3_plan<double, double>(n, team, lpb).work; }
 
 }  // namespace aniso

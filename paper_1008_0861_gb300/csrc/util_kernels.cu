@@ -12,13 +12,6 @@ cudaError_t launch_col_f64(const ColArgs &a, int nblocks, int nthreads, size_t s
 cudaError_t launch_line2_f32(int coef_fp16, const Line2Args &a, int nblocks, int nthreads, size_t smem,
                              cudaStream_t s, bool kahan);
 cudaError_t launch_line2_f64(const Line2Args &a, int nblocks, int nthreads, size_t smem, cudaStream_t s);
-cudaError_t launch_line3_f32(int coef_fp16, const Line3Args &a, int nthreads, size_t smem, cudaStream_t s);
-cudaError_t launch_line3_f64(const Line3Args &a, int nthreads, size_t smem, cudaStream_t s);
-size_t line3_smem_f32(int coef_fp16, int n, int team, int lpb);
-size_t line3_smem_f64(int n, int team, int lpb);
-size_t line3_stage_f32(int coef_fp16, int n, int team, int lpb);
-size_t line3_stage_f64(int n, int team, int lpb);
-
 static int pow2floor(int v)
 {
     int p = 1;
@@ -135,50 +128,6 @@ bool line2_config(int prec, int n, bool transposed, int *team, int *lines_per_bl
     }
 }
 
-size_t line3_smem_bytes(int prec, int coef_fp16, int n, int team, int lines_per_block)
-{
-    return prec == PREC_FP64 ? line3_smem_f64(n, team, lines_per_block)
-                             : line3_smem_f32(coef_fp16, n, team, lines_per_block);
-}
-
-size_t line3_stage_bytes(int prec, int coef_fp16, int n, int team, int lines_per_block)
-{
-    return prec == PREC_FP64 ? line3_stage_f64(n, team, lines_per_block)
-                             : line3_stage_f32(coef_fp16, n, team, lines_per_block);
-}
-
-// Same segment choice as line2; the block size is lowered (fewer lines per
-// block) until the staged rows plus the working arrays fit two blocks per SM,
-// or one block at worst.
-bool line3_config(int prec, int coef_fp16, int n, bool transposed, int seg_chunks, int *team,
-                  int *lines_per_block, int *nthreads, size_t *smem)
-{
-    const int N = prec == PREC_FP64 ? 2 : 4;
-    if (n % N != 0 || n < 2 * N) return false;
-    if (coef_fp16 && n % 8 != 0) return false;
-    if (transposed && n > MAX_LINE2_TRANSPOSED) return false;
-    const int sc = seg_chunks > 0 ? seg_chunks : 4;
-    const int m = n / N;
-    int P = pow2ceil((m + sc - 1) / sc);
-    if (P > m) P = pow2floor(m);
-    if (P > 512) P = 512;
-    for (int budget : {110 * 1024, (int)SMEM_LIMIT - 2048}) {
-        for (int NT = P > 256 ? P : 256; NT >= P && NT >= 32; NT /= 2) {
-            const int lpb = NT / P;
-            if (transposed && lpb % N != 0) continue;
-            const size_t sm = line3_smem_bytes(prec, coef_fp16, n, P, lpb);
-            if (sm <= (size_t)budget) {
-                *team = P;
-                *lines_per_block = lpb;
-                *nthreads = NT;
-                *smem = sm;
-                return true;
-            }
-        }
-    }
-    return false;
-}
-
 // Warp-autonomous line kernel: a team of P <= 32 lanes per line with about
 // seg_chunks (default 4: 16 FP32 / 8 FP64 cells) chunks per lane or more, at
 // most 16 chunks a lane; the warp's shared area holds 3 arrays of its lines' chunks.  Blocks
@@ -225,12 +174,6 @@ cudaError_t launch_source(int prec, void *T, const void *Q, double dt, size_t n,
     else
         source_kernel<float><<<blocks, threads, 0, s>>>(static_cast<float *>(T), static_cast<const float *>(Q), (float)dt, n);
     return cudaGetLastError();
-}
-
-cudaError_t launch_line3(int prec, int coef_fp16, const Line3Args &a, int nthreads, size_t smem, cudaStream_t s)
-{
-    if (prec == PREC_FP64) return launch_line3_f64(a, nthreads, smem, s);
-    return launch_line3_f32(coef_fp16, a, nthreads, smem, s);
 }
 
 cudaError_t launch_line2(int prec, int coef_fp16, const Line2Args &a, int nblocks, int nthreads,

@@ -36,7 +36,7 @@ class GpuGrid:
         P.aniso_set_option(self.h, P.ANISO_OPT_LIMITER, limiter)
         P.aniso_set_option(self.h, P.ANISO_OPT_ORDER, order)
         P.aniso_set_option(self.h, P.ANISO_OPT_GRAPH, int(graph))
-        if fast is not None:  # None: the library default (3); 1 line2, 2 staged line3, 0 general
+        if fast is not None:  # None: the library default (3); 1 line2, 0 general
             P.aniso_set_option(self.h, P.ANISO_OPT_FAST_PATH, int(fast))
         self.bx = torch.tensor(inst.bx, dtype=self.dtype, device="cuda")
         self.by = torch.tensor(inst.by, dtype=self.dtype, device="cuda")
