@@ -277,12 +277,14 @@ int aniso_batch_kernel_count(aniso_batch_t b, long long *kernels);
  * `stream` is a cudaStream_t (NULL: the legacy default stream); the call is
  * asynchronous on it.
  * Working memory (the face coefficients and T*) lives in one fixed device
- * array of 20 MiB compiled into the library, which every GPU that loads the
- * library holds until the process exits: at most 1,048,576 cells in FP32
- * and 524,288 in FP64 (larger grids fail with ANISO_ERR_ARG and a message),
- * and ny <= 1024.  The first call on a device looks up that array's device
- * address (once per device, with the device current); make that first call
- * before any stream capture.  Every call reuses the same array, so calls whose
+ * array of 20 MiB compiled into the library, allocated on first use per
+ * device and then held by that GPU until the process exits: at most
+ * 1,048,576 cells in FP32 and 524,288 in FP64 (larger grids fail with
+ * ANISO_ERR_ARG and a message), and ny <= 1024.  Each call made outside a
+ * stream capture looks up that array's device address (with the device
+ * current); a call inside a capture reuses the address of the last such call
+ * on the device, so make a first call before any stream capture
+ * (ANISO_ERR_STATE otherwise).  Every call reuses the same array, so calls whose
  * GPU work overlaps (other streams or host threads) race and corrupt each
  * other: serialise them.  Non-finite results are not reported by this call. */
 int aniso_step_noalloc(int nx, int ny, double dx, double dy, double chi_par, double chi_perp, int bc,

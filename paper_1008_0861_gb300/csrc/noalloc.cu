@@ -9,8 +9,9 @@
 // keeps all of its working memory in one file-scope device array instead:
 //
 //   g_noalloc_scratch: NOALLOC_SCRATCH_BYTES (20 MiB + 256 bytes), allocated
-//   by the CUDA runtime when the library is loaded on a device and held by
-//   every GPU that loads the library until the process exits.
+//   by the CUDA runtime on first use per device (with lazy module loading,
+//   when the library's module is first loaded there) and then held by that
+//   GPU until the process exits.
 //
 // Layout of the array for a call with `cells` = nx*ny cells of `es` bytes:
 //   [0, 256)                 : non-finite flag (cleared at the start of each call)
@@ -51,20 +52,32 @@ int noalloc_fail(int code, const char *msg)
     return code;
 }
 
-// Device address of the scratch array on the current device (looked up once
-// per device, with that device current).
-int scratch_address(void **out)
+// Device address of the scratch array on the current device.  Outside a
+// stream capture it is looked up again on every call (with the device
+// current), so a cudaDeviceReset, after which the module is loaded afresh and
+// the array may sit elsewhere, never leaves a stale address behind.  Inside a
+// capture only the address of the last uncaptured call on this device is
+// used: the lookup itself may load the module, which a capture does not allow.
+int scratch_address(cudaStream_t s, void **out)
 {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return noalloc_fail(ANISO_ERR_CUDA, cudaGetErrorString(e));
     if (dev < 0 || dev >= MAX_DEVICES) return noalloc_fail(ANISO_ERR_UNSUPPORTED, "device index out of range");
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+        (void)cudaGetLastError();  // the query's own error is not sticky; treat as capturing
+        cs = cudaStreamCaptureStatusActive;
+    }
     std::lock_guard<std::mutex> lock(g_mutex);
-    if (!g_scratch_ptr[dev]) {
+    if (cs == cudaStreamCaptureStatusNone) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p) return noalloc_fail(ANISO_ERR_CUDA, cudaGetErrorString(e));
         g_scratch_ptr[dev] = p;
+    } else if (!g_scratch_ptr[dev]) {
+        return noalloc_fail(ANISO_ERR_STATE,
+                            "aniso_step_noalloc: the first call on a device must come before any stream capture");
     }
     *out = g_scratch_ptr[dev];
     return ANISO_OK;
@@ -99,10 +112,10 @@ extern "C" int aniso_step_noalloc(int nx, int ny, double dx, double dy, double c
         return noalloc_fail(ANISO_ERR_UNSUPPORTED, "aniso_step_noalloc: needs ny <= 1024 and nx within the line limit");
     if (nsteps == 0) return ANISO_OK;
 
-    void *base = nullptr;
-    int rc = scratch_address(&base);
-    if (rc) return rc;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    void *base = nullptr;
+    int rc = scratch_address(s, &base);
+    if (rc) return rc;
     unsigned char *b = static_cast<unsigned char *>(base);
     unsigned *err = reinterpret_cast<unsigned *>(b);
     void *tstar = b + 256;
