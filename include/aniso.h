@@ -224,6 +224,15 @@ int aniso_batch_create(int n, const aniso_t *hs, aniso_batch_t *out);
  * Asynchronous. */
 int aniso_step_batched(aniso_batch_t b, void *const *T, const double *dt, const int *nsteps);
 
+/* aniso_step_batched on host arrays: T_host[k] is a host array of grid k's
+ * nx*ny values (handle precision; page-locked memory makes the copies
+ * asynchronous DMA, pageable memory works too).  Each grid is copied into a
+ * device buffer the batch owns (allocated on the first call, freed by
+ * aniso_batch_destroy), the batched call runs as above, and the results are
+ * copied back.  Returns when T_host holds the result (synchronises the
+ * batch's stream).  Errors: as aniso_step_batched, ANISO_ERR_OOM. */
+int aniso_step_batched_host(aniso_batch_t b, void *const *T_host, const double *dt, const int *nsteps);
+
 void aniso_batch_destroy(aniso_batch_t b);
 
 /* Block-shape autotuner for aniso_step_batched (the batched configuration

@@ -55,7 +55,7 @@ ANISO_KERNEL_TRANSPOSE = 2
 EXPORTED = ("aniso_create", "aniso_set_option", "aniso_set_field", "aniso_step", "aniso_sweep",
             "aniso_total", "aniso_get_state", "aniso_set_state", "aniso_sync",
             "aniso_kernel_times", "aniso_destroy", "aniso_last_error", "aniso_batch_create",
-            "aniso_step_batched", "aniso_batch_destroy", "aniso_step_noalloc",
+            "aniso_step_batched", "aniso_step_batched_host", "aniso_batch_destroy", "aniso_step_noalloc",
             "aniso_batch_autotune", "aniso_autotune_candidate", "aniso_set_source",
             "aniso_batch_kernel_count", "aniso_set_nonlinear",
             "aniso3_create", "aniso3_set_option", "aniso3_set_field", "aniso3_step",
@@ -97,6 +97,7 @@ def load():
         "aniso_last_error": (ctypes.c_char_p, []),
         "aniso_batch_create": (i, [i, P(vp), P(vp)]),
         "aniso_step_batched": (i, [vp, P(vp), P(d), P(i)]),
+        "aniso_step_batched_host": (i, [vp, P(vp), P(d), P(i)]),
         "aniso_batch_destroy": (None, [vp]),
         "aniso_step_noalloc": (i, [i, i, d, d, d, d, i, i, vp, vp, vp, d, i, vp]),
         "aniso_batch_autotune": (i, [vp, P(vp), P(d), i, i, P(i), P(d)]),
@@ -209,6 +210,24 @@ def aniso_step_batched(batch, Ts, dts, nsteps):
     darr = (ctypes.c_double * n)(*[float(x) for x in dts])
     narr = (ctypes.c_int * n)(*[int(x) for x in nsteps])
     _check(load().aniso_step_batched(batch, Tarr, darr, narr))
+
+
+def aniso_step_batched_host(batch, Ts, dts, nsteps):
+    """aniso_step_batched on host arrays (numpy arrays or CPU tensors, pinned
+    or not, in the batch's precision); returns when they hold the result."""
+    n = len(Ts)
+    ptrs = []
+    for t in Ts:
+        if hasattr(t, "data_ptr"):
+            if getattr(t, "is_cuda", False):
+                raise ValueError("aniso_step_batched_host takes host arrays")
+            ptrs.append(t.data_ptr())
+        else:
+            ptrs.append(t.ctypes.data)
+    Tarr = (ctypes.c_void_p * n)(*ptrs)
+    darr = (ctypes.c_double * n)(*[float(x) for x in dts])
+    narr = (ctypes.c_int * n)(*[int(x) for x in nsteps])
+    _check(load().aniso_step_batched_host(batch, Tarr, darr, narr))
 
 
 def aniso_batch_autotune(batch, Ts, dts, nsteps=2, reps=3):

@@ -907,6 +907,7 @@ struct aniso_batch {
     cudaStream_t side[kSide] = {};
     cudaEvent_t fork_ev = nullptr, join_ev[kSide] = {};
     long long kernels_per_call = 0;  // kernel nodes of the captured graph
+    std::vector<void *> dev_T;       // device copies of T for aniso_step_batched_host
 };
 
 extern "C" int aniso_batch_create(int n, const aniso_t *hs, aniso_batch_t *out)
@@ -1397,6 +1398,41 @@ extern "C" int aniso_step_batched(aniso_batch_t b, void *const *T, const double 
     return ANISO_OK;
 }
 
+// aniso_step_batched on host buffers: each grid's T is copied to a device
+// buffer the batch owns, the batched call runs on the device, and the result
+// is copied back; returns once the host arrays hold it.
+extern "C" int aniso_step_batched_host(aniso_batch_t b, void *const *T_host, const double *dt, const int *nsteps)
+{
+    TraceRange trace("aniso_step_batched_host");
+    if (!b) return fail(ANISO_ERR_ARG, "aniso_step_batched_host: null batch");
+    if (!T_host || !dt || !nsteps) return fail(ANISO_ERR_ARG, "aniso_step_batched_host: null array");
+    const int n = (int)b->hs.size();
+    for (int k = 0; k < n; ++k)
+        if (!T_host[k]) return fail(ANISO_ERR_ARG, "aniso_step_batched_host: T_host[%d] is NULL", k);
+    if ((int)b->dev_T.size() != n) {
+        for (int k = 0; k < n; ++k) {
+            void *p = nullptr;
+            if (cudaMalloc(&p, b->hs[k]->cells() * b->hs[k]->esz()) != cudaSuccess) {
+                (void)cudaGetLastError();
+                for (void *q : b->dev_T) cudaFree(q);
+                b->dev_T.clear();
+                return fail(ANISO_ERR_OOM, "aniso_step_batched_host: device copy of grid %d", k);
+            }
+            b->dev_T.push_back(p);
+        }
+    }
+    for (int k = 0; k < n; ++k)
+        CU(cudaMemcpyAsync(b->dev_T[k], T_host[k], b->hs[k]->cells() * b->hs[k]->esz(), cudaMemcpyHostToDevice,
+                           b->stream));
+    int rc = aniso_step_batched(b, b->dev_T.data(), dt, nsteps);
+    if (rc) return rc;
+    for (int k = 0; k < n; ++k)
+        CU(cudaMemcpyAsync(T_host[k], b->dev_T[k], b->hs[k]->cells() * b->hs[k]->esz(), cudaMemcpyDeviceToHost,
+                           b->stream));
+    CU(cudaStreamSynchronize(b->stream));
+    return ANISO_OK;
+}
+
 // Candidates of the block-shape autotuner: kernel option, warps per block
 // (warp-autonomous kernel), 16-byte chunks per lane / segment.
 struct Cand {
@@ -1548,6 +1584,7 @@ extern "C" void aniso_batch_destroy(aniso_batch_t b)
     }
     if (b->fork_ev) cudaEventDestroy(b->fork_ev);
     if (b->d_jobs) cudaFree(b->d_jobs);
+    for (void *p : b->dev_T) cudaFree(p);
     b->prof.destroy();
     delete b;
 }

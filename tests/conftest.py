@@ -21,3 +21,17 @@ def lib():
     import paper_1008_0861_gb300 as P
     P.load()  # raises if libaniso.so is absent
     return P
+
+
+def pytest_terminal_summary(terminalreporter):
+    """List the FP32 cases whose tolerance was raised above 1e-4 by the
+    problem's own FP32 noise floor (tests/gpu_util.py: fp32_tol)."""
+    try:
+        import gpu_util
+    except Exception:
+        return
+    cases = getattr(gpu_util, "LOOSE_FP32_CASES", [])
+    if cases:
+        terminalreporter.section("FP32 cases with a tolerance above 1e-4 (noise floor)")
+        for c in cases:
+            terminalreporter.write_line(c)

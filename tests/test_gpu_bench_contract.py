@@ -43,10 +43,19 @@ def _check_common(d, steps, warmup):
 
 
 def test_batched_line():
-    d = _run(["--instances", "8", "--steps", "3", "--warmup", "3", "--no-cpu-baseline", "--no-tune"])
+    d = _run(["--instances", "8", "--steps", "3", "--warmup", "3", "--no-cpu-baseline", "--no-tune",
+              "--no-big"])
     _check_common(d, 3, 3)
     assert d["dtype"] == "f32"
-    assert d["accuracy"]["rel_linf_vs_fp64_oracle"] < 1e-4
+    acc = d["accuracy"]
+    assert acc["instances"] == 8 and acc["oracle_sample"]["instances"] == 8
+    # FP64 on the GPU after 200 steps: rounding-order differences from the
+    # oracle grow with the scheme's own sensitivity, so only a loose bound
+    assert acc["oracle_sample"]["fp64_gpu_max_rel_linf"] < 1e-2
+    assert acc["rel_linf_vs_fp64"]["max"] >= acc["rel_linf_vs_fp64"]["median"] > 0
+    assert acc["rel_linf_vs_fp64_oracle"] < 1e-2
+    assert d["fp64_batch"]["value"] > 0 and d["fp64_batch"]["fp32_speedup"] > 1
+    assert d["fp64_single"]["rel_linf_vs_fp64_oracle"] < 100 * 1e-12
     # 2 sweeps per step, every sweep at least one launch
     assert d["gpu_launches"] >= 3 * 200 * 2
     assert d["fp64_plain"]["rel_linf_vs_oracle"] < 250 * 1e-12

@@ -154,3 +154,30 @@ def test_kahan_vectorised_and_general_kernels_agree(lib, nx, ny):
     finally:
         lib.aniso_destroy(a)
         lib.aniso_destroy(b)
+
+
+@pytest.mark.parametrize("nx,ny", [(96, 1024), (1024, 64)])
+def test_kahan_on_grids_at_the_fp32_noise_floor(lib, nx, ny):
+    """Strongly non-square grids, where the van Leer step amplifies one-ulp
+    FP32 changes of the state (lam ~ 50 across the short side): the plain
+    FP32 state cannot come closer to the FP64 oracle than that floor.  The
+    compensated state carries T to about twice FP32's precision between
+    steps; this records how close it comes and checks that it is at least as
+    close as plain FP32 and within the floor-based tolerance."""
+    inst = W.random_instance(nx, ny, seed=19, chi_par=0.05, dt_factor=100.0)
+    steps = 100
+    T0, co = oracle_inputs(lib, inst, FP32)
+    ref = oracle_step(inst, T0, co, steps)
+    plain = GpuGrid(lib, inst, FP32, fast=0)
+    h, T = _kahan_grid(lib, inst, fast=0)
+    try:
+        e_plain = rel_linf(plain.step(steps), ref)
+        lib.aniso_step(h, T, inst.dt, steps)
+        e_hilo = rel_linf(_hi_lo(lib, h, T), ref)
+    finally:
+        plain.close()
+        lib.aniso_destroy(h)
+    tol = fp32_tol(inst, T0, co, steps, ref)
+    print("%dx%d: plain FP32 %.2e, hi+lo %.2e, tolerance %.2e" % (nx, ny, e_plain, e_hilo, tol))
+    assert e_hilo < tol
+    assert e_hilo <= 1.5 * e_plain
