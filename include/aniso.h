@@ -85,9 +85,21 @@ enum {
                                  shallower PCR) */
     ANISO_OPT_BLOCK_WARPS = 10, /* warps per block of the warp-autonomous kernel (0 = default 4;
                                    1, 2, 4 or 8): lines per block = warps x lines per warp */
-    ANISO_OPT_SCHEME = 11      /* ANISO_SCHEME_2STEP (default), _4STEP or _EXPLICIT; the other
+    ANISO_OPT_SCHEME = 11,     /* ANISO_SCHEME_2STEP (default), _4STEP or _EXPLICIT; the other
                                   schemes run on single handles (aniso_step, not batches) with
                                   the plain state; ANISO_ERR_UNSUPPORTED with the compensated one */
+    ANISO_OPT_DIAGNOSTICS = 12, /* 1: batched calls record, after every step of every grid on the
+                                  fast path, the FP64 sum of T, its minimum and its maximum (read
+                                  with aniso_batch_diagnostics); taken from the batch's first handle */
+    ANISO_OPT_TMA_LINES = 13   /* batched calls, FP32 with FP32 coefficients: 1 (default) solves the
+                                  lines of 768 to 1024 cells (multiples of 32) with the kernel that
+                                  stages each block's rows by tensor-map (TMA) tile loads and keeps
+                                  the line state in registers; 0 uses the warp-per-line kernel for
+                                  all lines; 2 is for testing the failure path only: that kernel
+                                  issues no loads, its bounded wait gives up and the call reports
+                                  ANISO_ERR_TIMEOUT at the next aniso_sync / aniso_total of the
+                                  first handle.  Taken from the batch's first handle.  Y-updates
+                                  recorded by ANISO_OPT_DIAGNOSTICS use the warp-per-line kernel. */
 };
 enum { ANISO_PREC_FP64 = 0, ANISO_PREC_FP32 = 1 };
 enum {
@@ -232,6 +244,22 @@ int aniso_step_batched(aniso_batch_t b, void *const *T, const double *dt, const 
  * copied back.  Returns when T_host holds the result (synchronises the
  * batch's stream).  Errors: as aniso_step_batched, ANISO_ERR_OOM. */
 int aniso_step_batched_host(aniso_batch_t b, void *const *T_host, const double *dt, const int *nsteps);
+
+/* Per-step diagnostics of the last aniso_step_batched(_host) call that ran
+ * with ANISO_OPT_DIAGNOSTICS on the batch's first handle: for grid k and
+ * step s (0-based within the call), out[(k * steps + s) * 3 + {0, 1, 2}] =
+ * FP64 sum of T after that step, minimum, maximum.  The abstract calls the
+ * scheme conservative; the sum follows conservation step by step, and min T
+ * the monotonicity Section 3.1 measures (its relative non-monotonicity is
+ * (min T0 - min T) / min T0).  The values are formed inside the y-update
+ * kernel (each block's values in a fixed order, FP64 across blocks) and
+ * finished by one small kernel per launch, so the call stays one graph.
+ * Slots of steps a grid does not take, and of grids off the fast path, are
+ * NaN.  *steps (may be NULL) receives the steps per grid (the call's largest
+ * nsteps); out may be NULL to query it.  capacity: doubles available at out.
+ * Synchronises the batch's stream.  Errors: ANISO_ERR_ARG (capacity),
+ * ANISO_ERR_STATE (no such call yet). */
+int aniso_batch_diagnostics(aniso_batch_t b, double *out, long long capacity, int *steps);
 
 void aniso_batch_destroy(aniso_batch_t b);
 

@@ -34,6 +34,8 @@ ANISO_OPT_FAST_PATH = 8
 ANISO_OPT_SEGMENT = 9
 ANISO_OPT_BLOCK_WARPS = 10
 ANISO_OPT_SCHEME = 11
+ANISO_OPT_DIAGNOSTICS = 12
+ANISO_OPT_TMA_LINES = 13
 ANISO_SCHEME_2STEP = 0
 ANISO_SCHEME_4STEP = 1
 ANISO_SCHEME_EXPLICIT = 2
@@ -55,7 +57,8 @@ ANISO_KERNEL_TRANSPOSE = 2
 EXPORTED = ("aniso_create", "aniso_set_option", "aniso_set_field", "aniso_step", "aniso_sweep",
             "aniso_total", "aniso_get_state", "aniso_set_state", "aniso_sync",
             "aniso_kernel_times", "aniso_destroy", "aniso_last_error", "aniso_batch_create",
-            "aniso_step_batched", "aniso_step_batched_host", "aniso_batch_destroy", "aniso_step_noalloc",
+            "aniso_step_batched", "aniso_step_batched_host", "aniso_batch_diagnostics", "aniso_batch_destroy",
+            "aniso_step_noalloc",
             "aniso_batch_autotune", "aniso_autotune_candidate", "aniso_set_source",
             "aniso_batch_kernel_count", "aniso_set_nonlinear",
             "aniso3_create", "aniso3_set_option", "aniso3_set_field", "aniso3_step",
@@ -98,6 +101,7 @@ def load():
         "aniso_batch_create": (i, [i, P(vp), P(vp)]),
         "aniso_step_batched": (i, [vp, P(vp), P(d), P(i)]),
         "aniso_step_batched_host": (i, [vp, P(vp), P(d), P(i)]),
+        "aniso_batch_diagnostics": (i, [vp, P(d), ll, P(i)]),
         "aniso_batch_destroy": (None, [vp]),
         "aniso_step_noalloc": (i, [i, i, d, d, d, d, i, i, vp, vp, vp, d, i, vp]),
         "aniso_batch_autotune": (i, [vp, P(vp), P(d), i, i, P(i), P(d)]),
@@ -228,6 +232,18 @@ def aniso_step_batched_host(batch, Ts, dts, nsteps):
     darr = (ctypes.c_double * n)(*[float(x) for x in dts])
     narr = (ctypes.c_int * n)(*[int(x) for x in nsteps])
     _check(load().aniso_step_batched_host(batch, Tarr, darr, narr))
+
+
+def aniso_batch_diagnostics(batch, n_grids):
+    """Per-step (sum, min, max) of the last diagnostics-enabled batched call as
+    a numpy array [n_grids, steps, 3] (NaN where a grid took no such step)."""
+    import numpy as np
+    steps = ctypes.c_int()
+    _check(load().aniso_batch_diagnostics(batch, None, 0, ctypes.byref(steps)))
+    out = np.empty((n_grids, steps.value, 3), dtype=np.float64)
+    _check(load().aniso_batch_diagnostics(batch, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                          out.size, ctypes.byref(steps)))
+    return out
 
 
 def aniso_batch_autotune(batch, Ts, dts, nsteps=2, reps=3):

@@ -15,6 +15,7 @@
 #include "../../include/aniso.h"
 #include "aniso_internal.h"
 #include "status.h"
+#include "line5_types.h"
 
 // NVTX range around a public call, for timeline tools (a no-op without one).
 struct TraceRange {
@@ -88,7 +89,8 @@ struct aniso_ctx {
     int nx = 0, ny = 0, bc = 0;
     double dx = 0, dy = 0, chi_par = 0, chi_perp = 0;
     int prec = PREC_FP64, field_fp16 = 0, kahan = 0, limiter = LIM_VANLEER, order = ANISO_ORDER_XY;
-    int use_graph = 1, profile = 0, fast = 3, seg_chunks = 0, l4_warps = 0, scheme = 0;
+    int use_graph = 1, profile = 0, fast = 3, seg_chunks = 0, l4_warps = 0, scheme = 0, diag = 0;
+    int tma_lines = 1;  // ANISO_OPT_TMA_LINES
     double nl_alpha = 0, nl_tref = 1;  // temperature-dependent diffusivity (aniso_set_nonlinear)
     void *t4 = nullptr;  // intermediate of the 4-step scheme
     void *q = nullptr;   // source term (aniso_set_source), handle precision
@@ -237,6 +239,13 @@ extern "C" int aniso_set_option(aniso_t h, int key, long long v)
         break;
     case ANISO_OPT_PROFILE:
         h->profile = v != 0;
+        break;
+    case ANISO_OPT_DIAGNOSTICS:
+        h->diag = v != 0;
+        break;
+    case ANISO_OPT_TMA_LINES:
+        if (v < 0 || v > 2) return fail(ANISO_ERR_ARG, "bad TMA-lines value %lld", v);
+        h->tma_lines = (int)v;
         break;
     case ANISO_OPT_FAST_PATH:
         if (v < 0 || v > 3 || v == 2) return fail(ANISO_ERR_ARG, "bad fast-path value %lld", v);
@@ -903,11 +912,19 @@ struct aniso_batch {
     int profile = 0;
     int use_graph = 1;
     // concurrent branches of one sweep (line4 occupancy classes)
-    static constexpr int kSide = 4;
+    static constexpr int kSide = 6;
     cudaStream_t side[kSide] = {};
     cudaEvent_t fork_ev = nullptr, join_ev[kSide] = {};
     long long kernels_per_call = 0;  // kernel nodes of the captured graph
     std::vector<void *> dev_T;       // device copies of T for aniso_step_batched_host
+    // per-step diagnostics (ANISO_OPT_DIAGNOSTICS of the first handle)
+    int key_diag = -1;
+    int key_tma = -1;
+    double *d_ring = nullptr;  // [grid][step][sum, min, max] of the last call
+    size_t ring_count = 0;     // doubles
+    int ring_steps = 0;        // steps per grid in the ring (the call's largest nsteps)
+    DiagPart *d_part = nullptr;
+    size_t part_count = 0;
 };
 
 extern "C" int aniso_batch_create(int n, const aniso_t *hs, aniso_batch_t *out)
@@ -952,13 +969,14 @@ static int batch_build(aniso_batch *b, void *const *T, const double *dt, const i
     const int n = (int)b->hs.size();
     const int prec = b->hs[0]->prec;
     const int fp16 = b->hs[0]->field_fp16;
+    const bool diag = b->hs[0]->diag != 0;
     int max_steps = 0;
     for (int k = 0; k < n; ++k) max_steps = std::max(max_steps, nsteps[k]);
 
     // Every (global step, phase) launch is one list of line jobs (x) and one
     // of column jobs (y).  Identical lists are shared.
     struct Launch {
-        int kind;  // 0 line, 1 col, 2/3 line2 (x/y), 7/8 line4 (x/y)
+        int kind;  // 0 line, 1 col, 2/3 line2 (x/y), 7/8 line4 (x/y), 9/10 line5 (x/y)
         size_t offset;
         int njobs, nblocks, nthreads;
         size_t smem;
@@ -971,6 +989,8 @@ static int batch_build(aniso_batch *b, void *const *T, const double *dt, const i
         const void *in = nullptr, *in_lo = nullptr;
         void *out = nullptr, *out_lo = nullptr;
         double dt = 0;
+        long long table = -1;  // line4: offset of the block -> job table, or -1
+        int diag_region = -1;  // line4 y-update with diagnostics: its partials region
     };
     std::vector<unsigned char> blob;
     std::vector<Launch> launches;  // in enqueue order
@@ -1053,7 +1073,7 @@ static int batch_build(aniso_batch *b, void *const *T, const double *dt, const i
     // classes of a sweep run concurrently (one graph branch each).
     int shape_rc = ANISO_OK;
     int next_group = 0;
-    auto add_line4 = [&](std::vector<Line2Job> &jobs, int kind_xy) {
+    auto add_line4 = [&](std::vector<Line2Job> &jobs, int kind_xy, int group) {
         if (jobs.empty()) return;
         const int warps = b->hs[0]->l4_warps, seg = b->hs[0]->seg_chunks;
         std::stable_sort(jobs.begin(), jobs.end(),
@@ -1079,13 +1099,12 @@ static int batch_build(aniso_batch *b, void *const *T, const double *dt, const i
             cls[k] = {occ > 0 ? occ : 0, sm};
         }
         // classes in ascending occupancy (largest lines first); at most
-        // 1 + kSide of them, the highest-occupancy ones merged
+        // five of them, the highest-occupancy ones merged
         std::vector<int> occs;
         for (auto &c : cls) occs.push_back(c.first);
         std::sort(occs.begin(), occs.end());
         occs.erase(std::unique(occs.begin(), occs.end()), occs.end());
-        while ((int)occs.size() > 1 + aniso_batch::kSide) occs.erase(occs.end() - 2);
-        const int group = occs.size() > 1 ? next_group++ : -1;
+        while ((int)occs.size() > 5) occs.erase(occs.end() - 2);
         for (size_t ci = 0; ci < occs.size(); ++ci) {
             const int lo = occs[ci], hi = ci + 1 < occs.size() ? occs[ci + 1] : 1 << 30;
             std::vector<Line2Job> part;
@@ -1103,11 +1122,59 @@ static int batch_build(aniso_batch *b, void *const *T, const double *dt, const i
             if (part.empty()) continue;
             Launch L{kind_xy == 0 ? 7 : 8, blob.size(), (int)part.size(), blocks, nthreads, smem};
             L.group = group;
+            if (kind_xy == 1 && diag) L.diag_region = (int)ci;
             const unsigned char *p = reinterpret_cast<const unsigned char *>(part.data());
             blob.insert(blob.end(), p, p + part.size() * sizeof(Line2Job));
             while (blob.size() % 16) blob.push_back(0);
+            std::vector<int> table(blocks);
+            for (size_t k = 0; k < part.size(); ++k)
+                for (int bk = 0; bk < part[k].nblocks; ++bk) table[part[k].block0 + bk] = (int)k;
+            L.table = (long long)blob.size();
+            const unsigned char *tp = reinterpret_cast<const unsigned char *>(table.data());
+            blob.insert(blob.end(), tp, tp + table.size() * sizeof(int));
+            while (blob.size() % 16) blob.push_back(0);
             launches.push_back(L);
         }
+    };
+
+    // line5 jobs (TMA-staged, lines of 768-1024 cells): one launch per sweep,
+    // a branch of the same group as the line4 classes
+    const int tma_mode = b->hs[0]->tma_lines;
+    auto add_line5 = [&](std::vector<Line5Job> &jobs, int kind_xy, int group) {
+        if (jobs.empty()) return;
+        std::stable_sort(jobs.begin(), jobs.end(),
+                         [](const Line5Job &a, const Line5Job &c) { return (long long)a.n * a.nlines > (long long)c.n * c.nlines; });
+        int tiles = 0, nthreads = 0;
+        size_t stage = 0;
+        for (auto &J : jobs) {
+            J.block0 = tiles;
+            J.nblocks = (J.nlines + J.lines_per_block - 1) / J.lines_per_block;
+            tiles += J.nblocks;
+            int tm, lp, nt;
+            size_t st;
+            line5_config(prec, fp16, J.n, &tm, &lp, &nt, &st);
+            nthreads = std::max(nthreads, nt);
+            stage = std::max(stage, st);
+        }
+        const int resident = line5_prepare(b->hs[0]->limiter, nthreads, stage);
+        if (resident < 1) {
+            shape_rc = fail(ANISO_ERR_CUDA, "batch: the TMA line kernel cannot be resident with %zu bytes", stage);
+            return;
+        }
+        while (blob.size() % 128) blob.push_back(0);
+        Launch L{kind_xy == 0 ? 9 : 10, blob.size(), (int)jobs.size(), tiles, nthreads, stage};
+        L.group = group;
+        L.inst = resident;  // the prefetch distance in tiles
+        const unsigned char *p = reinterpret_cast<const unsigned char *>(jobs.data());
+        blob.insert(blob.end(), p, p + jobs.size() * sizeof(Line5Job));
+        std::vector<int> table(tiles);
+        for (size_t k = 0; k < jobs.size(); ++k)
+            for (int t = 0; t < jobs[k].nblocks; ++t) table[jobs[k].block0 + t] = (int)k;
+        L.table = (long long)blob.size();
+        const unsigned char *tp = reinterpret_cast<const unsigned char *>(table.data());
+        blob.insert(blob.end(), tp, tp + table.size() * sizeof(int));
+        while (blob.size() % 16) blob.push_back(0);
+        launches.push_back(L);
     };
 
     for (int s = 0; s < max_steps; ++s) {
@@ -1115,6 +1182,7 @@ static int batch_build(aniso_batch *b, void *const *T, const double *dt, const i
             std::vector<LineJob> xl;
             std::vector<ColJob> yl;
             std::vector<Line2Job> fl, fl4;
+            std::vector<Line5Job> fl5;
             std::vector<Launch> solo;
             for (int k = 0; k < n; ++k) {
                 if (s >= nsteps[k]) continue;
@@ -1147,6 +1215,26 @@ static int batch_build(aniso_batch *b, void *const *T, const double *dt, const i
                     J.per_line = per;
                     J.per_cross = per;
                     J.transpose_out = 1;
+                    J.diag_slot = (diag && phase == 1) ? k * max_steps + s : -1;
+                    int t5, l5, n5;
+                    size_t s5;
+                    if (h->fast_kind() == 4 && tma_mode && !(diag && phase == 1) && line5_available() &&
+                        line5_config(prec, fp16, J.n, &t5, &l5, &n5, &s5)) {
+                        Line5Job J5{};
+                        J5.Tout = J.Tout;
+                        J5.lam = J.lam;
+                        J5.mu = J.mu;
+                        J5.n = J.n;
+                        J5.nlines = J.nlines;
+                        J5.per_line = J.per_line;
+                        J5.per_cross = J.per_cross;
+                        J5.team = t5;
+                        J5.lines_per_block = l5;
+                        if (line5_make_maps(J5, J.Tin, J.g, J.e, (size_t)J.n * J.nlines)) {
+                            fl5.push_back(J5);
+                            continue;
+                        }
+                    }
                     if (h->fast_kind() == 4) {
                         fl4.push_back(J);  // team and block shape set by add_line4
                     } else {
@@ -1212,13 +1300,41 @@ static int batch_build(aniso_batch *b, void *const *T, const double *dt, const i
                 }
             }
             add_line2(fl, phase);
-            add_line4(fl4, phase);
+            {
+                const int grp = next_group++;  // the sweep's line4 classes and line5 launch run concurrently
+                add_line4(fl4, phase, grp);
+                add_line5(fl5, phase, grp);
+            }
             add_line(xl);
             add_col(yl);
             launches.insert(launches.end(), solo.begin(), solo.end());
         }
     }
     if (shape_rc) return shape_rc;
+    // diagnostics buffers: the ring of the call and one partials region per
+    // concurrent class launch of a y-update
+    size_t part_blocks = 0;
+    for (const Launch &L : launches)
+        if (L.diag_region >= 0) part_blocks = std::max(part_blocks, (size_t)L.nblocks);
+    if (diag) {
+        const size_t ring = (size_t)n * (size_t)max_steps * 3;
+        if (ring > b->ring_count) {
+            if (b->d_ring) cudaFree(b->d_ring);
+            b->d_ring = nullptr;
+            b->ring_count = 0;
+            CU(cudaMalloc(&b->d_ring, std::max<size_t>(ring, 3) * sizeof(double)));
+            b->ring_count = ring;
+        }
+        b->ring_steps = max_steps;
+        const size_t parts = part_blocks * (1 + aniso_batch::kSide);
+        if (parts > b->part_count) {
+            if (b->d_part) cudaFree(b->d_part);
+            b->d_part = nullptr;
+            b->part_count = 0;
+            CU(cudaMalloc(&b->d_part, std::max<size_t>(parts, 1) * sizeof(DiagPart)));
+            b->part_count = parts;
+        }
+    }
     // device copy of the job lists
     if (b->d_jobs && b->d_jobs_bytes < blob.size()) {
         cudaFree(b->d_jobs);
@@ -1244,11 +1360,34 @@ static int batch_build(aniso_batch *b, void *const *T, const double *dt, const i
     CU(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
     int rc = ANISO_OK;
     unsigned *err = b->hs[0]->err;
+    if (diag && launch_fill_nan(b->d_ring, (size_t)n * (size_t)max_steps * 3, b->cap_stream) != cudaSuccess)
+        rc = fail(ANISO_ERR_CUDA, "diagnostics ring fill failed");
     auto launch_one = [&](const Launch &L, cudaStream_t st) -> cudaError_t {
+        if (L.kind == 9 || L.kind == 10) {
+            Line5Args a{};
+            a.jobs = reinterpret_cast<const Line5Job *>(static_cast<unsigned char *>(b->d_jobs) + L.offset);
+            a.njobs = L.njobs;
+            a.total_tiles = L.nblocks;
+            a.limiter = b->hs[0]->limiter;
+            a.err = err;
+            a.test_no_load = tma_mode == 2 ? 1 : 0;
+            a.wait_limit = a.test_no_load ? 4096u : (1u << 20);
+            a.tile_job = reinterpret_cast<const int *>(static_cast<unsigned char *>(b->d_jobs) + L.table);
+            a.pf_dist = L.inst;
+            return launch_line5(a, L.nthreads, L.smem, st);
+        }
         if (L.kind == 7 || L.kind == 8) {
             Line2Args a{};
             a.jobs = reinterpret_cast<const Line2Job *>(static_cast<unsigned char *>(b->d_jobs) + L.offset);
             a.njobs = L.njobs;
+            if (L.table >= 0)
+                a.block_job = reinterpret_cast<const int *>(static_cast<unsigned char *>(b->d_jobs) + L.table);
+            if (L.diag_region >= 0) {
+                a.diag_part = b->d_part + (size_t)L.diag_region * part_blocks;
+                cudaError_t e = launch_line4(prec, fp16, a, L.nblocks, L.nthreads, L.smem, st);
+                if (e != cudaSuccess) return e;
+                return launch_diag_finish(a.jobs, L.njobs, a.diag_part, b->d_ring, st);
+            }
             a.limiter = b->hs[0]->limiter;
             a.err = err;
             return launch_line4(prec, fp16, a, L.nblocks, L.nthreads, L.smem, st);
@@ -1274,7 +1413,7 @@ static int batch_build(aniso_batch *b, void *const *T, const double *dt, const i
         a.err = err;
         return launch_col(prec, fp16, a, L.nblocks, L.nthreads, L.smem, st, b->hs[0]->kahan != 0);
     };
-    for (size_t i = 0; i < launches.size();) {
+    for (size_t i = 0; i < launches.size() && rc == ANISO_OK;) {
         const Launch &L = launches[i];
         if (L.kind == 6) {
             aniso_ctx *h = b->hs[L.inst];
@@ -1287,10 +1426,14 @@ static int batch_build(aniso_batch *b, void *const *T, const double *dt, const i
             continue;
         }
         size_t j = i + 1;  // [i, j): one concurrent group
-        while (L.group >= 0 && j < launches.size() && launches[j].group == L.group) ++j;
+        // (at most 1 + kSide launches run side by side; more of the same group
+        // form the next set of branches)
+        while (L.group >= 0 && j < launches.size() && launches[j].group == L.group &&
+               j - i < (size_t)(1 + aniso_batch::kSide))
+            ++j;
         int pidx = -1;
         if (b->profile) {
-            pidx = b->prof.take((L.kind == 0 || L.kind == 2 || L.kind == 7)
+            pidx = b->prof.take((L.kind == 0 || L.kind == 2 || L.kind == 7 || L.kind == 9)
                                     ? ANISO_KERNEL_XSWEEP
                                     : ANISO_KERNEL_YSWEEP);
             if (pidx < 0 || cudaEventRecordWithFlags(b->prof.pool[pidx].a, b->cap_stream,
@@ -1304,15 +1447,21 @@ static int batch_build(aniso_batch *b, void *const *T, const double *dt, const i
             ce = launch_one(L, b->cap_stream);
         } else {
             ce = cudaEventRecord(b->fork_ev, b->cap_stream);
+            size_t forked = 0;  // side streams that joined the capture
             for (size_t k = i + 1; k < j && ce == cudaSuccess; ++k) {
                 cudaStream_t st = b->side[k - i - 1];
                 ce = cudaStreamWaitEvent(st, b->fork_ev, 0);
+                if (ce == cudaSuccess) ++forked;
                 if (ce == cudaSuccess) ce = launch_one(launches[k], st);
-                if (ce == cudaSuccess) ce = cudaEventRecord(b->join_ev[k - i - 1], st);
             }
             if (ce == cudaSuccess) ce = launch_one(L, b->cap_stream);
-            for (size_t k = i + 1; k < j && ce == cudaSuccess; ++k)
-                ce = cudaStreamWaitEvent(b->cap_stream, b->join_ev[k - i - 1], 0);
+            // every forked branch is joined back, also after an error, so that
+            // the capture can end and leave no stream in capture mode
+            for (size_t k = 0; k < forked; ++k) {
+                cudaError_t e2 = cudaEventRecord(b->join_ev[k], b->side[k]);
+                if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(b->cap_stream, b->join_ev[k], 0);
+                if (ce == cudaSuccess) ce = e2;
+            }
         }
         if (ce != cudaSuccess) {
             rc = fail(ANISO_ERR_CUDA, "batched launch: %s", cudaGetErrorString(ce));
@@ -1368,7 +1517,8 @@ extern "C" int aniso_step_batched(aniso_batch_t b, void *const *T, const double 
     std::vector<int> parity(n);
     for (int k = 0; k < n; ++k)
         parity[k] = b->hs[k]->order == ANISO_ORDER_ALTERNATE ? (int)(b->hs[k]->step_counter & 1) : -b->hs[k]->order;
-    const bool hit = b->gexec && b->key_profile == b->profile &&
+    const bool hit = b->gexec && b->key_profile == b->profile && b->key_diag == b->hs[0]->diag &&
+                     b->key_tma == b->hs[0]->tma_lines &&
                      b->key_T == std::vector<void *>(T, T + n) &&
                      b->key_dt == std::vector<double>(dt, dt + n) &&
                      b->key_n == std::vector<int>(nsteps, nsteps + n) && b->key_parity == parity;
@@ -1386,6 +1536,8 @@ extern "C" int aniso_step_batched(aniso_batch_t b, void *const *T, const double 
         b->key_n.assign(nsteps, nsteps + n);
         b->key_parity = parity;
         b->key_profile = b->profile;
+        b->key_diag = b->hs[0]->diag;
+        b->key_tma = b->hs[0]->tma_lines;
     }
     if (b->profile && !b->prof.pending.empty()) {
         CU(cudaStreamSynchronize(b->stream));
@@ -1430,6 +1582,21 @@ extern "C" int aniso_step_batched_host(aniso_batch_t b, void *const *T_host, con
         CU(cudaMemcpyAsync(T_host[k], b->dev_T[k], b->hs[k]->cells() * b->hs[k]->esz(), cudaMemcpyDeviceToHost,
                            b->stream));
     CU(cudaStreamSynchronize(b->stream));
+    return ANISO_OK;
+}
+
+extern "C" int aniso_batch_diagnostics(aniso_batch_t b, double *out, long long capacity, int *steps)
+{
+    if (!b) return fail(ANISO_ERR_ARG, "aniso_batch_diagnostics: null batch");
+    if (!b->d_ring || b->key_diag != 1)
+        return fail(ANISO_ERR_STATE, "aniso_batch_diagnostics: no batched call has run with ANISO_OPT_DIAGNOSTICS");
+    const size_t count = b->hs.size() * (size_t)b->ring_steps * 3;
+    if (steps) *steps = b->ring_steps;
+    if (!out) return ANISO_OK;
+    if (capacity < (long long)count)
+        return fail(ANISO_ERR_ARG, "aniso_batch_diagnostics: need %zu doubles, got %lld", count, capacity);
+    CU(cudaStreamSynchronize(b->stream));
+    CU(cudaMemcpy(out, b->d_ring, count * sizeof(double), cudaMemcpyDeviceToHost));
     return ANISO_OK;
 }
 
@@ -1585,6 +1752,8 @@ extern "C" void aniso_batch_destroy(aniso_batch_t b)
     if (b->fork_ev) cudaEventDestroy(b->fork_ev);
     if (b->d_jobs) cudaFree(b->d_jobs);
     for (void *p : b->dev_T) cudaFree(p);
+    if (b->d_ring) cudaFree(b->d_ring);
+    if (b->d_part) cudaFree(b->d_part);
     b->prof.destroy();
     delete b;
 }

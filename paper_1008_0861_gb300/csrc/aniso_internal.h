@@ -98,6 +98,15 @@ struct Line2Job {
     // coefficients are scaled by the harmonic mean of (max(T,0) * chi_itref)^
     // chi_alpha over the two cells beside the face, T the update's input.
     double chi_alpha, chi_itref;
+    // Per-step diagnostics (batched y-updates with args.diag_part set): slot
+    // of this update's (sum, min, max) in the batch's ring, instance * steps + step.
+    int diag_slot;
+};
+
+// One block's diagnostics partial: FP64 sum, min and max of its lines' output.
+struct DiagPart {
+    double sum;
+    double mn, mx;
 };
 struct Line2Args {
     const Line2Job *jobs;
@@ -105,7 +114,19 @@ struct Line2Args {
     int limiter;
     unsigned *err;
     Line2Job one;
+    // optional: job index of every block of the launch (one load instead of
+    // a binary search over the jobs at block start)
+    const int *block_job;
+    // optional (line4, 2-D): every block writes the sum, min and max of the
+    // values it stores to diag_part[blockIdx.x]
+    DiagPart *diag_part;
 };
+// Finish the diagnostics of one line4 launch: for every job, the partials of
+// its blocks in block order -> ring[diag_slot] = (sum, min, max).
+cudaError_t launch_diag_finish(const Line2Job *jobs, int njobs, const DiagPart *part, double *ring,
+                               cudaStream_t s);
+// ring[0 .. count) = NaN (slots no step writes read as NaN).
+cudaError_t launch_fill_nan(double *ring, size_t count, cudaStream_t s);
 constexpr int MAX_LINE2_TRANSPOSED = 2048;
 
 // Launch configuration helpers (host).

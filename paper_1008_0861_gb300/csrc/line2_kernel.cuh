@@ -127,7 +127,9 @@ __global__ void __launch_bounds__(512, 2) line2_kernel(Line2Args args)
     constexpr int N = V16<R>::N;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ Line2Job J;
-    if (threadIdx.x == 0) J = args.jobs ? args.jobs[find_job(args.jobs, args.njobs)] : args.one;
+    if (threadIdx.x == 0)
+        J = args.jobs ? args.jobs[args.block_job ? args.block_job[blockIdx.x] : find_job(args.jobs, args.njobs)]
+                      : args.one;
     __syncthreads();
 
     const int lim = args.limiter;

@@ -152,7 +152,9 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? (D3 ? 3 : 4) : 2) line4_
     constexpr int LOGN = N == 4 ? 2 : 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ Line2Job J;
-    if (threadIdx.x == 0) J = args.jobs ? args.jobs[find_job(args.jobs, args.njobs)] : args.one;
+    if (threadIdx.x == 0)
+        J = args.jobs ? args.jobs[args.block_job ? args.block_job[blockIdx.x] : find_job(args.jobs, args.njobs)]
+                      : args.one;
     __syncthreads();
 
     const int lim = args.limiter;
@@ -436,6 +438,9 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? (D3 ? 3 : 4) : 2) line4_
 
     // ---- C: T_new = T_old + delta, coalesced
     bool bad = false;
+    // diagnostics: compensated sum of the chunk sums, min, max of this lane's cells
+    const bool diag = args.diag_part != nullptr;
+    R dh = R(0), dl = R(0), dmn = R(INFINITY), dmx = R(-INFINITY);
     {
         VT *vout = reinterpret_cast<VT *>(static_cast<R *>(J.Tout) + (size_t)lc * n);
         for (int v = 0; v < V; ++v) {
@@ -453,6 +458,16 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? (D3 ? 3 : 4) : 2) line4_
                 sum += to[j];
             }
             bad |= !(fabs(sum) < R(INFINITY));  // a NaN or infinity in the chunk
+            if (diag && active) {
+                const R y = sum - dl, tt = dh + y;
+                dl = (tt - dh) - y;
+                dh = tt;
+#pragma unroll
+                for (int j = 0; j < N; ++j) {
+                    dmn = fmin(dmn, to[j]);
+                    dmx = fmax(dmx, to[j]);
+                }
+            }
             if (!J.transpose_out) {
                 if (active) vout[c] = V16<R>::pack(to);
             } else {
@@ -492,6 +507,27 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? (D3 ? 3 : 4) : 2) line4_
         }
     }
     if (bad && active) atomicOr(args.err, 1u);
+    if (diag) {  // the block's partial, reduced in a fixed order (deterministic)
+        __shared__ DiagPart s_diag[8];
+        double ds = (double)dh - (double)dl, mn = (double)dmn, mx = (double)dmx;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            ds += __shfl_xor_sync(full, ds, o);
+            mn = fmin(mn, __shfl_xor_sync(full, mn, o));
+            mx = fmax(mx, __shfl_xor_sync(full, mx, o));
+        }
+        if (lane == 0) s_diag[warp] = DiagPart{ds, mn, mx};
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            DiagPart p = s_diag[0];
+            for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+                p.sum += s_diag[w].sum;
+                p.mn = fmin(p.mn, s_diag[w].mn);
+                p.mx = fmax(p.mx, s_diag[w].mx);
+            }
+            args.diag_part[blockIdx.x] = p;
+        }
+    }
 }
 
 }  // namespace aniso

@@ -34,51 +34,10 @@
 // line).  The mbarrier wait is bounded: a block that gives up sets bit 2 of
 // the error word, waits (bounded again) for its copies to land, and returns.
 #pragma once
-#include <cuda.h>
-
 #include "line4_kernel.cuh"
+#include "line5_types.h"
 
 namespace aniso {
-
-struct alignas(128) Line5Job {
-    CUtensorMap tm_T;   // T lines, box {32, n/32 * L}
-    CUtensorMap tm_T1;  // T lines, box {32, n/32}: one line
-    CUtensorMap tm_g;   // normal coefficient, box {32, n/32 * L}
-    CUtensorMap tm_e;   // transverse coefficient, same box
-    void *Tout;         // transposed output, [n][nlines]
-    double lam, mu;
-    int n, nlines;
-    int per_line, per_cross;
-    int team, lines_per_block;
-    int block0, nblocks;
-};
-
-struct Line5Args {
-    const Line5Job *jobs;  // device array sorted by block0 (128-byte aligned)
-    int njobs;
-    int limiter;
-    unsigned *err;
-    unsigned wait_limit;  // tries of the bounded wait for the tiles
-    int test_no_load;     // 1: issue no loads, so that the wait gives up (failure-path test)
-};
-
-// Shared-memory plan of a block (bytes from a 1024-byte aligned base).
-struct Line5Smem {
-    unsigned tmain, tdn, tup, g, e, total;
-};
-__host__ __device__ inline unsigned round1k(unsigned v) { return (v + 1023u) & ~1023u; }
-__host__ __device__ inline Line5Smem line5_smem(int n, int L)
-{
-    Line5Smem s;
-    const unsigned line = (unsigned)n * 4u, box = line * (unsigned)L;
-    s.tmain = 0;
-    s.tdn = round1k(box);
-    s.tup = s.tdn + round1k(line);
-    s.g = s.tup + round1k(line);
-    s.e = s.g + round1k(box);
-    s.total = s.e + round1k(box);
-    return s;
-}
 
 __device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ void mbar_init(unsigned bar, unsigned count)
@@ -136,60 +95,123 @@ __device__ __forceinline__ void tmap_acquire(const CUtensorMap *map)
 // 128-byte swizzle (tile base 1024-byte aligned).
 __device__ __forceinline__ unsigned swz128(unsigned o) { return o ^ ((o >> 3) & 0x70u); }
 
+// Job owning tile `tile` (jobs sorted by their first tile).
+__device__ __forceinline__ int find_job5(const Line5Job *jobs, int njobs, int tile)
+{
+    int lo = 0, hi = njobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (jobs[mid].block0 <= tile) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int line5_job_of(const Line5Args &args, int tile)
+{
+    return args.tile_job ? args.tile_job[tile] : find_job5(args.jobs, args.njobs, tile);
+}
+
+// Issue the five tile loads of `tile` into the stage at byte offset `st`
+// (from the aligned base) on barrier `bar`.  One thread.
+__device__ __forceinline__ void line5_issue(const Line5Job *Jp, int tile, unsigned base, unsigned st, unsigned bar)
+{
+    const int n = Jp->n, nl = Jp->nlines, L = Jp->lines_per_block;
+    const int line0 = (tile - Jp->block0) * L;
+    const int L_act = min(L, nl - line0);
+    const Line5Smem sp = line5_smem(n, L);
+    const int rows_line = n >> 5;
+    const int dn = line0 > 0 ? line0 - 1 : (Jp->per_cross ? nl - 1 : 0);
+    const int up = line0 + L_act < nl ? line0 + L_act : (Jp->per_cross ? 0 : nl - 1);
+    const unsigned box = (unsigned)n * 4u * (unsigned)L, line = (unsigned)n * 4u;
+    tmap_acquire(&Jp->tm_T);
+    tmap_acquire(&Jp->tm_T1);
+    tmap_acquire(&Jp->tm_g);
+    tmap_acquire(&Jp->tm_e);
+    mbar_expect_tx(bar, 3u * box + 2u * line);
+    tma_load_2d(base + st + sp.tmain, &Jp->tm_T, 0, line0 * rows_line, bar);
+    tma_load_2d(base + st + sp.g, &Jp->tm_g, 0, line0 * rows_line, bar);
+    tma_load_2d(base + st + sp.e, &Jp->tm_e, 0, line0 * rows_line, bar);
+    tma_load_2d(base + st + sp.tdn, &Jp->tm_T1, 0, dn * rows_line, bar);
+    tma_load_2d(base + st + sp.tup, &Jp->tm_T1, 0, up * rows_line, bar);
+}
+
+__device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap *map, int x, int y)
+{
+    asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global [%0, {%1, %2}];" ::"l"(
+                     reinterpret_cast<unsigned long long>(map)),
+                 "r"(x), "r"(y)
+                 : "memory");
+}
+// Ask L2 for the main tiles of `tile` (T, g, e of its lines; a hint).
+__device__ __forceinline__ void line5_prefetch(const Line5Job *Jp, int tile)
+{
+    const int row = (tile - Jp->block0) * Jp->lines_per_block * (Jp->n >> 5);
+    tma_prefetch_2d(&Jp->tm_T, 0, row);
+    tma_prefetch_2d(&Jp->tm_g, 0, row);
+    tma_prefetch_2d(&Jp->tm_e, 0, row);
+}
+
 // UMAX: largest number of 4-cell chunks a lane owns (compile-time, so that
-// the per-cell rho of the segment lives in registers).
-template <int UMAX, bool VL>
-__global__ void __launch_bounds__(256, 1) line5_kernel(Line5Args args)
+// the per-cell rho of the segment lives in registers).  Persistent blocks
+// with two stages: while a tile is solved from one stage, the next tile of
+// the block lands in the other.  The dynamic shared memory holds two stages
+// of line5_smem(n_max, L).total bytes each (stage size `stage_bytes`), plus
+// 1 KB for alignment.
+template <int UMAX, bool VL, int STAGES = 2>
+__global__ void __launch_bounds__(256, 1) line5_kernel(Line5Args args, unsigned stage_bytes)
 {
     constexpr int SMAX = 4 * UMAX;
     extern __shared__ __align__(1024) unsigned char smem5_raw[];
-    __shared__ __align__(8) unsigned long long s_bar;
-    __shared__ int s_job;
+    __shared__ __align__(8) unsigned long long s_bar[2];
 
     // 1024-byte aligned base inside the dynamic area (the host adds 1 KB)
     const unsigned raw = smem_addr(smem5_raw);
     const unsigned base = (raw + 1023u) & ~1023u;
-    unsigned char *const sb = smem5_raw + (base - raw);
-    const unsigned bar = smem_addr(&s_bar);
+    unsigned char *const sb0 = smem5_raw + (base - raw);
+    const unsigned bar0 = smem_addr(&s_bar[0]), bar1 = smem_addr(&s_bar[1]);
 
     if (threadIdx.x == 0) {
-        s_job = find_job(args.jobs, args.njobs);
-        mbar_init(bar, 1);
+        mbar_init(bar0, 1);
+        mbar_init(bar1, 1);
         mbar_fence_init();
+        if (!args.test_no_load && (int)blockIdx.x < args.total_tiles)
+            line5_issue(args.jobs + line5_job_of(args, blockIdx.x), blockIdx.x, base, 0u, bar0);
     }
     __syncthreads();
-    const Line5Job *Jp = args.jobs + s_job;
-    const int n = Jp->n, nl = Jp->nlines, P = Jp->team, L = Jp->lines_per_block;
-    const int line0 = (blockIdx.x - Jp->block0) * L;
-    const int L_act = min(L, nl - line0);
-    const Line5Smem sp = line5_smem(n, L);
-    const int rows_line = n >> 5;  // 128-byte rows per line
-
-    if (threadIdx.x == 0 && !args.test_no_load) {
-        const int dn = line0 > 0 ? line0 - 1 : (Jp->per_cross ? nl - 1 : 0);
-        const int up = line0 + L_act < nl ? line0 + L_act : (Jp->per_cross ? 0 : nl - 1);
-        const unsigned box = (unsigned)n * 4u * (unsigned)L, line = (unsigned)n * 4u;
-        tmap_acquire(&Jp->tm_T);
-        tmap_acquire(&Jp->tm_T1);
-        tmap_acquire(&Jp->tm_g);
-        tmap_acquire(&Jp->tm_e);
-        mbar_expect_tx(bar, 3u * box + 2u * line);
-        tma_load_2d(base + sp.tmain, &Jp->tm_T, 0, line0 * rows_line, bar);
-        tma_load_2d(base + sp.g, &Jp->tm_g, 0, line0 * rows_line, bar);
-        tma_load_2d(base + sp.e, &Jp->tm_e, 0, line0 * rows_line, bar);
-        tma_load_2d(base + sp.tdn, &Jp->tm_T1, 0, dn * rows_line, bar);
-        tma_load_2d(base + sp.tup, &Jp->tm_T1, 0, up * rows_line, bar);
-    }
 
     const int lim = args.limiter;
+    const unsigned full = 0xffffffffu;
+    int k = 0;  // tiles done by this block
+    for (int tile = blockIdx.x; tile < args.total_tiles; tile += gridDim.x, ++k) {
+    const int stage = STAGES == 2 ? (k & 1) : 0;
+    const unsigned bar = stage ? bar1 : bar0;
+    const unsigned phase = STAGES == 2 ? (unsigned)((k >> 1) & 1) : (unsigned)(k & 1);
+    if (threadIdx.x == 0 && !args.test_no_load) {
+        // with two stages the next tile of this block starts loading into the
+        // other stage, freed by the barrier at the end of the previous iteration
+        const int nt = tile + gridDim.x;
+        if (STAGES == 2 && nt < args.total_tiles) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            line5_issue(args.jobs + line5_job_of(args, nt), nt, base, stage ? 0u : stage_bytes,
+                        stage ? bar0 : bar1);
+        }
+        const int pt = tile + args.pf_dist;
+        if (args.pf_dist > 0 && pt < args.total_tiles) line5_prefetch(args.jobs + line5_job_of(args, pt), pt);
+    }
+    unsigned char *const sb = sb0 + (stage ? stage_bytes : 0u);
+    const Line5Job *Jp = args.jobs + line5_job_of(args, tile);
+    const int n = Jp->n, nl = Jp->nlines, P = Jp->team, L = Jp->lines_per_block;
+    const int line0 = (tile - Jp->block0) * L;
+    const int L_act = min(L, nl - line0);
+    const Line5Smem sp = line5_smem(n, L);
     const float lam = (float)Jp->lam, mu = (float)Jp->mu;
     const int per_line = Jp->per_line;
     const int logP = __ffs(P) - 1;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int q = lane >> logP, t = lane & (P - 1);
-    const int l = (warp << (5 - logP)) + q;  // line within the block
+    const int l = (warp << (5 - logP)) + q;  // line within the tile
     const bool active = l < L_act;
-    const unsigned full = 0xffffffffu;
 
     // segment of lane t: chunks [c_lo, c_lo + Ut); the first rr lanes one more
     const int m = n >> 2, U = m >> logP, rr = m & (P - 1);
@@ -225,11 +247,17 @@ __global__ void __launch_bounds__(256, 1) line5_kernel(Line5Args args)
         *reinterpret_cast<float4 *>(sb + off) = make_float4(x, y, z, w);
     };
 
-    // ---- wait for the tiles (bounded)
-    if (!mbar_wait_bounded(bar, 0u, args.wait_limit)) {
+    // ---- wait for this tile's stage (bounded; phase k >> 1 of its barrier)
+    // (the decision to give up is made for the whole block at once)
+    const bool got = mbar_wait_bounded(bar, phase, args.wait_limit);
+    if (__syncthreads_or(!got)) {
         if (threadIdx.x == 0) atomicOr(args.err, 2u);
         // the copies this block issued must land before it exits
-        if (!args.test_no_load) mbar_wait_bounded(bar, 0u, 1u << 20);
+        if (!args.test_no_load) {
+            mbar_wait_bounded(bar, phase, 1u << 20);
+            if (STAGES == 2 && tile + (int)gridDim.x < args.total_tiles)
+                mbar_wait_bounded(stage ? bar0 : bar1, (unsigned)(((k + 1) >> 1) & 1), 1u << 20);
+        }
         return;
     }
 
@@ -393,15 +421,24 @@ __global__ void __launch_bounds__(256, 1) line5_kernel(Line5Args args)
                 for (int k4 = 0; k4 < L; k4 += 4) {
                     float o4[4];
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) o4[k] = f1(tg0 + swz128((unsigned)(k4 + k) * LN + op));
+                    for (int kk = 0; kk < 4; ++kk) o4[kk] = f1(tg0 + swz128((unsigned)(k4 + kk) * LN + op));
                     *reinterpret_cast<float4 *>(dst + k4) = make_float4(o4[0], o4[1], o4[2], o4[3]);
                 }
             } else {
-                for (int k = 0; k < L_act; ++k) dst[k] = f1(tg0 + swz128((unsigned)k * LN + op));
+                for (int kk = 0; kk < L_act; ++kk) dst[kk] = f1(tg0 + swz128((unsigned)kk * LN + op));
             }
         }
     }
     if (bad) atomicOr(args.err, 1u);
+    __syncthreads();  // the stage is free again
+    if (STAGES == 1 && threadIdx.x == 0 && !args.test_no_load) {
+        const int nt = tile + gridDim.x;
+        if (nt < args.total_tiles) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            line5_issue(args.jobs + line5_job_of(args, nt), nt, base, 0u, bar0);
+        }
+    }
+    }
 }
 
 }  // namespace aniso

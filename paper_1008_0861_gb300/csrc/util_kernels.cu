@@ -158,6 +158,47 @@ bool line4_config(int prec, int n, bool transposed, int warps, int seg_chunks, i
     return true;
 }
 
+// Diagnostics of one batched line4 launch: job j's blocks are
+// [block0, block0 + nblocks); their partials are added in block order.
+__global__ void diag_finish_kernel(const Line2Job *jobs, int njobs, const DiagPart *part, double *ring)
+{
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < njobs; j += gridDim.x * blockDim.x) {
+        const Line2Job &J = jobs[j];
+        if (J.diag_slot < 0) continue;
+        double sum = 0.0, mn = INFINITY, mx = -INFINITY;
+        for (int b = J.block0; b < J.block0 + J.nblocks; ++b) {
+            sum += part[b].sum;
+            mn = fmin(mn, part[b].mn);
+            mx = fmax(mx, part[b].mx);
+        }
+        double *o = ring + 3 * (size_t)J.diag_slot;
+        o[0] = sum;
+        o[1] = mn;
+        o[2] = mx;
+    }
+}
+
+cudaError_t launch_diag_finish(const Line2Job *jobs, int njobs, const DiagPart *part, double *ring, cudaStream_t s)
+{
+    if (njobs <= 0) return cudaSuccess;
+    diag_finish_kernel<<<(njobs + 127) / 128, 128, 0, s>>>(jobs, njobs, part, ring);
+    return cudaGetLastError();
+}
+
+__global__ void fill_nan_kernel(double *p, size_t n)
+{
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x)
+        p[k] = __longlong_as_double(0x7ff8000000000000ll);
+}
+
+cudaError_t launch_fill_nan(double *ring, size_t count, cudaStream_t s)
+{
+    if (count == 0) return cudaSuccess;
+    const int blocks = (int)std::min<size_t>((count + 255) / 256, 152 * 4);
+    fill_nan_kernel<<<blocks, 256, 0, s>>>(ring, count);
+    return cudaGetLastError();
+}
+
 // Source stage of a step: T += dt Q, elementwise.
 template <typename R> __global__ void source_kernel(R *T, const R *Q, R dt, size_t n)
 {
