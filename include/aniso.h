@@ -91,11 +91,13 @@ enum {
     ANISO_OPT_DIAGNOSTICS = 12, /* 1: batched calls record, after every step of every grid on the
                                   fast path, the FP64 sum of T, its minimum and its maximum (read
                                   with aniso_batch_diagnostics); taken from the batch's first handle */
-    ANISO_OPT_TMA_LINES = 13   /* batched calls, FP32 with FP32 coefficients: 1 (default) solves the
-                                  lines of 768 to 1024 cells (multiples of 32) with the kernel that
-                                  stages each block's rows by tensor-map (TMA) tile loads and keeps
-                                  the line state in registers; 0 uses the warp-per-line kernel for
-                                  all lines; 2 is for testing the failure path only: that kernel
+    ANISO_OPT_TMA_LINES = 13   /* batched calls, FP32 with FP32 coefficients: 1 solves the lines of
+                                  768 to 1024 cells (multiples of 32) with the kernel that stages
+                                  each block's rows by tensor-map (TMA) tile loads and keeps the
+                                  line state in registers; 0 (default: faster on the uneven batch,
+                                  where that kernel shares the GPU with the other line classes)
+                                  uses the warp-per-line kernel for all lines; 2 is for testing
+                                  the failure path only: that kernel
                                   issues no loads, its bounded wait gives up and the call reports
                                   ANISO_ERR_TIMEOUT at the next aniso_sync / aniso_total of the
                                   first handle.  Taken from the batch's first handle.  Y-updates

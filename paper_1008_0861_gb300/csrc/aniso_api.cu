@@ -90,7 +90,7 @@ struct aniso_ctx {
     double dx = 0, dy = 0, chi_par = 0, chi_perp = 0;
     int prec = PREC_FP64, field_fp16 = 0, kahan = 0, limiter = LIM_VANLEER, order = ANISO_ORDER_XY;
     int use_graph = 1, profile = 0, fast = 3, seg_chunks = 0, l4_warps = 0, scheme = 0, diag = 0;
-    int tma_lines = 1;  // ANISO_OPT_TMA_LINES
+    int tma_lines = 0;  // ANISO_OPT_TMA_LINES
     double nl_alpha = 0, nl_tref = 1;  // temperature-dependent diffusivity (aniso_set_nonlinear)
     void *t4 = nullptr;  // intermediate of the 4-step scheme
     void *q = nullptr;   // source term (aniso_set_source), handle precision
