@@ -127,14 +127,21 @@ struct aniso_ctx {
     int vec() const { return prec == PREC_FP64 ? 2 : 4; }
     // Grid shapes the vectorised x-then-y path handles: both line lengths a
     // multiple of the 16-byte vector and short enough for transposed output.
-    // 4: warp-per-line kernel (line4, option value 3), 2: line2, 0: none of them.
+    // 4: warp-per-line kernel (line4, option value 3); 6: line4 for the lines
+    // it takes and the long-line kernel (line6, above 2048 cells, FP32) for
+    // the others, x-then-y steps only; 2: line2; 0: none of them.
     int fast_kind() const
     {
         int a, b, c;
         size_t d;
-        if (fast == 3 && line4_config(prec, nx, true, l4_warps, seg_chunks, &a, &b, &c, &d) &&
-            line4_config(prec, ny, true, l4_warps, seg_chunks, &a, &b, &c, &d))
-            return 4;
+        if (fast == 3) {
+            const bool x4 = line4_config(prec, nx, true, l4_warps, seg_chunks, &a, &b, &c, &d);
+            const bool y4 = line4_config(prec, ny, true, l4_warps, seg_chunks, &a, &b, &c, &d);
+            if (x4 && y4) return 4;
+            if ((x4 || line6_config(prec, field_fp16, nx, &a, &b, &c, &d)) &&
+                (y4 || line6_config(prec, field_fp16, ny, &a, &b, &c, &d)))
+                return 6;
+        }
         if (line2_config(prec, nx, true, &a, &b, &c, &d, seg_chunks) &&
             line2_config(prec, ny, true, &a, &b, &c, &d, seg_chunks))
             return 2;
@@ -353,10 +360,14 @@ static int enqueue_line2(aniso_ctx *h, const void *in, void *out, const void *g,
     }
     int nthreads;
     size_t smem;
-    const bool ok = v4 ? line4_config(h->prec, n, transposed, h->l4_warps, h->seg_chunks, &J.team,
-                                      &J.lines_per_block, &nthreads, &smem)
-                       : line2_config(h->prec, n, transposed, &J.team, &J.lines_per_block, &nthreads, &smem,
-                                      h->seg_chunks);
+    bool ok = v4 ? line4_config(h->prec, n, transposed, h->l4_warps, h->seg_chunks, &J.team, &J.lines_per_block,
+                                &nthreads, &smem)
+                 : line2_config(h->prec, n, transposed, &J.team, &J.lines_per_block, &nthreads, &smem,
+                                h->seg_chunks);
+    // lines above line4's limit: the long-line kernel (constant diffusivity only)
+    const bool v6 = v4 && !ok && h->nl_alpha == 0.0 &&
+                    line6_config(h->prec, h->field_fp16, n, &J.team, &J.lines_per_block, &nthreads, &smem);
+    ok = ok || v6;
     if (!ok) return fail(ANISO_ERR_UNSUPPORTED, "vectorised line kernel cannot take n=%d", n);
     J.block0 = 0;
     J.nblocks = (nlines + J.lines_per_block - 1) / J.lines_per_block;
@@ -367,8 +378,9 @@ static int enqueue_line2(aniso_ctx *h, const void *in, void *out, const void *g,
         if (pidx < 0) return fail(ANISO_ERR_CUDA, "event creation failed");
         CU(cudaEventRecordWithFlags(h->prof.pool[pidx].a, s, rec_flags));
     }
-    CU(v4 ? launch_line4(h->prec, h->field_fp16, a, J.nblocks, nthreads, smem, s)
-          : launch_line2(h->prec, h->field_fp16, a, J.nblocks, nthreads, smem, s, in_lo != nullptr));
+    CU(v6   ? launch_line6(h->field_fp16, a, J.nblocks, nthreads, smem, s)
+       : v4 ? launch_line4(h->prec, h->field_fp16, a, J.nblocks, nthreads, smem, s)
+            : launch_line2(h->prec, h->field_fp16, a, J.nblocks, nthreads, smem, s, in_lo != nullptr));
     if (h->profile) {
         CU(cudaEventRecordWithFlags(h->prof.pool[pidx].b, s, rec_flags));
         if (pairs) pairs->push_back(pidx);
@@ -393,11 +405,12 @@ static int enqueue_fast_step(aniso_ctx *h, void *T, double dt, cudaStream_t s, s
     const double mu = h->chi_par * dt / (h->dx * h->dy);
     const int per = h->bc == ANISO_BC_PERIODIC;
     const int fk = h->fast_kind();
+    const bool v4 = fk == 4 || fk == 6;  // line4, or line6 for lines above its limit
     int rc = enqueue_line2(h, T, h->tstar, h->cxx, h->cxy, h->nx, h->ny, per, per, lamx, mu, true,
-                           ANISO_KERNEL_XSWEEP, s, pairs, fk == 4);
+                           ANISO_KERNEL_XSWEEP, s, pairs, v4);
     if (rc) return rc;
     return enqueue_line2(h, h->tstar, T, h->cyyT, h->cyxT, h->ny, h->nx, per, per, lamy, mu, true,
-                         ANISO_KERNEL_YSWEEP, s, pairs, fk == 4);
+                         ANISO_KERNEL_YSWEEP, s, pairs, v4);
 }
 
 // One directional update from `in` to `out` (distinct buffers) on stream s.
@@ -976,7 +989,7 @@ static int batch_build(aniso_batch *b, void *const *T, const double *dt, const i
     // Every (global step, phase) launch is one list of line jobs (x) and one
     // of column jobs (y).  Identical lists are shared.
     struct Launch {
-        int kind;  // 0 line, 1 col, 2/3 line2 (x/y), 7/8 line4 (x/y), 9/10 line5 (x/y)
+        int kind;  // 0 line, 1 col, 2/3 line2 (x/y), 7/8 line4 (x/y), 9/10 line5 (x/y), 11/12 line6 (x/y)
         size_t offset;
         int njobs, nblocks, nthreads;
         size_t smem;
@@ -1177,12 +1190,54 @@ static int batch_build(aniso_batch *b, void *const *T, const double *dt, const i
         launches.push_back(L);
     };
 
+    // line6 jobs (lines above line4's limit): one launch per team size (the
+    // kernel's block barriers need one block shape per launch)
+    auto add_line6 = [&](std::vector<Line2Job> &jobs, int kind_xy, int group) {
+        if (jobs.empty()) return;
+        std::vector<int> teams;
+        for (auto &J : jobs) teams.push_back(J.team);
+        std::sort(teams.begin(), teams.end());
+        teams.erase(std::unique(teams.begin(), teams.end()), teams.end());
+        for (int P : teams) {
+            std::vector<Line2Job> part;
+            size_t smem = 0;
+            int blocks = 0, nthreads = 0;
+            for (auto &J0 : jobs) {
+                if (J0.team != P) continue;
+                Line2Job J = J0;
+                int tm, lp, nt;
+                size_t sm;
+                line6_config(prec, fp16, J.n, &tm, &lp, &nt, &sm);
+                smem = std::max(smem, sm);
+                nthreads = nt;
+                J.block0 = blocks;
+                J.nblocks = (J.nlines + J.lines_per_block - 1) / J.lines_per_block;
+                blocks += J.nblocks;
+                part.push_back(J);
+            }
+            Launch L{kind_xy == 0 ? 11 : 12, blob.size(), (int)part.size(), blocks, nthreads, smem};
+            L.group = group;
+            const unsigned char *p = reinterpret_cast<const unsigned char *>(part.data());
+            blob.insert(blob.end(), p, p + part.size() * sizeof(Line2Job));
+            while (blob.size() % 16) blob.push_back(0);
+            std::vector<int> table(blocks);
+            for (size_t k = 0; k < part.size(); ++k)
+                for (int bk = 0; bk < part[k].nblocks; ++bk) table[part[k].block0 + bk] = (int)k;
+            L.table = (long long)blob.size();
+            const unsigned char *tp = reinterpret_cast<const unsigned char *>(table.data());
+            blob.insert(blob.end(), tp, tp + table.size() * sizeof(int));
+            while (blob.size() % 16) blob.push_back(0);
+            launches.push_back(L);
+        }
+    };
+
     for (int s = 0; s < max_steps; ++s) {
         for (int phase = 0; phase < 2; ++phase) {
             std::vector<LineJob> xl;
             std::vector<ColJob> yl;
             std::vector<Line2Job> fl, fl4;
             std::vector<Line5Job> fl5;
+            std::vector<Line2Job> fl6;
             std::vector<Launch> solo;
             for (int k = 0; k < n; ++k) {
                 if (s >= nsteps[k]) continue;
@@ -1218,7 +1273,8 @@ static int batch_build(aniso_batch *b, void *const *T, const double *dt, const i
                     J.diag_slot = (diag && phase == 1) ? k * max_steps + s : -1;
                     int t5, l5, n5;
                     size_t s5;
-                    if (h->fast_kind() == 4 && tma_mode && !(diag && phase == 1) && line5_available() &&
+                    const int fk = h->fast_kind();
+                    if ((fk == 4 || fk == 6) && tma_mode && !(diag && phase == 1) && line5_available() &&
                         line5_config(prec, fp16, J.n, &t5, &l5, &n5, &s5)) {
                         Line5Job J5{};
                         J5.Tout = J.Tout;
@@ -1235,7 +1291,13 @@ static int batch_build(aniso_batch *b, void *const *T, const double *dt, const i
                             continue;
                         }
                     }
-                    if (h->fast_kind() == 4) {
+                    if (fk == 6 && !line4_config(prec, J.n, true, b->hs[0]->l4_warps, b->hs[0]->seg_chunks, &nt,
+                                                 &nt, &nt, &sm)) {
+                        // above line4's limit: the long-line kernel
+                        line6_config(prec, fp16, J.n, &J.team, &J.lines_per_block, &nt, &sm);
+                        J.diag_slot = -1;
+                        fl6.push_back(J);
+                    } else if (fk == 4 || fk == 6) {
                         fl4.push_back(J);  // team and block shape set by add_line4
                     } else {
                         line2_config(prec, J.n, true, &J.team, &J.lines_per_block, &nt, &sm, h->seg_chunks);
@@ -1304,6 +1366,7 @@ static int batch_build(aniso_batch *b, void *const *T, const double *dt, const i
                 const int grp = next_group++;  // the sweep's line4 classes and line5 launch run concurrently
                 add_line4(fl4, phase, grp);
                 add_line5(fl5, phase, grp);
+                add_line6(fl6, phase, grp);
             }
             add_line(xl);
             add_col(yl);
@@ -1363,6 +1426,15 @@ static int batch_build(aniso_batch *b, void *const *T, const double *dt, const i
     if (diag && launch_fill_nan(b->d_ring, (size_t)n * (size_t)max_steps * 3, b->cap_stream) != cudaSuccess)
         rc = fail(ANISO_ERR_CUDA, "diagnostics ring fill failed");
     auto launch_one = [&](const Launch &L, cudaStream_t st) -> cudaError_t {
+        if (L.kind == 11 || L.kind == 12) {
+            Line2Args a{};
+            a.jobs = reinterpret_cast<const Line2Job *>(static_cast<unsigned char *>(b->d_jobs) + L.offset);
+            a.njobs = L.njobs;
+            a.limiter = b->hs[0]->limiter;
+            a.err = err;
+            a.block_job = reinterpret_cast<const int *>(static_cast<unsigned char *>(b->d_jobs) + L.table);
+            return launch_line6(fp16, a, L.nblocks, L.nthreads, L.smem, st);
+        }
         if (L.kind == 9 || L.kind == 10) {
             Line5Args a{};
             a.jobs = reinterpret_cast<const Line5Job *>(static_cast<unsigned char *>(b->d_jobs) + L.offset);
@@ -1433,7 +1505,7 @@ static int batch_build(aniso_batch *b, void *const *T, const double *dt, const i
             ++j;
         int pidx = -1;
         if (b->profile) {
-            pidx = b->prof.take((L.kind == 0 || L.kind == 2 || L.kind == 7 || L.kind == 9)
+            pidx = b->prof.take((L.kind == 0 || L.kind == 2 || L.kind == 7 || L.kind == 9 || L.kind == 11)
                                     ? ANISO_KERNEL_XSWEEP
                                     : ANISO_KERNEL_YSWEEP);
             if (pidx < 0 || cudaEventRecordWithFlags(b->prof.pool[pidx].a, b->cap_stream,
