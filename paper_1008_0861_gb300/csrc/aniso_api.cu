@@ -366,7 +366,8 @@ static int enqueue_line2(aniso_ctx *h, const void *in, void *out, const void *g,
                                 h->seg_chunks);
     // lines above line4's limit: the long-line kernel (constant diffusivity only)
     const bool v6 = v4 && !ok && h->nl_alpha == 0.0 &&
-                    line6_config(h->prec, h->field_fp16, n, &J.team, &J.lines_per_block, &nthreads, &smem);
+                    line6_config(h->prec, h->field_fp16, n, &J.team, &J.lines_per_block, &nthreads, &smem,
+                                 h->l4_warps == 8 ? 2 : 4);
     ok = ok || v6;
     if (!ok) return fail(ANISO_ERR_UNSUPPORTED, "vectorised line kernel cannot take n=%d", n);
     J.block0 = 0;
@@ -1207,7 +1208,7 @@ static int batch_build(aniso_batch *b, void *const *T, const double *dt, const i
                 Line2Job J = J0;
                 int tm, lp, nt;
                 size_t sm;
-                line6_config(prec, fp16, J.n, &tm, &lp, &nt, &sm);
+                line6_config(prec, fp16, J.n, &tm, &lp, &nt, &sm, J.lines_per_block);
                 smem = std::max(smem, sm);
                 nthreads = nt;
                 J.block0 = blocks;
@@ -1294,7 +1295,8 @@ static int batch_build(aniso_batch *b, void *const *T, const double *dt, const i
                     if (fk == 6 && !line4_config(prec, J.n, true, b->hs[0]->l4_warps, b->hs[0]->seg_chunks, &nt,
                                                  &nt, &nt, &sm)) {
                         // above line4's limit: the long-line kernel
-                        line6_config(prec, fp16, J.n, &J.team, &J.lines_per_block, &nt, &sm);
+                        line6_config(prec, fp16, J.n, &J.team, &J.lines_per_block, &nt, &sm,
+                                     b->hs[0]->l4_warps == 8 ? 2 : 4);
                         J.diag_slot = -1;
                         fl6.push_back(J);
                     } else if (fk == 4 || fk == 6) {

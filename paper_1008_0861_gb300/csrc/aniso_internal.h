@@ -160,9 +160,10 @@ bool line4_config(int prec, int n, bool transposed, int warps, int seg_chunks, i
                   int *nthreads, size_t *smem);
 cudaError_t launch_line4(int prec, int coef_fp16, const Line2Args &a, int nblocks, int nthreads,
                          size_t smem, cudaStream_t s);
-// Long lines (line6): 2048 < n <= 4096, FP32, teams of 64 or 128 lanes over
-// several warps, four lines per block.  False when the line does not fit.
-bool line6_config(int prec, int coef_fp16, int n, int *team, int *lines_per_block, int *nthreads, size_t *smem);
+// Long lines (line6): 2048 < n <= 4096, FP32, teams of 128 lanes over four
+// warps, `lines` (4 or 2) lines per block.  False when the line does not fit.
+bool line6_config(int prec, int coef_fp16, int n, int *team, int *lines_per_block, int *nthreads, size_t *smem,
+                  int lines = 4);
 cudaError_t launch_line6(int coef_fp16, const Line2Args &a, int nblocks, int nthreads, size_t smem, cudaStream_t s);
 // Resident blocks per SM of the 2-D line4 kernel for that block size and
 // dynamic shared memory (CUDA's occupancy calculator), or -1.

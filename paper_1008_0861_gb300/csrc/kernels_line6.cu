@@ -5,18 +5,20 @@
 namespace aniso {
 
 // Lines of 2048 < n <= 4096 cells (multiples of the 16-byte vector): a team
-// of P = 64 or 128 lanes (about 8 chunks of 4 cells a lane), four lines per
-// block (16-byte pieces in the transposed store).  The shared memory holds
-// the three per-line arrays of line4 plus the team exchange area.
-bool line6_config(int prec, int coef_fp16, int n, int *team, int *lines_per_block, int *nthreads, size_t *smem)
+// of P = 128 lanes (4 to 8 chunks of 4 cells a lane), `lines` (2 or 4) lines
+// per block: 16-byte pieces in the transposed store with four, 8-byte ones
+// with two (and then two blocks per SM).  The shared memory holds the three
+// per-line arrays of line4 plus the team exchange area.
+bool line6_config(int prec, int coef_fp16, int n, int *team, int *lines_per_block, int *nthreads, size_t *smem,
+                  int lines)
 {
     if (prec != PREC_FP32) return false;
     if (n % 4 != 0 || n <= MAX_LINE2_TRANSPOSED || n > 4096) return false;
     if (coef_fp16 && n % 8 != 0) return false;
+    if (lines != 2 && lines != 4) return false;
     const int m = n / 4;
-    int P = 64;
-    while (P < 128 && m / (2 * P) >= 8) P *= 2;
-    const int L = 4;
+    const int P = 128;
+    const int L = lines;
     const size_t sm = (size_t)L * (3 * (size_t)m * 16 + 4 * (size_t)P * sizeof(float));
     if (sm > SMEM_LIMIT - 2048) return false;
     *team = P;

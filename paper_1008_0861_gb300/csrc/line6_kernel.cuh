@@ -77,40 +77,58 @@ __global__ void __launch_bounds__(512, 1) line6_kernel(Line2Args args)
     R *ex0 = ex, *ex1 = ex + P, *ex2 = ex + 2 * P, *ex3 = ex + 3 * P;  // team exchange
     auto swz = [mfull, logU](int c) { return c < mfull ? c ^ ((c >> logU) & 7) : c; };
 
-    // ---- A: face fluxes and lam*g, coalesced (lane t: chunks v*P + t), last round first
+    // ---- A: face fluxes and lam*g, coalesced (lane t: chunks v*P + t), last
+    // round first, with the loads of the next two rounds in flight.  The
+    // cell after a chunk comes from the next lane by a shuffle; the warp's
+    // last lane and the lane with the line's last chunk read it directly
+    // (issued with the round's loads).
     {
         const VT *vd = reinterpret_cast<const VT *>(rd), *vc = reinterpret_cast<const VT *>(rc),
                  *vu = reinterpret_cast<const VT *>(ru);
-        int cl = min((V - 1) * P + t, m - 1);
-        VT xc = vc[cl], xd = vd[cl], xu = vu[cl];
-        auto xg = ld_raw(G + cl * N), xe = ld_raw(E + cl * N);
+        typedef decltype(ld_raw(G)) CT;
+        struct In {
+            VT c, d, u;
+            CT g, e;
+            R nc, nd, nu;  // T of the cell after the chunk (loaded where needed)
+            int cur;
+        };
+        auto load = [&](int v) {
+            In x;
+            x.cur = min(v * P + t, m - 1);
+            x.c = vc[x.cur];
+            x.d = vd[x.cur];
+            x.u = vu[x.cur];
+            x.g = ld_raw(G + x.cur * N);
+            x.e = ld_raw(E + x.cur * N);
+            x.nc = x.nd = x.nu = R(0);
+            if (lane == 31 || x.cur == m - 1) {
+                const int p1 = x.cur == m - 1 ? (J.per_line ? 0 : n - 1) : N * (x.cur + 1);
+                x.nc = rc[p1];
+                x.nd = rd[p1];
+                x.nu = ru[p1];
+            }
+            return x;
+        };
+        In cur = load(V - 1);
+        In nxt = V >= 2 ? load(V - 2) : cur;
         for (int v = V - 1; v >= 0; --v) {
+            const In x = cur;
+            cur = nxt;
+            if (v >= 2) nxt = load(v - 2);
             const int c = v * P + t;
             R Td[N], Tc[N], Tu[N], Gv[N], Ev[N];
-            V16<R>::unpack(xc, Tc);
-            V16<R>::unpack(xd, Td);
-            V16<R>::unpack(xu, Tu);
-            unpack_raw(xg, Gv);
-            unpack_raw(xe, Ev);
-            const int cur = cl;
-            if (v > 0) {
-                cl = (v - 1) * P + t;  // always < m
-                xc = vc[cl];
-                xd = vd[cl];
-                xu = vu[cl];
-                xg = ld_raw(G + cl * N);
-                xe = ld_raw(E + cl * N);
-            }
+            V16<R>::unpack(x.c, Tc);
+            V16<R>::unpack(x.d, Td);
+            V16<R>::unpack(x.u, Tu);
+            unpack_raw(x.g, Gv);
+            unpack_raw(x.e, Ev);
             R vv[N];
 #pragma unroll
             for (int j = 0; j < N; ++j) vv[j] = level<R, VL>(lim, Tu[j] - Tc[j], Tc[j] - Td[j]);
             R nT = __shfl_down_sync(full, Tc[0], 1), nv = __shfl_down_sync(full, vv[0], 1);
-            if (lane == 31 || cur == m - 1) {
-                // the cell after this chunk: another warp's (or the next
-                // round's) first cell, or past the line's end
-                const int p1 = cur == m - 1 ? (J.per_line ? 0 : n - 1) : N * (cur + 1);
-                nT = rc[p1];
-                nv = level<R, VL>(lim, ru[p1] - nT, nT - rd[p1]);
+            if (lane == 31 || x.cur == m - 1) {
+                nT = x.nc;
+                nv = level<R, VL>(lim, x.nu - nT, nT - x.nd);
             }
             R F[N], lg[N];
 #pragma unroll
@@ -270,6 +288,20 @@ __global__ void __launch_bounds__(512, 1) line6_kernel(Line2Args args)
         R *out = static_cast<R *>(J.Tout);
         const int groups = LPB >> 2;
         const bool vec_ok = (nl & 3) == 0;
+        if (LPB == 2) {  // two lines: 8-byte pieces
+            for (int p = threadIdx.x; p < n; p += blockDim.x) {
+                const int sc = swz(p >> 2), j = p & 3;
+                const R o0 = reinterpret_cast<const R *>(reinterpret_cast<const VT *>(smem_raw) + sc)[j];
+                const R o1 = reinterpret_cast<const R *>(reinterpret_cast<const VT *>(smem_raw) + 3 * m + sc)[j];
+                R *dst = out + (size_t)p * nl + line0;
+                if ((nl & 1) == 0 && line0 + 2 <= nl) {
+                    *reinterpret_cast<float2 *>(dst) = make_float2(o0, o1);
+                } else {
+                    if (line0 < nl) dst[0] = o0;
+                    if (line0 + 1 < nl) dst[1] = o1;
+                }
+            }
+        }
         for (int p = threadIdx.x; p < n; p += blockDim.x) {
             const int sc = swz(p >> 2), j = p & 3;
             for (int grp = 0; grp < groups; ++grp) {
