@@ -60,9 +60,10 @@ def parse():
                     help="16-byte chunks per thread segment (0: library default)")
     ap.add_argument("--fast", type=int, default=-1,
                     help="ANISO_OPT_FAST_PATH value (-1: library default)")
-    ap.add_argument("--workload", default="batch", choices=["batch", "random3d"],
+    ap.add_argument("--workload", default="batch", choices=["batch", "random3d", "random4096"],
                     help="batch: the 512-grid 2-D benchmark (default); random3d: one 256^3 "
-                         "grid of the three-dimensional split")
+                         "grid of the three-dimensional split; random4096: one 4096^2 FP32 grid "
+                         "(100 steps per call, lines above 2048 cells)")
     return ap.parse_args()
 
 
@@ -103,8 +104,8 @@ def measured_peak():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("sweep_kernels.cuh", "line2_kernel.cuh", "line4_kernel.cuh",
-              "aniso_internal.h", "util_kernels.cu", "kernels_f32.cu", "kernels_line4.cu",
+    for f in ("sweep_kernels.cuh", "line2_kernel.cuh", "line4_kernel.cuh", "line6_kernel.cuh",
+              "aniso_internal.h", "util_kernels.cu", "kernels_f32.cu", "kernels_line4.cu", "kernels_line6.cu",
               "kernels_3d.cu"):
         h.update(open(os.path.join(ROOT, "paper_1008_0861_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
@@ -929,12 +930,149 @@ def run_reference_3d(args):
     return 0
 
 
+# ------------------------------------------------------ one large 2-D grid
+
+WS_N = 4096
+WS_STEPS = 100
+WORKLOAD_SINGLE = ("one periodic 4096^2 random-field grid (|k| <= 8, 16 Gaussians), chi_par 0.05, dt = 100 x "
+                   "the explicit limit, FP32 state and coefficients, 100 steps per call through aniso_step")
+
+
+def make_single(rank=0):
+    import workloads as W
+    return W.random_instance(WS_N, WS_N, seed=W.BASE_SEED + rank, dt_factor=100.0, nsteps=WS_STEPS)
+
+
+def main_single(args):
+    """bench.py --workload random4096: one JSON line for the 4096^2 grid (one
+    bench step = one aniso_step call of 100 steps; both updates run the
+    long-line kernel, whose launches are timed with CUDA events)."""
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_1008_0861_gb300 as P
+    P.load()
+    inst = make_single(rank)
+    h = P.aniso_create(inst.nx, inst.ny, inst.dx, inst.dy, inst.chi_par, 0.0, inst.bc)
+    P.aniso_set_option(h, P.ANISO_OPT_PRECISION, P.ANISO_PREC_FP32)
+    bx = torch.tensor(inst.bx, dtype=torch.float32, device="cuda")
+    by = torch.tensor(inst.by, dtype=torch.float32, device="cuda")
+    P.aniso_set_field(h, bx, by)
+    del bx, by
+    T = torch.tensor(inst.T0, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        P.aniso_step(h, T, inst.dt, inst.nsteps)
+    P.aniso_sync(h)
+    P.aniso_set_option(h, P.ANISO_OPT_PROFILE, 1)
+    P.aniso_step(h, T, inst.dt, inst.nsteps)  # graph with the timing events
+    P.aniso_sync(h)
+    P.aniso_kernel_times(h=h, kind=0, reset=True)
+    P.aniso_kernel_times(h=h, kind=1, reset=True)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            P.aniso_step(h, T, inst.dt, inst.nsteps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms_call = e0.elapsed_time(e1) / args.steps
+    kt = {k: P.aniso_kernel_times(h=h, kind=k) for k in (0, 1)}
+    cell_steps = inst.cells * inst.nsteps
+    value, ms_step, _ = job_throughput(cell_steps, ms_call, "cuda")
+    # e2e: pinned host T in, one call, host T out
+    host = torch.empty(T.shape, dtype=torch.float32, pin_memory=True)
+    host.copy_(T)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(max(1, min(3, args.steps))):
+        T.copy_(host, non_blocking=True)
+        P.aniso_step(h, T, inst.dt, inst.nsteps)
+        host.copy_(T, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_value, _, _ = job_throughput(cell_steps, e0.elapsed_time(e1) / max(1, min(3, args.steps)), "cuda")
+    peak, note = measured_peak()
+    names = {0: "xsweep", 1: "ysweep"}
+    dom = max(kt, key=lambda k: kt[k][0])
+    launch_ms = kt[dom][0] / max(1, kt[dom][1])
+    achieved = BYTES_PER_CELL_SWEEP * inst.cells / (launch_ms * 1e-3) / 1e9
+    line = {
+        "metric": "Gcell-steps/s, one 4096^2 FP32 grid; % HBM peak", "value": value, "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD_SINGLE, "cells_per_gpu": inst.cells, "steps_per_call": inst.nsteps,
+                   "l2": "inputs larger than L2: %.2f GB resident (T, T*, 4 coefficient arrays, 2 transposed)"
+                         % (inst.cells * 4 * 8 / 1e9),
+                   "parallelism": "one independent grid per GPU (no collective)"},
+        "roofline": {"bound": "hbm", "kernel": "line6_" + names[dom], "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak, "peak_source": note,
+                     "traffic": ncu_traffic("line6_4096"),
+                     "algorithmic_bytes_per_launch": BYTES_PER_CELL_SWEEP * inst.cells, "avg_launch_ms": launch_ms},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": inst.cells * 4,
+                "d2h_bytes_per_step": inst.cells * 4},
+        "clocks": clk.summary(),
+        "gpu_launches": 2 * inst.nsteps * args.steps,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    P.aniso_destroy(h)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def run_reference_single(args):
+    """The FP64 oracle on the 4096^2 grid: whole steps until the time budget."""
+    rank, _, _ = dist_env()
+    if rank != 0:
+        return 0
+    import numpy as np
+    import oracle as O
+    inst = make_single()
+    co = O.face_coeffs(_w32(inst.bx), _w32(inst.by), inst.bc, inst.chi_par)
+    budget = max(2.0, 120.0 / max(1, args.steps + args.warmup))
+    T = _w32(inst.T0)
+    vals, ms = [], []
+    for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        n = 0
+        while time.perf_counter() - t0 < budget:
+            T = O.step(T, co, inst.bc, inst.dt, inst.dx, inst.dy, inst.chi_par, nsteps=1)
+            n += 1
+        el = time.perf_counter() - t0
+        if k >= args.warmup:
+            vals.append(inst.cells * n / el / 1e9)
+            ms.append(el * 1e3)
+    v = statistics.median(vals)
+    line = {"impl": "reference", "metric": "Gcell-steps/s, one 4096^2 FP32 grid; % HBM peak", "value": v,
+            "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": statistics.median(ms), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": {"workload": WORKLOAD_SINGLE},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+                             "sample": "whole steps of the 4096^2 grid for %.0f s per bench step" % budget},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
-        return run_reference_3d(args) if args.workload == "random3d" else run_reference(args)
+        if args.workload == "random3d":
+            return run_reference_3d(args)
+        if args.workload == "random4096":
+            return run_reference_single(args)
+        return run_reference(args)
     if args.workload == "random3d":
         return main_3d(args)
+    if args.workload == "random4096":
+        return main_single(args)
     import numpy as np
     import torch
     rank, world, local = dist_env()
