@@ -159,29 +159,42 @@ bool line4_config(int prec, int n, bool transposed, int warps, int seg_chunks, i
 }
 
 // Diagnostics of one batched line4 launch: job j's blocks are
-// [block0, block0 + nblocks); their partials are added in block order.
+// [block0, block0 + nblocks).  One warp per job: lane l adds the partials of
+// blocks block0 + l, + 32, ... in order, then the lanes' sums are combined by
+// a fixed shuffle tree, so the result does not depend on timing.
 __global__ void diag_finish_kernel(const Line2Job *jobs, int njobs, const DiagPart *part, double *ring)
 {
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < njobs; j += gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const unsigned full = 0xffffffffu;
+    for (int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < njobs; j += (gridDim.x * blockDim.x) >> 5) {
         const Line2Job &J = jobs[j];
         if (J.diag_slot < 0) continue;
         double sum = 0.0, mn = INFINITY, mx = -INFINITY;
-        for (int b = J.block0; b < J.block0 + J.nblocks; ++b) {
+        for (int b = J.block0 + lane; b < J.block0 + J.nblocks; b += 32) {
             sum += part[b].sum;
             mn = fmin(mn, part[b].mn);
             mx = fmax(mx, part[b].mx);
         }
-        double *o = ring + 3 * (size_t)J.diag_slot;
-        o[0] = sum;
-        o[1] = mn;
-        o[2] = mx;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            sum += __shfl_xor_sync(full, sum, o);
+            mn = fmin(mn, __shfl_xor_sync(full, mn, o));
+            mx = fmax(mx, __shfl_xor_sync(full, mx, o));
+        }
+        if (lane == 0) {
+            double *out = ring + 3 * (size_t)J.diag_slot;
+            out[0] = sum;
+            out[1] = mn;
+            out[2] = mx;
+        }
     }
 }
 
 cudaError_t launch_diag_finish(const Line2Job *jobs, int njobs, const DiagPart *part, double *ring, cudaStream_t s)
 {
     if (njobs <= 0) return cudaSuccess;
-    diag_finish_kernel<<<(njobs + 127) / 128, 128, 0, s>>>(jobs, njobs, part, ring);
+    const int warps = 8;  // jobs per block
+    diag_finish_kernel<<<(njobs + warps - 1) / warps, 32 * warps, 0, s>>>(jobs, njobs, part, ring);
     return cudaGetLastError();
 }
 
