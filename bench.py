@@ -56,6 +56,8 @@ def parse():
                     help="only the timed batch: no accuracy, FP64, single-grid or 3-D legs")
     ap.add_argument("--tma-lines", type=int, default=-1,
                     help="ANISO_OPT_TMA_LINES for the batch (-1: library default)")
+    ap.add_argument("--tmem", type=int, default=-1,
+                    help="ANISO_OPT_TMEM for the batch (-1: library default)")
     ap.add_argument("--segment", type=int, default=0,
                     help="16-byte chunks per thread segment (0: library default)")
     ap.add_argument("--fast", type=int, default=-1,
@@ -1108,6 +1110,8 @@ def main():
     P.aniso_set_option(handles[0], P.ANISO_OPT_PROFILE, 1)
     if args.tma_lines >= 0:
         P.aniso_set_option(handles[0], P.ANISO_OPT_TMA_LINES, args.tma_lines)
+    if args.tmem >= 0:
+        P.aniso_set_option(handles[0], P.ANISO_OPT_TMEM, args.tmem)
     batch = P.aniso_batch_create(handles)
     P.aniso_set_option(handles[0], P.ANISO_OPT_PROFILE, 0)
     dts = [i.dt for i in insts]

@@ -91,7 +91,7 @@ enum {
     ANISO_OPT_DIAGNOSTICS = 12, /* 1: batched calls record, after every step of every grid on the
                                   fast path, the FP64 sum of T, its minimum and its maximum (read
                                   with aniso_batch_diagnostics); taken from the batch's first handle */
-    ANISO_OPT_TMA_LINES = 13   /* batched calls, FP32 with FP32 coefficients: 1 solves the lines of
+    ANISO_OPT_TMA_LINES = 13,  /* batched calls, FP32 with FP32 coefficients: 1 solves the lines of
                                   768 to 1024 cells (multiples of 32) with the kernel that stages
                                   each block's rows by tensor-map (TMA) tile loads and keeps the
                                   line state in registers; 0 (default: faster on the uneven batch,
@@ -102,6 +102,12 @@ enum {
                                   ANISO_ERR_TIMEOUT at the next aniso_sync / aniso_total of the
                                   first handle.  Taken from the batch's first handle.  Y-updates
                                   recorded by ANISO_OPT_DIAGNOSTICS use the warp-per-line kernel. */
+    ANISO_OPT_TMEM = 14        /* batched calls, FP32, four-warp blocks: 1 (default) keeps part of the
+                                  warp-per-line kernel's line state in the SM's tensor memory (TMEM)
+                                  instead of shared memory when every line of a sweep fits (at most
+                                  15 chunks of 4 cells a lane), so more blocks fit an SM; 0 keeps
+                                  it all in shared memory.  Results are the same bit for bit.
+                                  Taken from the batch's first handle. */
 };
 enum { ANISO_PREC_FP64 = 0, ANISO_PREC_FP32 = 1 };
 enum {

@@ -91,6 +91,7 @@ struct aniso_ctx {
     int prec = PREC_FP64, field_fp16 = 0, kahan = 0, limiter = LIM_VANLEER, order = ANISO_ORDER_XY;
     int use_graph = 1, profile = 0, fast = 3, seg_chunks = 0, l4_warps = 0, scheme = 0, diag = 0;
     int tma_lines = 0;  // ANISO_OPT_TMA_LINES
+    int tmem = 1;       // ANISO_OPT_TMEM
     double nl_alpha = 0, nl_tref = 1;  // temperature-dependent diffusivity (aniso_set_nonlinear)
     void *t4 = nullptr;  // intermediate of the 4-step scheme
     void *q = nullptr;   // source term (aniso_set_source), handle precision
@@ -249,6 +250,9 @@ extern "C" int aniso_set_option(aniso_t h, int key, long long v)
         break;
     case ANISO_OPT_DIAGNOSTICS:
         h->diag = v != 0;
+        break;
+    case ANISO_OPT_TMEM:
+        h->tmem = v != 0;
         break;
     case ANISO_OPT_TMA_LINES:
         if (v < 0 || v > 2) return fail(ANISO_ERR_ARG, "bad TMA-lines value %lld", v);
@@ -934,6 +938,7 @@ struct aniso_batch {
     // per-step diagnostics (ANISO_OPT_DIAGNOSTICS of the first handle)
     int key_diag = -1;
     int key_tma = -1;
+    int key_tmem = -1;
     double *d_ring = nullptr;  // [grid][step][sum, min, max] of the last call
     size_t ring_count = 0;     // doubles
     int ring_steps = 0;        // steps per grid in the ring (the call's largest nsteps)
@@ -1005,6 +1010,7 @@ static int batch_build(aniso_batch *b, void *const *T, const double *dt, const i
         double dt = 0;
         long long table = -1;  // line4: offset of the block -> job table, or -1
         int diag_region = -1;  // line4 y-update with diagnostics: its partials region
+        int tmem = 0;          // line4: gamma in tensor memory
     };
     std::vector<unsigned char> blob;
     std::vector<Launch> launches;  // in enqueue order
@@ -1101,15 +1107,22 @@ static int batch_build(aniso_batch *b, void *const *T, const double *dt, const i
             if (line4_config(prec, J.n, true, warps, seg, &J.team, &J.lines_per_block, &nt, &sm))
                 nthreads = std::max(nthreads, nt);
         }
+        // the tensor-memory form when every line of the sweep fits it
+        bool tm = b->hs[0]->tmem != 0;
+        for (auto &J : jobs) {
+            int t0, t1, t2;
+            size_t t3;
+            tm = tm && line4_config(prec, J.n, true, nthreads / 32, seg, &t0, &t1, &t2, &t3, true);
+        }
         std::vector<std::pair<int, size_t>> cls(jobs.size());  // (blocks per SM, own shared memory)
         for (size_t k = 0; k < jobs.size(); ++k) {
             Line2Job &J = jobs[k];
             int nt = 0;
             size_t sm = 0;
-            if (!line4_config(prec, J.n, true, nthreads / 32, seg, &J.team, &J.lines_per_block, &nt, &sm) ||
+            if (!line4_config(prec, J.n, true, nthreads / 32, seg, &J.team, &J.lines_per_block, &nt, &sm, tm) ||
                 nt != nthreads)
                 shape_rc = fail(ANISO_ERR_UNSUPPORTED, "batch: line length %d does not fit the block shape", J.n);
-            const int occ = line4_blocks_per_sm(prec, fp16, b->hs[0]->limiter, nthreads, sm);
+            const int occ = line4_blocks_per_sm(prec, fp16, b->hs[0]->limiter, nthreads, sm, tm);
             cls[k] = {occ > 0 ? occ : 0, sm};
         }
         // classes in ascending occupancy (largest lines first); at most
@@ -1136,6 +1149,7 @@ static int batch_build(aniso_batch *b, void *const *T, const double *dt, const i
             if (part.empty()) continue;
             Launch L{kind_xy == 0 ? 7 : 8, blob.size(), (int)part.size(), blocks, nthreads, smem};
             L.group = group;
+            L.tmem = tm ? 1 : 0;
             if (kind_xy == 1 && diag) L.diag_region = (int)ci;
             const unsigned char *p = reinterpret_cast<const unsigned char *>(part.data());
             blob.insert(blob.end(), p, p + part.size() * sizeof(Line2Job));
@@ -1456,6 +1470,7 @@ static int batch_build(aniso_batch *b, void *const *T, const double *dt, const i
             a.njobs = L.njobs;
             if (L.table >= 0)
                 a.block_job = reinterpret_cast<const int *>(static_cast<unsigned char *>(b->d_jobs) + L.table);
+            a.tmem = L.tmem;
             if (L.diag_region >= 0) {
                 a.diag_part = b->d_part + (size_t)L.diag_region * part_blocks;
                 cudaError_t e = launch_line4(prec, fp16, a, L.nblocks, L.nthreads, L.smem, st);
@@ -1592,7 +1607,7 @@ extern "C" int aniso_step_batched(aniso_batch_t b, void *const *T, const double 
     for (int k = 0; k < n; ++k)
         parity[k] = b->hs[k]->order == ANISO_ORDER_ALTERNATE ? (int)(b->hs[k]->step_counter & 1) : -b->hs[k]->order;
     const bool hit = b->gexec && b->key_profile == b->profile && b->key_diag == b->hs[0]->diag &&
-                     b->key_tma == b->hs[0]->tma_lines &&
+                     b->key_tma == b->hs[0]->tma_lines && b->key_tmem == b->hs[0]->tmem &&
                      b->key_T == std::vector<void *>(T, T + n) &&
                      b->key_dt == std::vector<double>(dt, dt + n) &&
                      b->key_n == std::vector<int>(nsteps, nsteps + n) && b->key_parity == parity;
@@ -1612,6 +1627,7 @@ extern "C" int aniso_step_batched(aniso_batch_t b, void *const *T, const double 
         b->key_profile = b->profile;
         b->key_diag = b->hs[0]->diag;
         b->key_tma = b->hs[0]->tma_lines;
+        b->key_tmem = b->hs[0]->tmem;
     }
     if (b->profile && !b->prof.pending.empty()) {
         CU(cudaStreamSynchronize(b->stream));

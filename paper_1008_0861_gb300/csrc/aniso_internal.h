@@ -120,6 +120,9 @@ struct Line2Args {
     // optional (line4, 2-D): every block writes the sum, min and max of the
     // values it stores to diag_part[blockIdx.x]
     DiagPart *diag_part;
+    // line4, FP32 2-D, four-warp blocks: 1 keeps each lane's gamma in tensor
+    // memory (the launch's shared memory then holds two arrays, not three)
+    int tmem;
 };
 // Finish the diagnostics of one line4 launch: for every job, the partials of
 // its blocks in block order -> ring[diag_slot] = (sum, min, max).
@@ -156,8 +159,10 @@ cudaError_t launch_source(int prec, void *T, const void *Q, double dt, size_t n,
 // warps: warps per block (0 = default of 4); seg_chunks: target 16-byte
 // chunks per lane (0 = default of 4), which sets the team size and so the
 // PCR depth.
+// tmem: the tensor-memory form (FP32, four-warp blocks, at most 15 chunks a
+// lane); false when the line does not fit it.
 bool line4_config(int prec, int n, bool transposed, int warps, int seg_chunks, int *team, int *lines_per_block,
-                  int *nthreads, size_t *smem);
+                  int *nthreads, size_t *smem, bool tmem = false);
 cudaError_t launch_line4(int prec, int coef_fp16, const Line2Args &a, int nblocks, int nthreads,
                          size_t smem, cudaStream_t s);
 // Long lines (line6): 2048 < n <= 4096, FP32, teams of 128 lanes over four
@@ -167,7 +172,7 @@ bool line6_config(int prec, int coef_fp16, int n, int *team, int *lines_per_bloc
 cudaError_t launch_line6(int coef_fp16, const Line2Args &a, int nblocks, int nthreads, size_t smem, cudaStream_t s);
 // Resident blocks per SM of the 2-D line4 kernel for that block size and
 // dynamic shared memory (CUDA's occupancy calculator), or -1.
-int line4_blocks_per_sm(int prec, int coef_fp16, int limiter, int nthreads, size_t smem);
+int line4_blocks_per_sm(int prec, int coef_fp16, int limiter, int nthreads, size_t smem, bool tmem = false);
 // Three-dimensional grids (kernels_3d.cu).  c[0..2] = x faces (normal, with
 // y, with z) in layout [nz][ny][nx]; c[3..5] = y faces (normal, with z, with
 // x) in [nx][nz][ny]; c[6..8] = z faces (normal, with x, with y) in

@@ -39,6 +39,13 @@ cudaError_t launch_line4(int prec, int coef_fp16, const Line2Args &a, int nblock
         return vl ? run4(line4_kernel<float, float, true, false, true>, a, nblocks, nthreads, smem, s)
                   : run4(line4_kernel<float, float, false, false, true>, a, nblocks, nthreads, smem, s);
     }
+    if (a.tmem && prec == PREC_FP32) {  // gamma in tensor memory
+        if (coef_fp16)
+            return vl ? run4(line4_kernel<float, __half, true, false, false, false, true>, a, nblocks, nthreads, smem, s)
+                      : run4(line4_kernel<float, __half, false, false, false, false, true>, a, nblocks, nthreads, smem, s);
+        return vl ? run4(line4_kernel<float, float, true, false, false, false, true>, a, nblocks, nthreads, smem, s)
+                  : run4(line4_kernel<float, float, false, false, false, false, true>, a, nblocks, nthreads, smem, s);
+    }
     if (prec == PREC_FP64)
         return vl ? run4(line4_kernel<double, double, true>, a, nblocks, nthreads, smem, s)
                   : run4(line4_kernel<double, double, false>, a, nblocks, nthreads, smem, s);
@@ -63,9 +70,16 @@ template <typename K> static int occ4(K kern, int nthreads, size_t smem)
     return blocks;
 }
 
-int line4_blocks_per_sm(int prec, int coef_fp16, int limiter, int nthreads, size_t smem)
+int line4_blocks_per_sm(int prec, int coef_fp16, int limiter, int nthreads, size_t smem, bool tmem)
 {
     const bool vl = limiter == LIM_VANLEER;
+    if (tmem && prec == PREC_FP32) {
+        if (coef_fp16)
+            return vl ? occ4(line4_kernel<float, __half, true, false, false, false, true>, nthreads, smem)
+                      : occ4(line4_kernel<float, __half, false, false, false, false, true>, nthreads, smem);
+        return vl ? occ4(line4_kernel<float, float, true, false, false, false, true>, nthreads, smem)
+                  : occ4(line4_kernel<float, float, false, false, false, false, true>, nthreads, smem);
+    }
     if (prec == PREC_FP64)
         return vl ? occ4(line4_kernel<double, double, true>, nthreads, smem)
                   : occ4(line4_kernel<double, double, false>, nthreads, smem);

@@ -141,12 +141,59 @@ template <typename R> __device__ __forceinline__ R face_harmonic(R a, R b)
     return (a > R(0) && b > R(0)) ? R(2) * a * Fast<R>::div(b, a + b) : R(0);
 }
 
+// Tensor memory (TMEM) as per-thread scratch.  A block of four warps
+// allocates TM_COLS columns; warp w owns TMEM lanes 32 (w % 4) .. + 31, one per
+// thread, so each thread has TM_COLS private 32-bit words.  The 32x32b shape
+// moves four consecutive columns of the thread's own lane per instruction
+// (warp-wide, aligned).
+constexpr unsigned TM_COLS = 64;
+__device__ __forceinline__ void tm_alloc(unsigned *s_dst)
+{
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     (unsigned)__cvta_generic_to_shared(s_dst)),
+                 "r"(TM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tm_dealloc(unsigned base)
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(base), "r"(TM_COLS) : "memory");
+}
+__device__ __forceinline__ void tm_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tm_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tm_st4(unsigned taddr, float a, float b, float c, float d)
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(taddr), "r"(__float_as_uint(a)),
+                 "r"(__float_as_uint(b)), "r"(__float_as_uint(c)), "r"(__float_as_uint(d))
+                 : "memory");
+}
+// (the load and its wait in one statement: the registers are defined on exit)
+__device__ __forceinline__ void tm_ld4(unsigned taddr, float *o)
+{
+    unsigned r0, r1, r2, r3;
+    asm volatile(
+        "{\n\ttcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];\n\t"
+        "tcgen05.wait::ld.sync.aligned;\n\t}"
+        : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+        : "r"(taddr)
+        : "memory");
+    o[0] = __uint_as_float(r0);
+    o[1] = __uint_as_float(r1);
+    o[2] = __uint_as_float(r2);
+    o[3] = __uint_as_float(r3);
+}
+__device__ __forceinline__ void tm_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
 // IMPL: a purely implicit update (no transverse term, mu = mu2 = 0: the second
 // half-update of each axis in the 4-step scheme); neighbouring lines and
 // transverse coefficients are then neither loaded nor limited.
-template <typename R, typename C, bool VL, bool D3 = false, bool NL = false, bool IMPL = false>
+// TM (FP32, 2-D, four-warp blocks, at most 15 chunks a lane): each lane's
+// gamma lives in its TMEM lane instead of shared memory, so the line state in
+// shared memory is 8 bytes a cell instead of 12 and more blocks fit an SM.
+template <typename R, typename C, bool VL, bool D3 = false, bool NL = false, bool IMPL = false, bool TM = false>
 __global__ void __launch_bounds__(256, sizeof(R) == 4 ? (D3 ? 3 : 4) : 2) line4_kernel(Line2Args args)
 {
+    static_assert(!TM || (sizeof(R) == 4 && !D3), "TMEM line state: FP32 2-D only");
     typedef typename V16<R>::T VT;
     constexpr int N = V16<R>::N;
     constexpr int LOGN = N == 4 ? 2 : 1;
@@ -215,10 +262,22 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? (D3 ? 3 : 4) : 2) line4_
     const int V = U + (rr ? 1 : 0);  // chunk rounds of the coalesced phases
     const int WA = m << logL;        // chunks per array in one warp's area
     const int mfull = m & ~7, logU = 31 - __clz(U);
-    VT *wbase = reinterpret_cast<VT *>(smem_raw) + (size_t)warp * 3 * WA;
+    constexpr int NARR = TM ? 2 : 3;  // shared arrays per warp area
+    VT *wbase = reinterpret_cast<VT *>(smem_raw) + (size_t)warp * NARR * WA;
     VT *sA = wbase + q * m;           // F -> rho -> delta -> T_new
     VT *sB = wbase + WA + q * m;      // lam*g -> alpha
-    VT *sC = wbase + 2 * WA + q * m;  // gamma
+    VT *sC = wbase + 2 * WA + q * m;  // gamma (shared-memory form only)
+    // TMEM form: the block's columns, this warp's lane quarter
+    __shared__ unsigned s_tmem;
+    unsigned tm_base = 0;
+    if constexpr (TM) {
+        if (warp == 0) tm_alloc(&s_tmem);
+        tm_fence_before();
+        __syncthreads();
+        tm_fence_after();
+        tm_base = s_tmem;
+    }
+    const unsigned tm_lane = tm_base + ((unsigned)(32 * (warp & 3)) << 16);
     auto swz = [mfull, logU](int c) { return c < mfull ? c ^ ((c >> logU) & 7) : c; };
 
     // ---- A: face fluxes and lam*g, coalesced (lane t: chunks v*P + t), last round first
@@ -358,7 +417,14 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? (D3 ? 3 : 4) : 2) line4_
         R ro[N], ao[N], go[N];  // maps of the chunk above, waiting for its row 0
 #pragma unroll
         for (int v = 0; v < N; ++v) ro[v] = ao[v] = go[v] = R(0);
-        for (int u = Ut - 1; u >= 0; --u) {
+        // (TMEM form: every lane runs all V rounds, so that the warp-wide TMEM
+        // stores stay uniform; a lane's rounds past its segment do nothing but
+        // store to columns its segment does not use)
+        for (int u = TM ? V - 1 : Ut - 1; u >= 0; --u) {
+            R gs[N];  // gamma of the chunk above once its row 0 is eliminated (TMEM form)
+#pragma unroll
+            for (int j = 0; j < N; ++j) gs[j] = R(0);
+            if (!TM || u < Ut) {
             const int c = c_lo + u;
             R F[N], lg[N], co[N], cao[N], cgo[N];
             V16<R>::unpack(sA[swz(c)], F);
@@ -379,7 +445,12 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? (D3 ? 3 : 4) : 2) line4_
                 elim(Fpend, F[N - 1], lgpend, lg[N - 1], ro[0], ao[0], go[0]);
                 sA[swz(c + 1)] = V16<R>::pack(ro);
                 sB[swz(c + 1)] = V16<R>::pack(ao);
-                sC[swz(c + 1)] = V16<R>::pack(go);
+                if constexpr (TM) {
+#pragma unroll
+                    for (int j = 0; j < N; ++j) gs[j] = go[j];
+                } else {
+                    sC[swz(c + 1)] = V16<R>::pack(go);
+                }
 #pragma unroll
                 for (int j = N - 1; j >= 1; --j) elim(F[j], F[j - 1], lg[j], lg[j - 1], co[j], cao[j], cgo[j]);
             }
@@ -391,6 +462,8 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? (D3 ? 3 : 4) : 2) line4_
                 ao[j] = cao[j];
                 go[j] = cgo[j];
             }
+            }
+            if constexpr (TM) tm_st4(tm_lane + 4u * (unsigned)(u + 1), gs[0], gs[1], gs[2], gs[3]);
         }
         // row s needs the face below the segment: the previous lane's last face
         const int tp = (t - 1) & (P - 1);
@@ -398,7 +471,12 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? (D3 ? 3 : 4) : 2) line4_
         elim(Fpend, Fprev, lgpend, lgprev, ro[0], ao[0], go[0]);
         sA[swz(c_lo)] = V16<R>::pack(ro);
         sB[swz(c_lo)] = V16<R>::pack(ao);
-        sC[swz(c_lo)] = V16<R>::pack(go);
+        if constexpr (TM) {
+            tm_st4(tm_lane, go[0], go[1], go[2], go[3]);
+            tm_wait_st();  // the recovery below reads these columns back
+        } else {
+            sC[swz(c_lo)] = V16<R>::pack(go);
+        }
     }
 
     // Phase C's first two chunks of T_old start loading now, so that their
@@ -420,12 +498,15 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? (D3 ? 3 : 4) : 2) line4_
     // ---- B2: forward recovery of lane t's segment (delta over rho)
     {
         R dprev = Xm;
-        for (int u = 0; u < Ut; ++u) {
+        for (int u = 0; u < (TM ? V : Ut); ++u) {
+            R g4[N];
+            if constexpr (TM) tm_ld4(tm_lane + 4u * (unsigned)u, reinterpret_cast<float *>(g4));  // warp-wide
+            if (TM && u >= Ut) continue;
             const int c = c_lo + u;
-            R r4[N], a4[N], g4[N], d[N];
+            R r4[N], a4[N], d[N];
             V16<R>::unpack(sA[swz(c)], r4);
             V16<R>::unpack(sB[swz(c)], a4);
-            V16<R>::unpack(sC[swz(c)], g4);
+            if constexpr (!TM) V16<R>::unpack(sC[swz(c)], g4);
 #pragma unroll
             for (int j = 0; j < N; ++j) {
                 d[j] = (u == Ut - 1 && j == N - 1) ? X : r4[j] - a4[j] * dprev - g4[j] * X;
@@ -490,7 +571,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? (D3 ? 3 : 4) : 2) line4_
 #pragma unroll
                 for (int i = 0; i < N; ++i) {
                     const int lb = (grp << LOGN) + i;
-                    const VT *src = reinterpret_cast<const VT *>(smem_raw) + (size_t)(lb >> logL) * 3 * WA +
+                    const VT *src = reinterpret_cast<const VT *>(smem_raw) + (size_t)(lb >> logL) * NARR * WA +
                                     (lb & ((1 << logL) - 1)) * m + sc;
                     o[i] = reinterpret_cast<const R *>(src)[j];
                 }
@@ -526,6 +607,14 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? (D3 ? 3 : 4) : 2) line4_
                 p.mx = fmax(p.mx, s_diag[w].mx);
             }
             args.diag_part[blockIdx.x] = p;
+        }
+    }
+    if constexpr (TM) {  // every warp is done with TMEM before the block frees it
+        tm_fence_before();
+        __syncthreads();
+        if (warp == 0) {
+            tm_fence_after();
+            tm_dealloc(tm_base);
         }
     }
 }

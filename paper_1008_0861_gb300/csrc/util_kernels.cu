@@ -134,7 +134,7 @@ bool line2_config(int prec, int n, bool transposed, int *team, int *lines_per_bl
 // of `warps` warps (default 4); with a transposed output the block's line
 // count must fill whole 16-byte stores.
 bool line4_config(int prec, int n, bool transposed, int warps, int seg_chunks, int *team, int *lines_per_block,
-                  int *nthreads, size_t *smem)
+                  int *nthreads, size_t *smem, bool tmem)
 {
     const int N = prec == PREC_FP64 ? 2 : 4;
     if (n % N != 0 || n < 2 * N) return false;
@@ -149,7 +149,9 @@ bool line4_config(int prec, int n, bool transposed, int warps, int seg_chunks, i
     const int L = 32 / P;
     while (transposed && (NW * L) % N != 0) NW *= 2;
     if (NW > 8) return false;
-    const size_t sm = (size_t)NW * 3 * L * m * 16;
+    // the tensor-memory form: each lane keeps 4 V gamma columns of the block's 64
+    if (tmem && (prec != PREC_FP32 || NW != 4 || 4 * V + 4 > 64)) return false;
+    const size_t sm = (size_t)NW * (tmem ? 2 : 3) * L * m * 16;
     if (sm > SMEM_LIMIT - 1024) return false;
     *team = P;
     *lines_per_block = NW * L;
