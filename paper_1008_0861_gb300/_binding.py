@@ -37,6 +37,7 @@ ANISO_OPT_SCHEME = 11
 ANISO_OPT_DIAGNOSTICS = 12
 ANISO_OPT_TMA_LINES = 13
 ANISO_OPT_TMEM = 14
+ANISO_OPT_CLUSTER_LINES = 15
 ANISO_SCHEME_2STEP = 0
 ANISO_SCHEME_4STEP = 1
 ANISO_SCHEME_EXPLICIT = 2

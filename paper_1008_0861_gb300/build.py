@@ -10,9 +10,9 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libaniso.so")
 SOURCES = ["aniso_api.cu", "kernels_f32.cu", "kernels_f64.cu", "util_kernels.cu", "noalloc.cu",
-           "kernels_line4.cu", "kernels_line5.cu", "kernels_line6.cu", "aniso3d_api.cu", "kernels_3d.cu"]
+           "kernels_line4.cu", "kernels_line5.cu", "kernels_line6.cu", "kernels_line7.cu", "aniso3d_api.cu", "kernels_3d.cu"]
 HEADERS = ["aniso_internal.h", "sweep_kernels.cuh", "line2_kernel.cuh",
-           "line4_kernel.cuh", "line5_kernel.cuh", "line5_types.h", "line6_kernel.cuh", "explicit_kernel.cuh", "status.h"]
+           "line4_kernel.cuh", "line5_kernel.cuh", "line5_types.h", "line6_kernel.cuh", "line7_kernel.cuh", "explicit_kernel.cuh", "status.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

@@ -92,6 +92,7 @@ struct aniso_ctx {
     int use_graph = 1, profile = 0, fast = 3, seg_chunks = 0, l4_warps = 0, scheme = 0, diag = 0;
     int tma_lines = 0;  // ANISO_OPT_TMA_LINES
     int tmem = 1;       // ANISO_OPT_TMEM
+    int cluster = 1;    // ANISO_OPT_CLUSTER_LINES
     double nl_alpha = 0, nl_tref = 1;  // temperature-dependent diffusivity (aniso_set_nonlinear)
     void *t4 = nullptr;  // intermediate of the 4-step scheme
     void *q = nullptr;   // source term (aniso_set_source), handle precision
@@ -129,19 +130,34 @@ struct aniso_ctx {
     // Grid shapes the vectorised x-then-y path handles: both line lengths a
     // multiple of the 16-byte vector and short enough for transposed output.
     // 4: warp-per-line kernel (line4, option value 3); 6: line4 for the lines
-    // it takes and the long-line kernel (line6, above 2048 cells, FP32) for
-    // the others, x-then-y steps only; 2: line2; 0: none of them.
+    // it takes and the long-line kernel (line6, 2049-4096 cells, FP32) for
+    // the others, x-then-y steps only; 7: as 6, with lines the cluster kernel
+    // (line7) takes, or the compensated state on line7 in both directions;
+    // 2: line2; 0: none of them.
+    int long_kernel(int n) const
+    {
+        int a, b, c;
+        size_t d;
+        if (cluster == 2 && line7_config(prec, field_fp16, n, &a, &b, &d)) return 7;
+        if (line6_config(prec, field_fp16, n, &a, &b, &c, &d)) return 6;
+        if (cluster != 0 && line7_config(prec, field_fp16, n, &a, &b, &d)) return 7;
+        return 0;
+    }
     int fast_kind() const
     {
         int a, b, c;
         size_t d;
+        if (kahan)
+            return fast == 3 && cluster != 0 && line7_config(prec, field_fp16, nx, &a, &b, &d) &&
+                           line7_config(prec, field_fp16, ny, &a, &b, &d)
+                       ? 7
+                       : 0;
         if (fast == 3) {
             const bool x4 = line4_config(prec, nx, true, l4_warps, seg_chunks, &a, &b, &c, &d);
             const bool y4 = line4_config(prec, ny, true, l4_warps, seg_chunks, &a, &b, &c, &d);
             if (x4 && y4) return 4;
-            if ((x4 || line6_config(prec, field_fp16, nx, &a, &b, &c, &d)) &&
-                (y4 || line6_config(prec, field_fp16, ny, &a, &b, &c, &d)))
-                return 6;
+            const int kx = x4 ? 4 : long_kernel(nx), ky = y4 ? 4 : long_kernel(ny);
+            if (kx && ky) return (kx == 7 || ky == 7) ? 7 : 6;
         }
         if (line2_config(prec, nx, true, &a, &b, &c, &d, seg_chunks) &&
             line2_config(prec, ny, true, &a, &b, &c, &d, seg_chunks))
@@ -253,6 +269,11 @@ extern "C" int aniso_set_option(aniso_t h, int key, long long v)
         break;
     case ANISO_OPT_TMEM:
         h->tmem = v != 0;
+        break;
+    case ANISO_OPT_CLUSTER_LINES:
+        if (v < 0 || v > 2) return fail(ANISO_ERR_ARG, "bad cluster-lines value %lld", v);
+        h->cluster = (int)v;
+        drop_graph(h);
         break;
     case ANISO_OPT_TMA_LINES:
         if (v < 0 || v > 2) return fail(ANISO_ERR_ARG, "bad TMA-lines value %lld", v);
@@ -368,11 +389,19 @@ static int enqueue_line2(aniso_ctx *h, const void *in, void *out, const void *g,
                                 &nthreads, &smem)
                  : line2_config(h->prec, n, transposed, &J.team, &J.lines_per_block, &nthreads, &smem,
                                 h->seg_chunks);
-    // lines above line4's limit: the long-line kernel (constant diffusivity only)
-    const bool v6 = v4 && !ok && h->nl_alpha == 0.0 &&
-                    line6_config(h->prec, h->field_fp16, n, &J.team, &J.lines_per_block, &nthreads, &smem,
-                                 h->l4_warps == 8 ? 2 : 4);
-    ok = ok || v6;
+    // lines above line4's limit: the long-line kernels (constant diffusivity
+    // only); the compensated state runs on the cluster kernel alone
+    if (v4 && in_lo) ok = false;
+    const int lk = v4 && !ok && h->nl_alpha == 0.0 ? (in_lo ? 7 : h->long_kernel(n)) : 0;
+    const bool v6 = lk == 6 && line6_config(h->prec, h->field_fp16, n, &J.team, &J.lines_per_block, &nthreads,
+                                            &smem, h->l4_warps == 8 ? 2 : 4);
+    int cs = 0;
+    const bool v7 = lk == 7 && line7_config(h->prec, h->field_fp16, n, &cs, &nthreads, &smem);
+    if (v7) {
+        J.team = 64;
+        J.lines_per_block = 4;
+    }
+    ok = ok || v6 || v7;
     if (!ok) return fail(ANISO_ERR_UNSUPPORTED, "vectorised line kernel cannot take n=%d", n);
     J.block0 = 0;
     J.nblocks = (nlines + J.lines_per_block - 1) / J.lines_per_block;
@@ -383,7 +412,8 @@ static int enqueue_line2(aniso_ctx *h, const void *in, void *out, const void *g,
         if (pidx < 0) return fail(ANISO_ERR_CUDA, "event creation failed");
         CU(cudaEventRecordWithFlags(h->prof.pool[pidx].a, s, rec_flags));
     }
-    CU(v6   ? launch_line6(h->field_fp16, a, J.nblocks, nthreads, smem, s)
+    CU(v7   ? launch_line7(h->field_fp16, a, cs, smem, s)
+       : v6 ? launch_line6(h->field_fp16, a, J.nblocks, nthreads, smem, s)
        : v4 ? launch_line4(h->prec, h->field_fp16, a, J.nblocks, nthreads, smem, s)
             : launch_line2(h->prec, h->field_fp16, a, J.nblocks, nthreads, smem, s, in_lo != nullptr));
     if (h->profile) {
@@ -397,25 +427,36 @@ static int enqueue_line2(aniso_ctx *h, const void *in, void *out, const void *g,
 // Fast path of one x-then-y step: the x-update reads T row-major and writes T*
 // column-major; the y-update reads T*'s columns as contiguous lines (with the
 // transposed y coefficients) and writes T back row-major.
+// With the compensated state the low parts travel the same way (tlo <->
+// tstar_lo), on the cluster kernel.
 static bool use_fast(const aniso_ctx *h, const void *T)
 {
-    return h->fast && !h->kahan && !h->dirichlet() && h->order == ANISO_ORDER_XY && h->cyyT && aligned16(T) &&
-           aligned16(h->tstar) && h->fast_shape();
+    return h->fast && !h->dirichlet() && h->order == ANISO_ORDER_XY && h->cyyT && aligned16(T) &&
+           aligned16(h->tstar) && (!h->kahan || (aligned16(h->tlo) && aligned16(h->tstar_lo))) &&
+           h->fast_shape();
+}
+
+// One update of the fast path: dir 0 the x-update (T -> T*), 1 the y-update (T* -> T).
+static int enqueue_fast_sweep(aniso_ctx *h, int dir, void *T, double dt, cudaStream_t s, std::vector<int> *pairs)
+{
+    const double mu = h->chi_par * dt / (h->dx * h->dy);
+    const int per = h->bc == ANISO_BC_PERIODIC;
+    const int fk = h->fast_kind();
+    const bool v4 = fk == 4 || fk == 6 || fk == 7;  // line4, or a long-line kernel above its limit
+    if (dir == 0)
+        return enqueue_line2(h, T, h->tstar, h->cxx, h->cxy, h->nx, h->ny, per, per,
+                             h->chi_par * dt / (h->dx * h->dx), mu, true, ANISO_KERNEL_XSWEEP, s, pairs, v4,
+                             h->kahan ? h->tlo : nullptr, h->kahan ? h->tstar_lo : nullptr);
+    return enqueue_line2(h, h->tstar, T, h->cyyT, h->cyxT, h->ny, h->nx, per, per, h->chi_par * dt / (h->dy * h->dy),
+                         mu, true, ANISO_KERNEL_YSWEEP, s, pairs, v4, h->kahan ? h->tstar_lo : nullptr,
+                         h->kahan ? h->tlo : nullptr);
 }
 
 static int enqueue_fast_step(aniso_ctx *h, void *T, double dt, cudaStream_t s, std::vector<int> *pairs)
 {
-    const double lamx = h->chi_par * dt / (h->dx * h->dx);
-    const double lamy = h->chi_par * dt / (h->dy * h->dy);
-    const double mu = h->chi_par * dt / (h->dx * h->dy);
-    const int per = h->bc == ANISO_BC_PERIODIC;
-    const int fk = h->fast_kind();
-    const bool v4 = fk == 4 || fk == 6;  // line4, or line6 for lines above its limit
-    int rc = enqueue_line2(h, T, h->tstar, h->cxx, h->cxy, h->nx, h->ny, per, per, lamx, mu, true,
-                           ANISO_KERNEL_XSWEEP, s, pairs, v4);
+    int rc = enqueue_fast_sweep(h, 0, T, dt, s, pairs);
     if (rc) return rc;
-    return enqueue_line2(h, h->tstar, T, h->cyyT, h->cyxT, h->ny, h->nx, per, per, lamy, mu, true,
-                         ANISO_KERNEL_YSWEEP, s, pairs, v4);
+    return enqueue_fast_sweep(h, 1, T, dt, s, pairs);
 }
 
 // One directional update from `in` to `out` (distinct buffers) on stream s.
@@ -995,7 +1036,8 @@ static int batch_build(aniso_batch *b, void *const *T, const double *dt, const i
     // Every (global step, phase) launch is one list of line jobs (x) and one
     // of column jobs (y).  Identical lists are shared.
     struct Launch {
-        int kind;  // 0 line, 1 col, 2/3 line2 (x/y), 7/8 line4 (x/y), 9/10 line5 (x/y), 11/12 line6 (x/y)
+        int kind;  // 0 line, 1 col, 2/3 line2 (x/y), 7/8 line4 (x/y), 9/10 line5 (x/y), 11/12 line6 (x/y),
+                   // 6 / 13 one grid's general / fast update on its own
         size_t offset;
         int njobs, nblocks, nthreads;
         size_t smem;
@@ -1257,6 +1299,17 @@ static int batch_build(aniso_batch *b, void *const *T, const double *dt, const i
             for (int k = 0; k < n; ++k) {
                 if (s >= nsteps[k]) continue;
                 aniso_ctx *h = b->hs[k];
+                if (use_fast(h, T[k]) && h->fast_kind() == 7) {
+                    // cluster-kernel grids (and the compensated state): the
+                    // grid's fast update captured on its own
+                    Launch L{13, 0, 0, 0, 0, 0};
+                    L.inst = k;
+                    L.dir = phase;
+                    L.out = T[k];
+                    L.dt = dt[k];
+                    solo.push_back(L);
+                    continue;
+                }
                 if (use_fast(h, T[k])) {
                     // x: T (rows) -> T* (column-major); y: T* (columns) -> T (rows)
                     const int per = h->bc == ANISO_BC_PERIODIC;
@@ -1504,11 +1557,12 @@ static int batch_build(aniso_batch *b, void *const *T, const double *dt, const i
     };
     for (size_t i = 0; i < launches.size() && rc == ANISO_OK;) {
         const Launch &L = launches[i];
-        if (L.kind == 6) {
+        if (L.kind == 6 || L.kind == 13) {
             aniso_ctx *h = b->hs[L.inst];
             const int saved = h->profile;  // these sweeps are not profiled inside the batch
             h->profile = 0;
-            rc = enqueue_sweep(h, L.dir, L.in, L.out, L.dt, b->cap_stream, nullptr, L.in_lo, L.out_lo);
+            rc = L.kind == 13 ? enqueue_fast_sweep(h, L.dir, L.out, L.dt, b->cap_stream, nullptr)
+                              : enqueue_sweep(h, L.dir, L.in, L.out, L.dt, b->cap_stream, nullptr, L.in_lo, L.out_lo);
             h->profile = saved;
             if (rc) break;
             ++i;
