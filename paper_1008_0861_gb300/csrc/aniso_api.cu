@@ -106,6 +106,10 @@ struct aniso_ctx {
     void *tA = nullptr, *tB = nullptr;      // transposed scratch (long columns)
     // compensated (Kahan) low parts: of T, of T*, of the transposed scratch
     void *tlo = nullptr, *tstar_lo = nullptr, *tAlo = nullptr, *tBlo = nullptr;
+    // compensated state on the cluster kernel: hi and lo interleaved by quads
+    // of 4 cells (8 floats), the state between the steps of a call (kq, row
+    // quads) and the intermediate (kqs, column quads)
+    void *kq = nullptr, *kqs = nullptr;
     double *partials = nullptr, *result = nullptr;
     unsigned *err = nullptr;
     // graph cache
@@ -172,6 +176,7 @@ static void free_buffers(aniso_ctx *h)
 {
     void **bufs[] = {&h->cxx, &h->cxy, &h->cyy,      &h->cyx,  &h->cyyT, &h->cyxT, &h->tstar,
                      &h->tA,  &h->tB,  &h->tlo, &h->tstar_lo, &h->tAlo, &h->tBlo, &h->t4,
+                     &h->kq,  &h->kqs,
                      &h->q};
     for (void **b : bufs) {
         if (*b) cudaFree(*b);
@@ -358,7 +363,7 @@ static bool aligned16(const void *p) { return ((uintptr_t)p & 15) == 0; }
 static int enqueue_line2(aniso_ctx *h, const void *in, void *out, const void *g, const void *e, int n,
                          int nlines, int per_line, int per_cross, double lam, double mu, bool transposed,
                          int kind, cudaStream_t s, std::vector<int> *pairs, bool v4 = false,
-                         const void *in_lo = nullptr, void *out_lo = nullptr)
+                         const void *in_lo = nullptr, void *out_lo = nullptr, int ilv_in = 0, int ilv_out = 0)
 {
     Line2Args a{};
     a.jobs = nullptr;
@@ -379,6 +384,8 @@ static int enqueue_line2(aniso_ctx *h, const void *in, void *out, const void *g,
     J.per_line = per_line;
     J.per_cross = per_cross;
     J.transpose_out = transposed ? 1 : 0;
+    J.ilv_in = ilv_in;
+    J.ilv_out = ilv_out;
     if (v4 && h->nl_alpha != 0.0) {
         J.chi_alpha = h->nl_alpha;
         J.chi_itref = 1.0 / h->nl_tref;
@@ -450,6 +457,39 @@ static int enqueue_fast_sweep(aniso_ctx *h, int dir, void *T, double dt, cudaStr
     return enqueue_line2(h, h->tstar, T, h->cyyT, h->cyxT, h->ny, h->nx, per, per, h->chi_par * dt / (h->dy * h->dy),
                          mu, true, ANISO_KERNEL_YSWEEP, s, pairs, v4, h->kahan ? h->tstar_lo : nullptr,
                          h->kahan ? h->tlo : nullptr);
+}
+
+// nsteps compensated steps on the cluster kernel: the first x-update reads
+// (T, lo), the last y-update writes them; in between the state and the
+// intermediate stay interleaved (kq, kqs), so that every transposed store
+// fills whole 32-byte sectors.
+static int enqueue_fast_steps_k(aniso_ctx *h, void *T, double dt, int nsteps, cudaStream_t s,
+                                std::vector<int> *pairs)
+{
+    const double mu = h->chi_par * dt / (h->dx * h->dy);
+    const double lamx = h->chi_par * dt / (h->dx * h->dx), lamy = h->chi_par * dt / (h->dy * h->dy);
+    const int per = h->bc == ANISO_BC_PERIODIC;
+    for (int k = 0; k < nsteps; ++k) {
+        const bool first = k == 0, last = k == nsteps - 1;
+        int rc = enqueue_line2(h, first ? T : h->kq, h->kqs, h->cxx, h->cxy, h->nx, h->ny, per, per, lamx, mu, true,
+                               ANISO_KERNEL_XSWEEP, s, pairs, true, first ? h->tlo : h->kq, h->kqs, first ? 0 : 1,
+                               1);
+        if (rc) return rc;
+        rc = enqueue_line2(h, h->kqs, last ? T : h->kq, h->cyyT, h->cyxT, h->ny, h->nx, per, per, lamy, mu, true,
+                           ANISO_KERNEL_YSWEEP, s, pairs, true, h->kqs, last ? h->tlo : h->kq, 1, last ? 0 : 1);
+        if (rc) return rc;
+    }
+    return ANISO_OK;
+}
+
+// The interleaved buffers of the compensated cluster path (allocated once,
+// outside any capture).
+static int ensure_kq(aniso_ctx *h)
+{
+    if (!h->kahan || h->kq || h->fast_kind() != 7) return ANISO_OK;
+    CU(cudaMalloc(&h->kq, h->cells() * 2 * sizeof(float)));
+    CU(cudaMalloc(&h->kqs, h->cells() * 2 * sizeof(float)));
+    return ANISO_OK;
 }
 
 static int enqueue_fast_step(aniso_ctx *h, void *T, double dt, cudaStream_t s, std::vector<int> *pairs)
@@ -735,6 +775,8 @@ static int enqueue_steps(aniso_ctx *h, void *T, double dt, int nsteps, long long
         }
         return ANISO_OK;
     }
+    if (use_fast(h, T) && h->kahan && h->kq && h->fast_kind() == 7)
+        return enqueue_fast_steps_k(h, T, dt, nsteps, s, pairs);
     if (use_fast(h, T)) {
         for (int k = 0; k < nsteps; ++k) {
             if (h->q) CU(launch_source(h->prec, T, h->q, dt, h->cells(), s));
@@ -818,6 +860,7 @@ extern "C" int aniso_step(aniso_t h, void *T, double dt, int nsteps)
     if (nsteps < 0) return fail(ANISO_ERR_ARG, "aniso_step: nsteps must be >= 0");
     if ((rc = check_nonlinear(h, T, "aniso_step"))) return rc;
     if (nsteps == 0) return ANISO_OK;
+    if ((rc = ensure_kq(h))) return rc;
     const int parity = h->order == ANISO_ORDER_ALTERNATE ? (int)(h->step_counter & 1) : 0;
     if (h->use_graph && nsteps >= 2) {
         const bool hit = h->gexec && h->g_T == T && h->g_dt == dt && h->g_nsteps == nsteps &&

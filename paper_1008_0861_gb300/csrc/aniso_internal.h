@@ -101,6 +101,11 @@ struct Line2Job {
     // Per-step diagnostics (batched y-updates with args.diag_part set): slot
     // of this update's (sum, min, max) in the batch's ring, instance * steps + step.
     int diag_slot;
+    // Compensated state on the cluster kernel (line7 with TinLo set): 1 = the
+    // input (ilv_in) or output (ilv_out) is one array of quads, per line and
+    // per 4 cells 4 hi values then 4 lo values (32 bytes, 2 n floats a line);
+    // the TinLo / ToutLo pointers then only mark the compensated state.
+    int ilv_in, ilv_out;
 };
 
 // One block's diagnostics partial: FP64 sum, min and max of its lines' output.

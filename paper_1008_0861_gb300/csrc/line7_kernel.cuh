@@ -69,6 +69,12 @@ __device__ __forceinline__ unsigned cl_id()
     return r;
 }
 __device__ __forceinline__ void cl_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory"); }
+// Arrival that orders nothing: it only says this block has finished reading
+// the others' shared memory (every value read has been used by then).
+__device__ __forceinline__ void cl_arrive_relaxed()
+{
+    asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
+}
 __device__ __forceinline__ void cl_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
 // Shared-window address of the same variable in block `rank` of the cluster.
 __device__ __forceinline__ unsigned cl_map(const void *p, unsigned rank)
@@ -78,17 +84,28 @@ __device__ __forceinline__ unsigned cl_map(const void *p, unsigned rank)
     asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
     return r;
 }
-__device__ __forceinline__ float cl_ld(unsigned addr)
+__device__ __forceinline__ float4 cl_ld4(unsigned addr)
 {
-    float v;
-    asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(addr) : "memory");
+    float4 v;
+    asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "r"(addr)
+                 : "memory");
     return v;
 }
-__device__ __forceinline__ double cl_ld_f64(unsigned addr)
+__device__ __forceinline__ float2 cl_ld2(unsigned addr)
 {
-    double v;
-    asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(addr) : "memory");
+    float2 v;
+    asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr) : "memory");
     return v;
+}
+// Double-word FP32 sum (ah + al) + (bh + bl), renormalised.
+__device__ __forceinline__ void dw_add(float ah, float al, float bh, float bl, float &sh, float &sl)
+{
+    float t, e;
+    two_sum(ah, bh, t, e);
+    e += al + bl;
+    fast_two_sum(t, e, sh, sl);
 }
 
 // Face flux of the delta form at the face between cells a and a + 1:
@@ -117,13 +134,13 @@ __global__ void __launch_bounds__(L7_THREADS, 2) line7_kernel(Line2Args args)
     typedef float4 VT;
     constexpr int N = 4, P = L7_P, WPL = L7_WPL, LPB = L7_LPB;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ float s_pub[LPB][WPL][L7_PUB];  // per warp: the interface system's inputs
+    __shared__ __align__(16) float s_pub[LPB][WPL][L7_PUB];  // per warp: the interface system's inputs
     __shared__ float s_b[LPB][32];             // interface unknowns b_g of each line
     __shared__ float s_ex[LPB][2][P];          // lane t's last face (F, lam g) for lane t + 1
     __shared__ float s_fb[LPB][2];             // the face before the piece (F, lam g)
-    __shared__ double s_wpart[LPB][WPL];       // K: per warp, compensated sum of delta
-    __shared__ double s_lpart[LPB];            // K: per line, this block's part
-    __shared__ double s_lsum[LPB];             // K: per line, the whole line's sum
+    __shared__ float s_wpart[LPB][WPL][2];      // K: per warp, sum of delta (double-word)
+    __shared__ __align__(8) float s_lpart[LPB][2];  // K: per line, this block's part
+    __shared__ float s_corr[LPB][2];            // K: per line, the line's sum / n
 
     const Line2Job &J = args.one;
     const int lim = args.limiter;
@@ -141,11 +158,18 @@ __global__ void __launch_bounds__(L7_THREADS, 2) line7_kernel(Line2Args args)
     if (lu >= nl) lu = J.per_cross ? 0 : nl - 1;  // mirrored ghost line
     if (ld < 0) ld = J.per_cross ? nl - 1 : 0;
     const size_t p0 = (size_t)rk * np;  // first cell of the piece
+    const size_t q0 = p0 / N;            // its first 4-cell quad
+    // Input layout: separate hi / lo arrays (n floats a line), or (ilv) one
+    // array of quads, 4 hi then 4 lo values per 4 cells (2 n floats a line).
+    const bool ilv_in = K && J.ilv_in, ilv_out = K && J.ilv_out;
+    const size_t ls = ilv_in ? 2 * (size_t)n : (size_t)n;
+    auto vi = [ilv_in](size_t qc) { return ilv_in ? 2 * qc : qc; };                    // 16-byte index of quad qc
+    auto si = [ilv_in](size_t q) { return ilv_in ? (((q >> 2) << 3) | (q & 3)) : q; };  // index of cell q
     const R *Tin = static_cast<const R *>(J.Tin);
-    const R *Lc = Tin + (size_t)lc * n, *Lu = Tin + (size_t)lu * n, *Ld = Tin + (size_t)ld * n;
-    const R *TinL = static_cast<const R *>(J.TinLo);
-    const R *Lcl = K ? TinL + (size_t)lc * n : nullptr, *Lul = K ? TinL + (size_t)lu * n : nullptr,
-            *Ldl = K ? TinL + (size_t)ld * n : nullptr;
+    const R *Lc = Tin + (size_t)lc * ls, *Lu = Tin + (size_t)lu * ls, *Ld = Tin + (size_t)ld * ls;
+    const R *TinL = ilv_in ? Tin + N : static_cast<const R *>(J.TinLo);
+    const R *Lcl = K ? TinL + (size_t)lc * ls : nullptr, *Lul = K ? TinL + (size_t)lu * ls : nullptr,
+            *Ldl = K ? TinL + (size_t)ld * ls : nullptr;
     const C *Gl = static_cast<const C *>(J.g) + (size_t)lc * n;
     const C *El = static_cast<const C *>(J.e) + (size_t)lc * n;
     const R lam = (R)J.lam, mu = (R)J.mu;
@@ -160,16 +184,32 @@ __global__ void __launch_bounds__(L7_THREADS, 2) line7_kernel(Line2Args args)
     VT *sC = sA + 2 * m;                                              // gamma
     auto swz = [mfull, logU](int c) { return c < mfull ? c ^ ((c >> logU) & 7) : c; };
 
+    // The block's rows of this piece into L2 (a hint): input lines line0 - 1
+    // .. line0 + 4 (clamped) and the four lines' coefficients.
+    if (threadIdx.x < 6) {
+        const int l = max(0, min(line0 - 1 + (int)threadIdx.x, nl - 1));
+        if (ilv_in) {
+            l2_prefetch(Tin + (size_t)l * ls + 2 * p0, 2 * (size_t)np * sizeof(R));
+        } else {
+            l2_prefetch(Tin + (size_t)l * n + p0, (size_t)np * sizeof(R));
+            if (K) l2_prefetch(static_cast<const R *>(J.TinLo) + (size_t)l * n + p0, (size_t)np * sizeof(R));
+        }
+    } else if (threadIdx.x < 6 + LPB) {
+        const int l = min(line0 + (int)threadIdx.x - 6, nl - 1);
+        l2_prefetch(static_cast<const C *>(J.g) + (size_t)l * n + p0, (size_t)np * sizeof(C));
+        l2_prefetch(static_cast<const C *>(J.e) + (size_t)l * n + p0, (size_t)np * sizeof(C));
+    }
+
     // ---- A: face fluxes and lam*g of the piece, coalesced (lane t: chunks
     // v*P + t), last round first with the next loads in flight.  The cell
     // after a chunk comes from the next lane by a shuffle; the warp's last
     // lane and the piece's last chunk read it directly.
     {
-        const VT *vc = reinterpret_cast<const VT *>(Lc + p0), *vd = reinterpret_cast<const VT *>(Ld + p0),
-                 *vu = reinterpret_cast<const VT *>(Lu + p0);
-        const VT *vcl = K ? reinterpret_cast<const VT *>(Lcl + p0) : nullptr,
-                 *vdl = K ? reinterpret_cast<const VT *>(Ldl + p0) : nullptr,
-                 *vul = K ? reinterpret_cast<const VT *>(Lul + p0) : nullptr;
+        const VT *vc = reinterpret_cast<const VT *>(Lc), *vd = reinterpret_cast<const VT *>(Ld),
+                 *vu = reinterpret_cast<const VT *>(Lu);
+        const VT *vcl = K ? reinterpret_cast<const VT *>(Lcl) : nullptr,
+                 *vdl = K ? reinterpret_cast<const VT *>(Ldl) : nullptr,
+                 *vul = K ? reinterpret_cast<const VT *>(Lul) : nullptr;
         typedef decltype(ld_raw(Gl)) CT;
         struct In {
             VT c, d, u;
@@ -180,13 +220,14 @@ __global__ void __launch_bounds__(L7_THREADS, 2) line7_kernel(Line2Args args)
         auto load = [&](int v) {
             In x;
             const int c = v * P + t;
-            x.c = vc[c];
-            x.d = vd[c];
-            x.u = vu[c];
+            const size_t vq = vi(q0 + c);
+            x.c = vc[vq];
+            x.d = vd[vq];
+            x.u = vu[vq];
             if (K) {
-                x.cl = vcl[c];
-                x.dl = vdl[c];
-                x.ul = vul[c];
+                x.cl = vcl[vq];
+                x.dl = vdl[vq];
+                x.ul = vul[vq];
             }
             x.g = ld_raw(Gl + p0 + (size_t)c * N);
             x.e = ld_raw(El + p0 + (size_t)c * N);
@@ -194,6 +235,7 @@ __global__ void __launch_bounds__(L7_THREADS, 2) line7_kernel(Line2Args args)
             if (lane == 31 || c == m - 1) {
                 size_t q = p0 + (size_t)N * (c + 1);
                 if (q >= (size_t)n) q = J.per_line ? 0 : n - 1;
+                q = si(q);
                 x.nc = Lc[q];
                 x.nd = Ld[q];
                 x.nu = Lu[q];
@@ -262,13 +304,14 @@ __global__ void __launch_bounds__(L7_THREADS, 2) line7_kernel(Line2Args args)
         }
         // the face before the piece: cells q = p0 - 1 (wrapping) and p0
         if (t == 0) {
-            const size_t q = p0 > 0 ? p0 - 1 : (size_t)n - 1, q1 = p0;
+            const size_t q = p0 > 0 ? p0 - 1 : (size_t)n - 1;
             R g1[1], e1[1];
             g1[0] = (R)Gl[q];
             e1[0] = (R)El[q];
-            const R c0 = Lc[q], d0 = Ld[q], u0 = Lu[q], c1 = Lc[q1], d1 = Ld[q1], u1 = Lu[q1];
-            const R c0l = K ? Lcl[q] : R(0), d0l = K ? Ldl[q] : R(0), u0l = K ? Lul[q] : R(0);
-            const R c1l = K ? Lcl[q1] : R(0), d1l = K ? Ldl[q1] : R(0), u1l = K ? Lul[q1] : R(0);
+            const size_t a0 = si(q), a1 = si(p0);
+            const R c0 = Lc[a0], d0 = Ld[a0], u0 = Lu[a0], c1 = Lc[a1], d1 = Ld[a1], u1 = Lu[a1];
+            const R c0l = K ? Lcl[a0] : R(0), d0l = K ? Ldl[a0] : R(0), u0l = K ? Lul[a0] : R(0);
+            const R c1l = K ? Lcl[a1] : R(0), d1l = K ? Ldl[a1] : R(0), u1l = K ? Lul[a1] : R(0);
             const R va = level<R, VL>(lim, dif7<K>(u0, u0l, c0, c0l), dif7<K>(c0, c0l, d0, d0l));
             const R vb = level<R, VL>(lim, dif7<K>(u1, u1l, c1, c1l), dif7<K>(c1, c1l, d1, d1l));
             const R lgq = __fmul_rn(lam, g1[0]);
@@ -347,13 +390,13 @@ __global__ void __launch_bounds__(L7_THREADS, 2) line7_kernel(Line2Args args)
     }
 
     // Phase C's first two chunks of T_old start loading now.
-    const VT *vcC = reinterpret_cast<const VT *>(Lc + p0);
-    const VT *vcCl = K ? reinterpret_cast<const VT *>(Lcl + p0) : nullptr;
-    VT pre0 = vcC[t], pre1 = V >= 2 ? vcC[t + P] : pre0;
+    const VT *vcC = reinterpret_cast<const VT *>(Lc);
+    const VT *vcCl = K ? reinterpret_cast<const VT *>(Lcl) : nullptr;
+    VT pre0 = vcC[vi(q0 + t)], pre1 = V >= 2 ? vcC[vi(q0 + t + P)] : pre0;
     VT pre0l = make_float4(0.f, 0.f, 0.f, 0.f), pre1l = pre0l;
     if (K) {
-        pre0l = vcCl[t];
-        pre1l = V >= 2 ? vcCl[t + P] : pre0l;
+        pre0l = vcCl[vi(q0 + t)];
+        pre1l = V >= 2 ? vcCl[vi(q0 + t + P)] : pre0l;
     }
 
     // ---- R1: the warp's unknowns through the interface unknowns around it
@@ -428,7 +471,13 @@ __global__ void __launch_bounds__(L7_THREADS, 2) line7_kernel(Line2Args args)
         const unsigned base = cl_map(&s_pub[lb][g % WPL][0], (unsigned)(g / WPL));
         float v[L7_PUB];
 #pragma unroll
-        for (int k = 0; k < L7_PUB; ++k) v[k] = cl_ld(base + 4u * k);
+        for (int k = 0; k < L7_PUB; k += 4) {
+            const float4 w = cl_ld4(base + 4u * k);
+            v[k] = w.x;
+            v[k + 1] = w.y;
+            v[k + 2] = w.z;
+            v[k + 3] = w.w;
+        }
         // the next warp's top map and its lane 0 in terms of (b_g, b_{g+1})
         const int gn = (g + 1) & (G - 1);
         const R rho_n = __shfl_sync(full, v[0], gn, G), alp_n = __shfl_sync(full, v[1], gn, G),
@@ -445,7 +494,7 @@ __global__ void __launch_bounds__(L7_THREADS, 2) line7_kernel(Line2Args args)
         const R b = pcr_team<R>(s, g, G);
         if (lane < G) s_b[lb][lane] = b;
     }
-    if (!K) cl_arrive();  // this block reads no other block's memory after this
+    if (!K) cl_arrive_relaxed();  // this block reads no other block's memory after this
     __syncthreads();
 
     // ---- X_t and X_{t-1}
@@ -481,27 +530,43 @@ __global__ void __launch_bounds__(L7_THREADS, 2) line7_kernel(Line2Args args)
     // K: the line's compensated sum of delta, the same in every block
     R ch = R(0), clo = R(0);
     if (K) {
-        double part = (double)acc.s + (double)acc.c;
+        // double-word FP32 throughout: lanes by a butterfly (both orders of
+        // an exact two-sum give the same pair), warps and blocks in order
+        float sh, sl;
+        two_sum(acc.s, acc.c, sh, sl);
 #pragma unroll
-        for (int o = 16; o >= 1; o >>= 1) part += __shfl_xor_sync(full, part, o);
-        if (lane == 0) s_wpart[lb][wl] = part;
+        for (int o = 16; o >= 1; o >>= 1) {
+            const float oh = __shfl_xor_sync(full, sh, o), ol = __shfl_xor_sync(full, sl, o);
+            dw_add(sh, sl, oh, ol, sh, sl);
+        }
+        if (lane == 0) {
+            s_wpart[lb][wl][0] = sh;
+            s_wpart[lb][wl][1] = sl;
+        }
         __syncthreads();
         if (threadIdx.x < LPB) {
-            double a = 0.0;
+            float ah = s_wpart[threadIdx.x][0][0], al = s_wpart[threadIdx.x][0][1];
 #pragma unroll
-            for (int w = 0; w < WPL; ++w) a += s_wpart[threadIdx.x][w];
-            s_lpart[threadIdx.x] = a;
+            for (int w = 1; w < WPL; ++w) dw_add(ah, al, s_wpart[threadIdx.x][w][0], s_wpart[threadIdx.x][w][1], ah, al);
+            s_lpart[threadIdx.x][0] = ah;
+            s_lpart[threadIdx.x][1] = al;
         }
         cl_arrive();
         cl_wait();
         if (threadIdx.x < LPB) {
-            double a = 0.0;
-            for (int k = 0; k < CS; ++k) a += cl_ld_f64(cl_map(&s_lpart[threadIdx.x], (unsigned)k));
-            s_lsum[threadIdx.x] = a;
+            float ah = R(0), al = R(0);
+            for (int k = 0; k < CS; ++k) {
+                const float2 b2 = cl_ld2(cl_map(&s_lpart[threadIdx.x][0], (unsigned)k));
+                dw_add(ah, al, b2.x, b2.y, ah, al);
+            }
+            const float inv = 1.0f / (float)n;  // n is a power of two: exact, and so are the products
+            s_corr[threadIdx.x][0] = ah * inv;
+            s_corr[threadIdx.x][1] = al * inv;
         }
-        cl_arrive();
+        cl_arrive_relaxed();
         __syncthreads();
-        split_f64(s_lsum[lb] / (double)n, ch, clo);
+        ch = s_corr[lb][0];
+        clo = s_corr[lb][1];
     } else {
         __syncthreads();
     }
@@ -516,8 +581,8 @@ __global__ void __launch_bounds__(L7_THREADS, 2) line7_kernel(Line2Args args)
         pre0 = pre1;
         if (K) pre0l = pre1l;
         if (v + 2 < V) {
-            pre1 = vcC[c + 2 * P];
-            if (K) pre1l = vcCl[c + 2 * P];
+            pre1 = vcC[vi(q0 + c + 2 * P)];
+            if (K) pre1l = vcCl[vi(q0 + c + 2 * P)];
         }
         V16<R>::unpack(sA[swz(c)], d);
         R hi[N], lo[N];
@@ -534,7 +599,11 @@ __global__ void __launch_bounds__(L7_THREADS, 2) line7_kernel(Line2Args args)
         }
         bad |= !(fabsf(sum) < INFINITY);
         if (!J.transpose_out) {
-            if (active) {
+            if (active && ilv_out) {
+                VT *o = reinterpret_cast<VT *>(static_cast<R *>(J.Tout) + (size_t)lc * 2 * n) + 2 * (q0 + c);
+                o[0] = V16<R>::pack(hi);
+                o[1] = V16<R>::pack(lo);
+            } else if (active) {
                 reinterpret_cast<VT *>(static_cast<R *>(J.Tout) + (size_t)lc * n + p0)[c] = V16<R>::pack(hi);
                 if (K) reinterpret_cast<VT *>(static_cast<R *>(J.ToutLo) + (size_t)lc * n + p0)[c] = V16<R>::pack(lo);
             }
@@ -544,8 +613,23 @@ __global__ void __launch_bounds__(L7_THREADS, 2) line7_kernel(Line2Args args)
         }
     }
 
-    // ---- transposed store: out[p][line], the block's four lines in 16-byte pieces
-    if (J.transpose_out) {
+    // ---- transposed store: out[p][line], the block's four lines in 16-byte
+    // pieces; interleaved, each position's hi and lo pieces fill one 32-byte
+    // sector (two neighbouring threads)
+    if (J.transpose_out && ilv_out) {
+        __syncthreads();
+        R *out = static_cast<R *>(J.Tout);
+        for (int idx = threadIdx.x; idx < 2 * np; idx += blockDim.x) {
+            const int p = idx >> 1, half = idx & 1;
+            const int sc = swz(p >> 2), j = p & 3;
+            R o[N];
+#pragma unroll
+            for (int i = 0; i < N; ++i)
+                o[i] = reinterpret_cast<const R *>(reinterpret_cast<const VT *>(smem_raw) + (size_t)i * 3 * m +
+                                                   (size_t)half * m + sc)[j];
+            *reinterpret_cast<VT *>(out + (size_t)(p0 + p) * 2 * nl + 2 * (size_t)line0 + N * half) = V16<R>::pack(o);
+        }
+    } else if (J.transpose_out) {
         __syncthreads();
         R *out = static_cast<R *>(J.Tout);
         R *outl = static_cast<R *>(J.ToutLo);
