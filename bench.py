@@ -106,9 +106,9 @@ def measured_peak():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    # the files that define the profiled kernels (line4 2-D and 3-D, line6) and their job structs
-    for f in ("sweep_kernels.cuh", "line2_kernel.cuh", "line4_kernel.cuh", "line6_kernel.cuh",
-              "aniso_internal.h", "kernels_line4.cu", "kernels_line6.cu", "kernels_3d.cu"):
+    # the files that define the profiled kernels (line4 2-D and 3-D, line7) and their job structs
+    for f in ("sweep_kernels.cuh", "line2_kernel.cuh", "line4_kernel.cuh", "line7_kernel.cuh",
+              "aniso_internal.h", "kernels_line4.cu", "kernels_line7.cu", "kernels_3d.cu"):
         h.update(open(os.path.join(ROOT, "paper_1008_0861_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -948,7 +948,8 @@ def make_single(rank=0):
 def main_single(args):
     """bench.py --workload random4096: one JSON line for the 4096^2 grid (one
     bench step = one aniso_step call of 100 steps; both updates run the
-    long-line kernel, whose launches are timed with CUDA events)."""
+    cluster kernel (2-block clusters), whose launches are timed with CUDA
+    events)."""
     import torch
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
@@ -1017,9 +1018,9 @@ def main_single(args):
                    "l2": "inputs larger than L2: %.2f GB resident (T, T*, 4 coefficient arrays, 2 transposed)"
                          % (inst.cells * 4 * 8 / 1e9),
                    "parallelism": "one independent grid per GPU (no collective)"},
-        "roofline": {"bound": "hbm", "kernel": "line6_" + names[dom], "achieved": achieved, "peak": peak,
+        "roofline": {"bound": "hbm", "kernel": "line7_" + names[dom], "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "peak_source": note,
-                     "traffic": ncu_traffic("line6_4096"),
+                     "traffic": ncu_traffic("line7_4096"),
                      "algorithmic_bytes_per_launch": BYTES_PER_CELL_SWEEP * inst.cells, "avg_launch_ms": launch_ms},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": inst.cells * 4,
                 "d2h_bytes_per_step": inst.cells * 4},

@@ -102,20 +102,22 @@ enum {
                                   ANISO_ERR_TIMEOUT at the next aniso_sync / aniso_total of the
                                   first handle.  Taken from the batch's first handle.  Y-updates
                                   recorded by ANISO_OPT_DIAGNOSTICS use the warp-per-line kernel. */
-    ANISO_OPT_TMEM = 14,       /* batched calls, FP32, four-warp blocks: 1 (default) keeps part of the
-                                  warp-per-line kernel's line state in the SM's tensor memory (TMEM)
-                                  instead of shared memory when every line of a sweep fits (at most
-                                  15 chunks of 4 cells a lane), so more blocks fit an SM; 0 keeps
-                                  it all in shared memory.  Results are the same bit for bit.
-                                  Taken from the batch's first handle. */
-    ANISO_OPT_CLUSTER_LINES = 15 /* FP32 fast path: 1 (default) solves lines of 8192 and 16384 cells,
-                                  and the lines of a compensated-state grid (ANISO_OPT_KAHAN) of
-                                  1024, 2048, 4096, 8192 or 16384 cells in both directions, on the
-                                  cluster kernel: each line is cut into pieces of 2048 (or 1024)
-                                  cells held by the blocks of one thread-block cluster, so these
-                                  grids need no transpose pass; 2 also takes lines of 2049-4096
-                                  cells from the long-line kernel; 0 leaves them to the general
-                                  kernels. */
+    ANISO_OPT_TMEM = 14,       /* FP32: 1 (default) keeps part of the line state in the SM's tensor
+                                  memory (TMEM) instead of shared memory, so more blocks fit an SM:
+                                  in batched calls the warp-per-line kernel's (four-warp blocks,
+                                  when every line of a sweep fits: at most 15 chunks of 4 cells a
+                                  lane; taken from the batch's first handle), and the cluster
+                                  kernel's for the plain state.  0 keeps it all in shared memory.
+                                  Results are the same bit for bit. */
+    ANISO_OPT_CLUSTER_LINES = 15 /* FP32 fast path, lines cut across the blocks of one thread-block
+                                  cluster (pieces of 2048 or 1024 cells), so that lines too long for
+                                  one block need no transpose pass.  2 (default): lines of 4096,
+                                  8192 and 16384 cells, and both directions of a compensated-state grid
+                                  (ANISO_OPT_KAHAN) whose sides are 1024, 2048, 4096, 8192 or 16384
+                                  cells; 1: as 2, but lines of 2049-4096 cells stay on the
+                                  long-line kernel; 0: none (the general kernels).  With
+                                  ANISO_OPT_TMEM the plain state keeps part of its line state in
+                                  tensor memory. */
 };
 enum { ANISO_PREC_FP64 = 0, ANISO_PREC_FP32 = 1 };
 enum {

@@ -92,7 +92,7 @@ struct aniso_ctx {
     int use_graph = 1, profile = 0, fast = 3, seg_chunks = 0, l4_warps = 0, scheme = 0, diag = 0;
     int tma_lines = 0;  // ANISO_OPT_TMA_LINES
     int tmem = 1;       // ANISO_OPT_TMEM
-    int cluster = 1;    // ANISO_OPT_CLUSTER_LINES
+    int cluster = 2;    // ANISO_OPT_CLUSTER_LINES
     double nl_alpha = 0, nl_tref = 1;  // temperature-dependent diffusivity (aniso_set_nonlinear)
     void *t4 = nullptr;  // intermediate of the 4-step scheme
     void *q = nullptr;   // source term (aniso_set_source), handle precision
@@ -403,10 +403,14 @@ static int enqueue_line2(aniso_ctx *h, const void *in, void *out, const void *g,
     const bool v6 = lk == 6 && line6_config(h->prec, h->field_fp16, n, &J.team, &J.lines_per_block, &nthreads,
                                             &smem, h->l4_warps == 8 ? 2 : 4);
     int cs = 0;
-    const bool v7 = lk == 7 && line7_config(h->prec, h->field_fp16, n, &cs, &nthreads, &smem);
+    // (tensor memory for the plain state only: the compensated kernel would
+    // spill at three blocks an SM, and measured no faster)
+    const bool tm7 = h->tmem != 0 && !in_lo;
+    const bool v7 = lk == 7 && line7_config(h->prec, h->field_fp16, n, &cs, &nthreads, &smem, tm7);
     if (v7) {
         J.team = 64;
         J.lines_per_block = 4;
+        a.tmem = tm7 ? 1 : 0;
     }
     ok = ok || v6 || v7;
     if (!ok) return fail(ANISO_ERR_UNSUPPORTED, "vectorised line kernel cannot take n=%d", n);

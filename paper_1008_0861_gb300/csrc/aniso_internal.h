@@ -177,9 +177,10 @@ bool line6_config(int prec, int coef_fp16, int n, int *team, int *lines_per_bloc
 cudaError_t launch_line6(int coef_fp16, const Line2Args &a, int nblocks, int nthreads, size_t smem, cudaStream_t s);
 // Lines cut across a thread-block cluster (line7): FP32, n = cs * np with
 // np = 2048 (else 1024) and cs = 1, 2, 4 or 8; four lines a block, one job
-// (args.one) a launch; with TinLo/ToutLo set, the compensated state.  False
-// when the line does not fit.
-bool line7_config(int prec, int coef_fp16, int n, int *cs, int *nthreads, size_t *smem);
+// (args.one) a launch; with TinLo/ToutLo set, the compensated state; with
+// args.tmem (and tmem here, for the shared-memory size) each lane's gamma in
+// tensor memory.  False when the line does not fit.
+bool line7_config(int prec, int coef_fp16, int n, int *cs, int *nthreads, size_t *smem, bool tmem = false);
 cudaError_t launch_line7(int coef_fp16, const Line2Args &a, int cs, size_t smem, cudaStream_t s);
 // Resident blocks per SM of the 2-D line4 kernel for that block size and
 // dynamic shared memory (CUDA's occupancy calculator), or -1.

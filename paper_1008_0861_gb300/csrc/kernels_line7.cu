@@ -1,13 +1,13 @@
 // Instantiations and launch configuration of the cluster line kernel
-// (line7_kernel.cuh): FP32 state, plain or compensated, FP32 or FP16 face
-// coefficients.
+// (line7_kernel.cuh): FP32 state, plain (gamma in shared or tensor memory) or
+// compensated (shared memory), FP32 or FP16 face coefficients.
 #include "line7_kernel.cuh"
 
 namespace aniso {
 
 // n = CS * np with np = 2048 (or 1024 when n is not a multiple of 2048) and
 // CS = 1, 2, 4 or 8 blocks a cluster; four lines a block.
-bool line7_config(int prec, int coef_fp16, int n, int *cs, int *nthreads, size_t *smem)
+bool line7_config(int prec, int coef_fp16, int n, int *cs, int *nthreads, size_t *smem, bool tmem)
 {
     if (prec != PREC_FP32 || n <= 0) return false;
     (void)coef_fp16;
@@ -18,7 +18,7 @@ bool line7_config(int prec, int coef_fp16, int n, int *cs, int *nthreads, size_t
     if (c != 1 && c != 2 && c != 4 && c != 8) return false;
     *cs = c;
     *nthreads = L7_THREADS;
-    *smem = (size_t)L7_LPB * 3 * (size_t)(np / 4) * 16;
+    *smem = (size_t)L7_LPB * (tmem ? 2 : 3) * (size_t)(np / 4) * 16;
     return true;
 }
 
@@ -47,14 +47,15 @@ static cudaError_t run7(Kern kern, const Line2Args &a, int cs, size_t smem, cuda
     return cudaLaunchKernelEx(&cfg, kern, a);
 }
 
-template <bool K> static cudaError_t launch7k(int coef_fp16, const Line2Args &a, int cs, size_t smem, cudaStream_t s)
+template <bool K, bool TM>
+static cudaError_t launch7k(int coef_fp16, const Line2Args &a, int cs, size_t smem, cudaStream_t s)
 {
     const bool vl = a.limiter == LIM_VANLEER;
     if (coef_fp16)
-        return vl ? run7(line7_kernel<__half, true, K>, a, cs, smem, s)
-                  : run7(line7_kernel<__half, false, K>, a, cs, smem, s);
-    return vl ? run7(line7_kernel<float, true, K>, a, cs, smem, s)
-              : run7(line7_kernel<float, false, K>, a, cs, smem, s);
+        return vl ? run7(line7_kernel<__half, true, K, TM>, a, cs, smem, s)
+                  : run7(line7_kernel<__half, false, K, TM>, a, cs, smem, s);
+    return vl ? run7(line7_kernel<float, true, K, TM>, a, cs, smem, s)
+              : run7(line7_kernel<float, false, K, TM>, a, cs, smem, s);
 }
 
 cudaError_t launch_line7(int coef_fp16, const Line2Args &a, int cs, size_t smem, cudaStream_t s)
@@ -62,7 +63,8 @@ cudaError_t launch_line7(int coef_fp16, const Line2Args &a, int cs, size_t smem,
     if (a.jobs || a.one.n % cs != 0) return cudaErrorInvalidValue;
     const bool k = a.one.TinLo != nullptr;
     if (k && (!a.one.ToutLo)) return cudaErrorInvalidValue;
-    return k ? launch7k<true>(coef_fp16, a, cs, smem, s) : launch7k<false>(coef_fp16, a, cs, smem, s);
+    if (k) return a.tmem ? cudaErrorInvalidValue : launch7k<true, false>(coef_fp16, a, cs, smem, s);
+    return a.tmem ? launch7k<false, true>(coef_fp16, a, cs, smem, s) : launch7k<false, false>(coef_fp16, a, cs, smem, s);
 }
 
 }  // namespace aniso

@@ -127,8 +127,11 @@ constexpr int L7_LPB = 4;    // lines a block holds
 constexpr int L7_THREADS = L7_P * L7_LPB;
 constexpr int L7_PUB = 16;   // numbers a warp publishes for the interface system
 
-template <typename C, bool VL, bool K>
-__global__ void __launch_bounds__(L7_THREADS, 2) line7_kernel(Line2Args args)
+// TM: each lane's gamma goes to its own tensor-memory lane (32 columns a
+// warp, 64 a block) instead of shared memory, so a block holds two arrays of
+// its lines' state in shared memory and three blocks fit an SM.
+template <typename C, bool VL, bool K, bool TM>
+__global__ void __launch_bounds__(L7_THREADS, TM ? 3 : 2) line7_kernel(Line2Args args)
 {
     typedef float R;
     typedef float4 VT;
@@ -179,9 +182,18 @@ __global__ void __launch_bounds__(L7_THREADS, 2) line7_kernel(Line2Args args)
     const int c_lo = t * U;
     const int V = U;      // chunk rounds of the coalesced phases
     const int mfull = m & ~7, logU = 31 - __clz(U);
-    VT *sA = reinterpret_cast<VT *>(smem_raw) + (size_t)lb * 3 * m;  // F -> rho -> delta -> T_new (hi)
-    VT *sB = sA + m;                                                  // lam*g -> alpha -> (K) T_new lo
-    VT *sC = sA + 2 * m;                                              // gamma
+    constexpr int NARR = TM ? 2 : 3;                                     // shared arrays a line
+    VT *sA = reinterpret_cast<VT *>(smem_raw) + (size_t)lb * NARR * m;  // F -> rho -> delta -> T_new (hi)
+    VT *sB = sA + m;                                                     // lam*g -> alpha -> (K) T_new lo
+    VT *sC = sA + 2 * m;                                                 // gamma (shared-memory form)
+    // TMEM form: warp 0 allocates the block's columns now; the address is read
+    // after the barrier that ends phase A.  Warp w: lanes 32 (w % 4) .. + 31,
+    // columns 32 (w / 4) .. + 31 (chunk u of the lane's segment at 4 u).
+    __shared__ unsigned s_tmem;
+    if (TM) {
+        if (warp == 0) tm_alloc(&s_tmem);
+        tm_fence_before();
+    }
     auto swz = [mfull, logU](int c) { return c < mfull ? c ^ ((c >> logU) & 7) : c; };
 
     // The block's rows of this piece into L2 (a hint): input lines line0 - 1
@@ -320,6 +332,11 @@ __global__ void __launch_bounds__(L7_THREADS, 2) line7_kernel(Line2Args args)
         }
     }
     __syncthreads();
+    unsigned tm_lane = 0;
+    if (TM) {
+        tm_fence_after();
+        tm_lane = s_tmem + ((unsigned)(32 * (warp & 3)) << 16) + 32u * (unsigned)(warp >> 2);
+    }
 
     // ---- B1: bottom-up elimination of lane t's segment (as line6)
     R rho1 = R(0), alp1 = R(0), gam1 = R(-1);
@@ -363,7 +380,8 @@ __global__ void __launch_bounds__(L7_THREADS, 2) line7_kernel(Line2Args args)
                 elim(Fpend, F[N - 1], lgpend, lg[N - 1], ro[0], ao[0], go[0]);
                 sA[swz(c + 1)] = V16<R>::pack(ro);
                 sB[swz(c + 1)] = V16<R>::pack(ao);
-                sC[swz(c + 1)] = V16<R>::pack(go);
+                if (TM) tm_st4(tm_lane + 4u * (unsigned)(u + 1), go[0], go[1], go[2], go[3]);  // warp-wide
+                else sC[swz(c + 1)] = V16<R>::pack(go);
 #pragma unroll
                 for (int j = N - 1; j >= 1; --j) elim(F[j], F[j - 1], lg[j], lg[j - 1], co[j], cao[j], cgo[j]);
             }
@@ -386,7 +404,12 @@ __global__ void __launch_bounds__(L7_THREADS, 2) line7_kernel(Line2Args args)
         elim(Fpend, Fb, lgpend, lgb, ro[0], ao[0], go[0]);
         sA[swz(c_lo)] = V16<R>::pack(ro);
         sB[swz(c_lo)] = V16<R>::pack(ao);
-        sC[swz(c_lo)] = V16<R>::pack(go);
+        if (TM) {
+            tm_st4(tm_lane, go[0], go[1], go[2], go[3]);
+            tm_wait_st();  // the recovery reads these columns back
+        } else {
+            sC[swz(c_lo)] = V16<R>::pack(go);
+        }
     }
 
     // Phase C's first two chunks of T_old start loading now.
@@ -516,7 +539,8 @@ __global__ void __launch_bounds__(L7_THREADS, 2) line7_kernel(Line2Args args)
             R r4[N], a4[N], g4[N], d[N];
             V16<R>::unpack(sA[swz(c)], r4);
             V16<R>::unpack(sB[swz(c)], a4);
-            V16<R>::unpack(sC[swz(c)], g4);
+            if (TM) tm_ld4(tm_lane + 4u * (unsigned)u, g4);  // warp-wide
+            else V16<R>::unpack(sC[swz(c)], g4);
 #pragma unroll
             for (int j = 0; j < N; ++j) {
                 d[j] = (u == U - 1 && j == N - 1) ? X : r4[j] - a4[j] * dprev - g4[j] * X;
@@ -625,7 +649,7 @@ __global__ void __launch_bounds__(L7_THREADS, 2) line7_kernel(Line2Args args)
             R o[N];
 #pragma unroll
             for (int i = 0; i < N; ++i)
-                o[i] = reinterpret_cast<const R *>(reinterpret_cast<const VT *>(smem_raw) + (size_t)i * 3 * m +
+                o[i] = reinterpret_cast<const R *>(reinterpret_cast<const VT *>(smem_raw) + (size_t)i * NARR * m +
                                                    (size_t)half * m + sc)[j];
             *reinterpret_cast<VT *>(out + (size_t)(p0 + p) * 2 * nl + 2 * (size_t)line0 + N * half) = V16<R>::pack(o);
         }
@@ -639,7 +663,7 @@ __global__ void __launch_bounds__(L7_THREADS, 2) line7_kernel(Line2Args args)
             R o[N], ol[N];
 #pragma unroll
             for (int i = 0; i < N; ++i) {
-                const VT *base = reinterpret_cast<const VT *>(smem_raw) + (size_t)i * 3 * m;
+                const VT *base = reinterpret_cast<const VT *>(smem_raw) + (size_t)i * NARR * m;
                 o[i] = reinterpret_cast<const R *>(base + sc)[j];
                 if (K) ol[i] = reinterpret_cast<const R *>(base + m + sc)[j];
             }
@@ -658,6 +682,14 @@ __global__ void __launch_bounds__(L7_THREADS, 2) line7_kernel(Line2Args args)
         }
     }
     if (bad && active) atomicOr(args.err, 1u);
+    if (TM) {  // every warp is done with TMEM before the block frees it
+        tm_fence_before();
+        __syncthreads();
+        if (warp == 0) {
+            tm_fence_after();
+            tm_dealloc(s_tmem);
+        }
+    }
     cl_wait();  // no block leaves while another may still read its shared memory
 }
 
