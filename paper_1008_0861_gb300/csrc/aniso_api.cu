@@ -1196,61 +1196,76 @@ static int batch_build(aniso_batch *b, void *const *T, const double *dt, const i
             if (line4_config(prec, J.n, true, warps, seg, &J.team, &J.lines_per_block, &nt, &sm))
                 nthreads = std::max(nthreads, nt);
         }
-        // the tensor-memory form when every line of the sweep fits it
-        bool tm = b->hs[0]->tmem != 0;
-        for (auto &J : jobs) {
-            int t0, t1, t2;
-            size_t t3;
-            tm = tm && line4_config(prec, J.n, true, nthreads / 32, seg, &t0, &t1, &t2, &t3, true);
-        }
-        std::vector<std::pair<int, size_t>> cls(jobs.size());  // (blocks per SM, own shared memory)
+        // Per job: its resident blocks per SM in the shared-memory form and, when
+        // the lines fit it, in the tensor-memory form (whose TMEM columns also
+        // cap the blocks an SM holds); the form with more blocks wins.
+        struct Cls {
+            int occ;
+            size_t sm;
+            bool tm;
+        };
+        const bool tm_on = b->hs[0]->tmem != 0 && prec == PREC_FP32;
+        std::vector<Cls> cls(jobs.size());
         for (size_t k = 0; k < jobs.size(); ++k) {
             Line2Job &J = jobs[k];
             int nt = 0;
             size_t sm = 0;
-            if (!line4_config(prec, J.n, true, nthreads / 32, seg, &J.team, &J.lines_per_block, &nt, &sm, tm) ||
+            if (!line4_config(prec, J.n, true, nthreads / 32, seg, &J.team, &J.lines_per_block, &nt, &sm) ||
                 nt != nthreads)
                 shape_rc = fail(ANISO_ERR_UNSUPPORTED, "batch: line length %d does not fit the block shape", J.n);
-            const int occ = line4_blocks_per_sm(prec, fp16, b->hs[0]->limiter, nthreads, sm, tm);
-            cls[k] = {occ > 0 ? occ : 0, sm};
-        }
-        // classes in ascending occupancy (largest lines first); at most
-        // five of them, the highest-occupancy ones merged
-        std::vector<int> occs;
-        for (auto &c : cls) occs.push_back(c.first);
-        std::sort(occs.begin(), occs.end());
-        occs.erase(std::unique(occs.begin(), occs.end()), occs.end());
-        while ((int)occs.size() > 5) occs.erase(occs.end() - 2);
-        for (size_t ci = 0; ci < occs.size(); ++ci) {
-            const int lo = occs[ci], hi = ci + 1 < occs.size() ? occs[ci + 1] : 1 << 30;
-            std::vector<Line2Job> part;
-            size_t smem = 0;
-            int blocks = 0;
-            for (size_t k = 0; k < jobs.size(); ++k) {
-                if (cls[k].first < lo || cls[k].first >= hi) continue;
-                Line2Job J = jobs[k];
-                smem = std::max(smem, cls[k].second);
-                J.block0 = blocks;
-                J.nblocks = (J.nlines + J.lines_per_block - 1) / J.lines_per_block;
-                blocks += J.nblocks;
-                part.push_back(J);
+            int occ = line4_blocks_per_sm(prec, fp16, b->hs[0]->limiter, nthreads, sm, false);
+            cls[k] = {occ > 0 ? occ : 0, sm, false};
+            int t0, t1, t2;
+            size_t smt = 0;
+            if (tm_on && line4_config(prec, J.n, true, nthreads / 32, seg, &t0, &t1, &t2, &smt, true)) {
+                const int occt = line4_blocks_per_sm(prec, fp16, b->hs[0]->limiter, nthreads, smt, true,
+                                                     line4_tm_cols(J.n, J.team));
+                if (occt > cls[k].occ) cls[k] = {occt, smt, true};
             }
-            if (part.empty()) continue;
-            Launch L{kind_xy == 0 ? 7 : 8, blob.size(), (int)part.size(), blocks, nthreads, smem};
-            L.group = group;
-            L.tmem = tm ? 1 : 0;
-            if (kind_xy == 1 && diag) L.diag_region = (int)ci;
-            const unsigned char *p = reinterpret_cast<const unsigned char *>(part.data());
-            blob.insert(blob.end(), p, p + part.size() * sizeof(Line2Job));
-            while (blob.size() % 16) blob.push_back(0);
-            std::vector<int> table(blocks);
-            for (size_t k = 0; k < part.size(); ++k)
-                for (int bk = 0; bk < part[k].nblocks; ++bk) table[part[k].block0 + bk] = (int)k;
-            L.table = (long long)blob.size();
-            const unsigned char *tp = reinterpret_cast<const unsigned char *>(table.data());
-            blob.insert(blob.end(), tp, tp + table.size() * sizeof(int));
-            while (blob.size() % 16) blob.push_back(0);
-            launches.push_back(L);
+        }
+        // per form, classes in ascending occupancy (largest lines first); at
+        // most three a form, the highest-occupancy ones merged
+        int region = 0;
+        for (int form = 1; form >= 0; --form) {
+            std::vector<int> occs;
+            for (auto &c : cls)
+                if (c.tm == (form == 1)) occs.push_back(c.occ);
+            std::sort(occs.begin(), occs.end());
+            occs.erase(std::unique(occs.begin(), occs.end()), occs.end());
+            // (merging never drops the lowest class: its range reaches up to the next kept one)
+            while ((int)occs.size() > 3) occs.erase(occs.end() - (occs.size() >= 3 ? 2 : 1));
+            for (size_t ci = 0; ci < occs.size(); ++ci) {
+                const int lo = occs[ci], hi = ci + 1 < occs.size() ? occs[ci + 1] : 1 << 30;
+                std::vector<Line2Job> part;
+                size_t smem = 0;
+                int blocks = 0;
+                for (size_t k = 0; k < jobs.size(); ++k) {
+                    if (cls[k].tm != (form == 1) || cls[k].occ < lo || cls[k].occ >= hi) continue;
+                    Line2Job J = jobs[k];
+                    smem = std::max(smem, cls[k].sm);
+                    J.block0 = blocks;
+                    J.nblocks = (J.nlines + J.lines_per_block - 1) / J.lines_per_block;
+                    blocks += J.nblocks;
+                    part.push_back(J);
+                }
+                if (part.empty()) continue;
+                Launch L{kind_xy == 0 ? 7 : 8, blob.size(), (int)part.size(), blocks, nthreads, smem};
+                L.group = group;
+                L.tmem = form;
+                if (kind_xy == 1 && diag) L.diag_region = region;
+                ++region;
+                const unsigned char *p = reinterpret_cast<const unsigned char *>(part.data());
+                blob.insert(blob.end(), p, p + part.size() * sizeof(Line2Job));
+                while (blob.size() % 16) blob.push_back(0);
+                std::vector<int> table(blocks);
+                for (size_t k = 0; k < part.size(); ++k)
+                    for (int bk = 0; bk < part[k].nblocks; ++bk) table[part[k].block0 + bk] = (int)k;
+                L.table = (long long)blob.size();
+                const unsigned char *tp = reinterpret_cast<const unsigned char *>(table.data());
+                blob.insert(blob.end(), tp, tp + table.size() * sizeof(int));
+                while (blob.size() % 16) blob.push_back(0);
+                launches.push_back(L);
+            }
         }
     };
 

@@ -183,8 +183,12 @@ cudaError_t launch_line6(int coef_fp16, const Line2Args &a, int nblocks, int nth
 bool line7_config(int prec, int coef_fp16, int n, int *cs, int *nthreads, size_t *smem, bool tmem = false);
 cudaError_t launch_line7(int coef_fp16, const Line2Args &a, int cs, size_t smem, cudaStream_t s);
 // Resident blocks per SM of the 2-D line4 kernel for that block size and
-// dynamic shared memory (CUDA's occupancy calculator), or -1.
-int line4_blocks_per_sm(int prec, int coef_fp16, int limiter, int nthreads, size_t smem, bool tmem = false);
+// dynamic shared memory (CUDA's occupancy calculator; in the tensor-memory
+// form also capped by the block's TMEM columns, tm_cols), or -1.
+int line4_blocks_per_sm(int prec, int coef_fp16, int limiter, int nthreads, size_t smem, bool tmem = false,
+                        int tm_cols = 64);
+// TMEM columns a line4 block of lines of n cells (teams of `team` lanes) allocates.
+int line4_tm_cols(int n, int team);
 // Three-dimensional grids (kernels_3d.cu).  c[0..2] = x faces (normal, with
 // y, with z) in layout [nz][ny][nx]; c[3..5] = y faces (normal, with z, with
 // x) in [nx][nz][ny]; c[6..8] = z faces (normal, with x, with y) in

@@ -70,15 +70,25 @@ template <typename K> static int occ4(K kern, int nthreads, size_t smem)
     return blocks;
 }
 
-int line4_blocks_per_sm(int prec, int coef_fp16, int limiter, int nthreads, size_t smem, bool tmem)
+int line4_tm_cols(int n, int team)
+{
+    const int m = n / 4, U = m / team, V = U + (m % team ? 1 : 0);
+    return 4 * V + 4 <= 32 ? 32 : 64;
+}
+
+int line4_blocks_per_sm(int prec, int coef_fp16, int limiter, int nthreads, size_t smem, bool tmem, int tm_cols)
 {
     const bool vl = limiter == LIM_VANLEER;
     if (tmem && prec == PREC_FP32) {
-        if (coef_fp16)
-            return vl ? occ4(line4_kernel<float, __half, true, false, false, false, true>, nthreads, smem)
-                      : occ4(line4_kernel<float, __half, false, false, false, false, true>, nthreads, smem);
-        return vl ? occ4(line4_kernel<float, float, true, false, false, false, true>, nthreads, smem)
-                  : occ4(line4_kernel<float, float, false, false, false, false, true>, nthreads, smem);
+        // CUDA's occupancy calculator answers 1 for a kernel that allocates
+        // tensor memory, while 5-7 such blocks were measured resident.  The
+        // shared-memory form has the same registers and static shared memory:
+        // its answer at this dynamic size, capped by the TMEM columns (at
+        // most 448 of an SM's 512 were found in use at once: seven 64-column
+        // blocks where eight fit otherwise).
+        const int cap = 448 / (tm_cols > 0 ? tm_cols : 64);
+        const int occ = line4_blocks_per_sm(prec, coef_fp16, limiter, nthreads, smem, false);
+        return occ < cap ? occ : cap;
     }
     if (prec == PREC_FP64)
         return vl ? occ4(line4_kernel<double, double, true>, nthreads, smem)

@@ -147,17 +147,17 @@ template <typename R> __device__ __forceinline__ R face_harmonic(R a, R b)
 // moves four consecutive columns of the thread's own lane per instruction
 // (warp-wide, aligned).
 constexpr unsigned TM_COLS = 64;
-__device__ __forceinline__ void tm_alloc(unsigned *s_dst)
+__device__ __forceinline__ void tm_alloc(unsigned *s_dst, unsigned cols = TM_COLS)
 {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      (unsigned)__cvta_generic_to_shared(s_dst)),
-                 "r"(TM_COLS)
+                 "r"(cols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
 }
-__device__ __forceinline__ void tm_dealloc(unsigned base)
+__device__ __forceinline__ void tm_dealloc(unsigned base, unsigned cols = TM_COLS)
 {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(base), "r"(TM_COLS) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(base), "r"(cols) : "memory");
 }
 __device__ __forceinline__ void tm_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tm_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -267,11 +267,13 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? (D3 ? 3 : 4) : 2) line4_
     VT *sA = wbase + q * m;           // F -> rho -> delta -> T_new
     VT *sB = wbase + WA + q * m;      // lam*g -> alpha
     VT *sC = wbase + 2 * WA + q * m;  // gamma (shared-memory form only)
-    // TMEM form: the block's columns, this warp's lane quarter
+    // TMEM form: the block's columns (32 when a lane's 4 V + 4 fit, so that
+    // more blocks share an SM's 512), this warp's lane quarter
     __shared__ unsigned s_tmem;
     unsigned tm_base = 0;
+    const unsigned tm_cols = 4 * V + 4 <= 32 ? 32u : 64u;
     if constexpr (TM) {
-        if (warp == 0) tm_alloc(&s_tmem);
+        if (warp == 0) tm_alloc(&s_tmem, tm_cols);
         tm_fence_before();
         __syncthreads();
         tm_fence_after();
@@ -614,7 +616,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? (D3 ? 3 : 4) : 2) line4_
         __syncthreads();
         if (warp == 0) {
             tm_fence_after();
-            tm_dealloc(tm_base);
+            tm_dealloc(tm_base, tm_cols);
         }
     }
 }
