@@ -559,16 +559,22 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? (D3 ? 3 : 4) : 2) line4_
         }
     }
 
-    // ---- transposed store: out[p][line], N lines per 16-byte store; a
-    // thread writes all of the block's line groups of one position in turn
+    // ---- transposed store: out[p][line], N lines per 16-byte store.  With
+    // two or more line groups a block (short lines), lanes l and l + 16 of a
+    // warp write neighbouring groups of one position, so that each store
+    // instruction fills whole 32-byte sectors (16 positions x 2 groups).
     if (J.transpose_out) {
         __syncthreads();
         R *out = static_cast<R *>(J.Tout);
-        const int groups = LPB >> LOGN;
+        const int groups = LPB >> LOGN, logG = __ffs(groups) - 1;
         const bool vec_ok = (nl & (N - 1)) == 0;
-        for (int p = threadIdx.x; p < n; p += blockDim.x) {
+        const int pairs = groups == 1 ? n : (((n + 15) & ~15) << logG);
+        for (int idx = threadIdx.x; idx < pairs; idx += blockDim.x) {
+            const int p = groups == 1 ? idx : (((idx >> (4 + logG)) << 4) | (idx & 15));
+            const int grp = groups == 1 ? 0 : ((idx >> 4) & (groups - 1));
+            if (p >= n) continue;
             const int sc = swz(p >> LOGN), j = p & (N - 1);
-            for (int grp = 0; grp < groups; ++grp) {
+            {
                 R o[N];
 #pragma unroll
                 for (int i = 0; i < N; ++i) {
