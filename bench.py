@@ -62,10 +62,17 @@ def parse():
                     help="16-byte chunks per thread segment (0: library default)")
     ap.add_argument("--fast", type=int, default=-1,
                     help="ANISO_OPT_FAST_PATH value (-1: library default)")
-    ap.add_argument("--workload", default="batch", choices=["batch", "random3d", "random4096"],
+    ap.add_argument("--workload", default="batch", choices=["batch", "random3d", "random4096", "compensated"],
                     help="batch: the 512-grid 2-D benchmark (default); random3d: one 256^3 "
                          "grid of the three-dimensional split; random4096: one 4096^2 FP32 grid "
-                         "(100 steps per call, lines above 2048 cells)")
+                         "(100 steps per call, lines above 2048 cells); compensated: one grid "
+                         "(--shape, default 16384x16384) with the FP32 hi+lo state and FP16 "
+                         "face coefficients, 50 steps per call")
+    ap.add_argument("--cluster-lines", type=int, default=-1,
+                    help="ANISO_OPT_CLUSTER_LINES for the random4096 workload (-1: library default; 1 "
+                         "puts its 4096-cell lines on the long-line kernel)")
+    ap.add_argument("--shape", default="16384x16384",
+                    help="NXxNY of the compensated workload (sides of 1024 * 2^k cells, up to 16384)")
     return ap.parse_args()
 
 
@@ -961,6 +968,8 @@ def main_single(args):
     inst = make_single(rank)
     h = P.aniso_create(inst.nx, inst.ny, inst.dx, inst.dy, inst.chi_par, 0.0, inst.bc)
     P.aniso_set_option(h, P.ANISO_OPT_PRECISION, P.ANISO_PREC_FP32)
+    if args.cluster_lines >= 0:
+        P.aniso_set_option(h, P.ANISO_OPT_CLUSTER_LINES, args.cluster_lines)
     bx = torch.tensor(inst.bx, dtype=torch.float32, device="cuda")
     by = torch.tensor(inst.by, dtype=torch.float32, device="cuda")
     P.aniso_set_field(h, bx, by)
@@ -1018,9 +1027,10 @@ def main_single(args):
                    "l2": "inputs larger than L2: %.2f GB resident (T, T*, 4 coefficient arrays, 2 transposed)"
                          % (inst.cells * 4 * 8 / 1e9),
                    "parallelism": "one independent grid per GPU (no collective)"},
-        "roofline": {"bound": "hbm", "kernel": "line7_" + names[dom], "achieved": achieved, "peak": peak,
-                     "unit": "GB/s", "frac": achieved / peak, "peak_source": note,
-                     "traffic": ncu_traffic("line7_4096"),
+        "roofline": {"bound": "hbm", "kernel": ("line6_" if args.cluster_lines == 1 else "line7_") + names[dom],
+                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "peak_source": note,
+                     "traffic": ncu_traffic("line6_4096" if args.cluster_lines == 1 else "line7_4096"),
                      "algorithmic_bytes_per_launch": BYTES_PER_CELL_SWEEP * inst.cells, "avg_launch_ms": launch_ms},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": inst.cells * 4,
                 "d2h_bytes_per_step": inst.cells * 4},
@@ -1033,6 +1043,166 @@ def main_single(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+    return 0
+
+
+WC_STEPS = 50
+WC_BYTES_PER_CELL_SWEEP = 20  # read hi + lo (8) + two FP16 face coefficients (4) + write hi + lo (8)
+
+
+def compensated_shape(args):
+    nx, ny = (int(v) for v in args.shape.lower().split("x"))
+    return nx, ny
+
+
+def make_compensated(nx, ny, rank=0):
+    import workloads as W
+    return W.random_instance(nx, ny, seed=W.BASE_SEED + rank, kmax=32, chi_par=1.0, dt_factor=1000.0,
+                             nsteps=WC_STEPS)
+
+
+def workload_compensated(nx, ny):
+    return ("one periodic %dx%d random-field grid (|k| <= 32, 16 Gaussians), chi_par 1, dt = 1000 x the "
+            "explicit limit, FP32 hi+lo (compensated) state, FP16 face coefficients, %d steps per call "
+            "through aniso_step" % (nx, ny, WC_STEPS))
+
+
+def main_compensated(args):
+    """bench.py --workload compensated: one JSON line for one compensated-state
+    grid (the 16384^2 configuration by default).  One bench step = one
+    aniso_step call of 50 steps; both updates run the cluster kernel, whose
+    launches are timed with CUDA events."""
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_1008_0861_gb300 as P
+    P.load()
+    nx, ny = compensated_shape(args)
+    inst = make_compensated(nx, ny, rank)
+    h = P.aniso_create(inst.nx, inst.ny, inst.dx, inst.dy, inst.chi_par, 0.0, inst.bc)
+    P.aniso_set_option(h, P.ANISO_OPT_PRECISION, P.ANISO_PREC_FP32)
+    P.aniso_set_option(h, P.ANISO_OPT_FIELD_FP16, 1)
+    P.aniso_set_option(h, P.ANISO_OPT_KAHAN, 1)
+    bx = torch.tensor(inst.bx, dtype=torch.float32, device="cuda")
+    by = torch.tensor(inst.by, dtype=torch.float32, device="cuda")
+    P.aniso_set_field(h, bx, by)
+    del bx, by
+    T = torch.tensor(inst.T0, dtype=torch.float32, device="cuda")
+    s0 = P.aniso_total(h, T)[0]
+    for _ in range(args.warmup):
+        P.aniso_step(h, T, inst.dt, inst.nsteps)
+    P.aniso_sync(h)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            P.aniso_step(h, T, inst.dt, inst.nsteps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms_call = e0.elapsed_time(e1) / args.steps
+    s1 = P.aniso_total(h, T)[0]
+    # per-launch durations: one more call with CUDA events around every launch
+    P.aniso_set_option(h, P.ANISO_OPT_PROFILE, 1)
+    P.aniso_step(h, T, inst.dt, inst.nsteps)
+    P.aniso_sync(h)
+    P.aniso_kernel_times(h=h, kind=0, reset=True)
+    P.aniso_kernel_times(h=h, kind=1, reset=True)
+    P.aniso_step(h, T, inst.dt, inst.nsteps)
+    P.aniso_sync(h)
+    kt = {k: P.aniso_kernel_times(h=h, kind=k) for k in (0, 1)}
+    P.aniso_set_option(h, P.ANISO_OPT_PROFILE, 0)
+    P.aniso_step(h, T, inst.dt, inst.nsteps)
+    P.aniso_sync(h)
+    cell_steps = inst.cells * inst.nsteps
+    value, ms_step, _ = job_throughput(cell_steps, ms_call, "cuda")
+    # e2e: pinned host T (the hi part) in, one call, host T out; the low parts
+    # stay with the handle on the device
+    host = torch.empty(T.shape, dtype=torch.float32, pin_memory=True)
+    host.copy_(T)
+    torch.cuda.synchronize()
+    reps = max(1, min(3, args.steps))
+    e0.record(stream)
+    for _ in range(reps):
+        T.copy_(host, non_blocking=True)
+        P.aniso_step(h, T, inst.dt, inst.nsteps)
+        host.copy_(T, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_value, _, _ = job_throughput(cell_steps, e0.elapsed_time(e1) / reps, "cuda")
+    peak, note = measured_peak()
+    names = {0: "xsweep", 1: "ysweep"}
+    dom = max(kt, key=lambda k: kt[k][0])
+    launch_ms = kt[dom][0] / max(1, kt[dom][1])
+    achieved = WC_BYTES_PER_CELL_SWEEP * inst.cells / (launch_ms * 1e-3) / 1e9
+    line = {
+        "metric": "Gcell-steps/s, one compensated FP32 grid (hi+lo state, FP16 coefficients); % HBM peak",
+        "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 hi+lo", "data": "synthetic",
+        "config": {"workload": workload_compensated(nx, ny), "cells_per_gpu": inst.cells,
+                   "steps_per_call": inst.nsteps,
+                   "l2": "inputs larger than L2: %.2f GB resident" % (inst.cells * 4 * 10 / 1e9),
+                   "parallelism": "one independent grid per GPU (no collective)"},
+        "roofline": {"bound": "hbm", "kernel": "line7k_" + names[dom], "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak, "peak_source": note,
+                     "traffic": ncu_traffic("line7k_%dx%d" % (nx, ny)),
+                     "algorithmic_bytes_per_launch": WC_BYTES_PER_CELL_SWEEP * inst.cells,
+                     "avg_launch_ms": launch_ms},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": inst.cells * 4,
+                "d2h_bytes_per_step": inst.cells * 4},
+        "conservation_drift": abs(s1 - s0) / abs(s0),
+        "clocks": clk.summary(),
+        "gpu_launches": 2 * inst.nsteps * args.steps,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    P.aniso_destroy(h)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def run_reference_compensated(args):
+    """The FP64 oracle on the compensated workload's grid (the same FP16-rounded
+    coefficients): whole steps until the time budget."""
+    rank, _, _ = dist_env()
+    if rank != 0:
+        return 0
+    import numpy as np
+    import oracle as O
+    nx, ny = compensated_shape(args)
+    inst = make_compensated(nx, ny)
+    co = O.face_coeffs(_w32(inst.bx), _w32(inst.by), inst.bc, inst.chi_par).rounded(np.float16)
+    budget = max(5.0, 120.0 / max(1, args.steps + args.warmup))
+    T = _w32(inst.T0)
+    vals, ms = [], []
+    for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        n = 0
+        while time.perf_counter() - t0 < budget:
+            T = O.step(T, co, inst.bc, inst.dt, inst.dx, inst.dy, inst.chi_par, nsteps=1)
+            n += 1
+        el = time.perf_counter() - t0
+        if k >= args.warmup:
+            vals.append(inst.cells * n / el / 1e9)
+            ms.append(el * 1e3)
+    v = statistics.median(vals)
+    line = {"impl": "reference",
+            "metric": "Gcell-steps/s, one compensated FP32 grid (hi+lo state, FP16 coefficients); % HBM peak",
+            "value": v, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": statistics.median(ms), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_compensated(nx, ny)},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+                             "sample": "whole FP64 steps of the grid for %.0f s per bench step" % budget},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
     return 0
 
 
@@ -1077,11 +1247,15 @@ def main():
             return run_reference_3d(args)
         if args.workload == "random4096":
             return run_reference_single(args)
+        if args.workload == "compensated":
+            return run_reference_compensated(args)
         return run_reference(args)
     if args.workload == "random3d":
         return main_3d(args)
     if args.workload == "random4096":
         return main_single(args)
+    if args.workload == "compensated":
+        return main_compensated(args)
     import numpy as np
     import torch
     rank, world, local = dist_env()
