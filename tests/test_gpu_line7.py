@@ -3,9 +3,11 @@
 holding a piece of four lines; the segment-end system is solved per warp
 against two interface unknowns, whose cyclic system (2 CS unknowns a line)
 every block solves after one exchange through distributed shared memory.
-It takes the plain FP32 state on lines of 8192 and 16384 cells (and of
-2049-4096 with ANISO_OPT_CLUSTER_LINES = 2), and the compensated state
-(hi + lo) in both directions.  Checked against the FP64 oracle, against the
+It takes the plain FP32 state on lines of 4096, 8192 and 16384 cells
+(ANISO_OPT_CLUSTER_LINES = 2, the default; 1 leaves 4096-cell lines to the
+long-line kernel), and the compensated state (hi + lo) in both directions.
+Checked against the FP64 oracle (also on the full 4096^2 and 16384^2
+configurations in the benchmark's launch configuration), against the
 general kernels, for conservation, on zero-flux boundaries, with FP16 face
 coefficients and inside a batch."""
 import numpy as np
@@ -60,8 +62,8 @@ def test_cluster_lines_other_limiters(lib, nx, ny, bc, limiter):
 
 @pytest.mark.parametrize("nx,ny,bc", [(4096, 128, 1), (128, 4096, 0), (2048, 96, 1)])
 def test_cluster_option_takes_4096_lines(lib, nx, ny, bc):
-    """ANISO_OPT_CLUSTER_LINES = 2 moves lines of 2049-4096 cells from the
-    long-line kernel to the cluster kernel (2 blocks a cluster at 4096)."""
+    """ANISO_OPT_CLUSTER_LINES = 2 (the default) puts lines of 4096 cells on
+    the cluster kernel (2 blocks a cluster) instead of the long-line kernel."""
     inst = _inst(nx, ny, bc, seed=17)
     g = GpuGrid(lib, inst, FP32, fast=3)
     lib.aniso_set_option(g.h, lib.ANISO_OPT_CLUSTER_LINES, 2)
@@ -169,3 +171,40 @@ def test_cluster_grids_in_a_batch_match_single_grids(lib):
     finally:
         for g in grids + singles:
             g.close()
+
+
+def test_config2_full_grid_against_the_oracle(lib):
+    """The 4096^2 random-field FP32 workload in the benchmark's launch
+    configuration (aniso_step, default options: both updates on 2-block
+    clusters), two steps, every cell against the oracle's full run."""
+    inst = W.random_instance(4096, 4096, seed=W.BASE_SEED, chi_par=0.05, dt_factor=100.0, nsteps=2)
+    g = GpuGrid(lib, inst, FP32)
+    try:
+        got = g.step(2)
+    finally:
+        g.close()
+    T0, co = oracle_inputs(lib, inst, FP32)
+    ref = oracle_step(inst, T0, co, 2)
+    assert rel_linf(got, ref) < fp32_tol(inst, T0, co, 2, ref)
+
+
+def test_config4_full_grid_against_the_oracle(lib):
+    """The 16384^2 compensated workload (FP32 hi+lo state, FP16 face
+    coefficients, |k| <= 32, chi_par 1, dt = 1000 x CFL) in the benchmark's
+    launch configuration (8-block clusters, the state interleaved between the
+    steps of a call): two steps, every cell of hi + lo against the oracle's
+    full run on the same FP16-rounded coefficients, and the sum of hi + lo."""
+    inst = W.random_instance(16384, 16384, seed=W.BASE_SEED, kmax=32, chi_par=1.0, dt_factor=1000.0, nsteps=2)
+    T0, co = oracle_inputs(lib, inst, FP32, fp16=True)
+    h, T = _kahan_grid(lib, inst, fp16=True)
+    try:
+        s0 = lib.aniso_total(h, T)[0]
+        lib.aniso_step(h, T, inst.dt, 2)
+        s1 = lib.aniso_total(h, T)[0]
+        got = _hi_lo(lib, h, T)
+    finally:
+        lib.aniso_destroy(h)
+    assert abs(s1 - s0) / abs(s0) < 1e-12
+    ref = oracle_step(inst, T0, co, 2)
+    assert np.isfinite(got).all()
+    assert rel_linf(got, ref) < 1e-4
