@@ -305,6 +305,19 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? (D3 ? 3 : 4) : 2) line4_
             xbu = vbu[cl];
             xe2 = ld_raw(E2 + cl * N);
         }
+        // the cell after the line (periodic wrap or mirrored ghost), issued
+        // with the first round's loads instead of inside that round
+        const int p1 = J.per_line ? 0 : n - 1;
+        const R eT = rc[p1];
+        R eU = eT, eD = eT, eBU = eT, eBD = eT;
+        if constexpr (!IMPL) {
+            eU = ru[p1];
+            eD = rd[p1];
+        }
+        if constexpr (D3 && !IMPL) {
+            eBU = rbu[p1];
+            eBD = rbd[p1];
+        }
         for (int v = V - 1; v >= 0; --v) {
             const int c = (v << logP) + t;
             R Td[N], Tc[N], Tu[N], Gv[N], Ev[N], Tbd[N], Tbu[N], E2v[N];
@@ -353,11 +366,10 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? (D3 ? 3 : 4) : 2) line4_
                 nv = vcar;
                 nw = wcar;
             }
-            if (cur == m - 1) {  // the cell after the line: periodic wrap or mirrored ghost
-                const int p1 = J.per_line ? 0 : n - 1;
-                nT = rc[p1];
-                if constexpr (!IMPL) nv = level<R, VL>(lim, ru[p1] - nT, nT - rd[p1]);
-                if constexpr (D3 && !IMPL) nw = level<R, VL>(lim, rbu[p1] - nT, nT - rbd[p1]);
+            if (cur == m - 1) {  // the cell after the line
+                nT = eT;
+                if constexpr (!IMPL) nv = level<R, VL>(lim, eU - nT, nT - eD);
+                if constexpr (D3 && !IMPL) nw = level<R, VL>(lim, eBU - nT, nT - eBD);
             }
             Tcar = __shfl_sync(full, Tc[0], 0, P);
             if constexpr (!IMPL) vcar = __shfl_sync(full, vv[0], 0, P);
