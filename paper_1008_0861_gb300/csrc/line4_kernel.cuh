@@ -269,17 +269,15 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? (D3 ? 3 : 4) : 2) line4_
     VT *sC = wbase + 2 * WA + q * m;  // gamma (shared-memory form only)
     // TMEM form: the block's columns (32 when a lane's 4 V + 4 fit, so that
     // more blocks share an SM's 512), this warp's lane quarter
+    // (warp 0 allocates now; the address is read after the barrier that
+    // follows the first round's loads, so the allocation overlaps them)
     __shared__ unsigned s_tmem;
-    unsigned tm_base = 0;
+    unsigned tm_base = 0, tm_lane = 0;
     const unsigned tm_cols = 4 * V + 4 <= 32 ? 32u : 64u;
     if constexpr (TM) {
         if (warp == 0) tm_alloc(&s_tmem, tm_cols);
         tm_fence_before();
-        __syncthreads();
-        tm_fence_after();
-        tm_base = s_tmem;
     }
-    const unsigned tm_lane = tm_base + ((unsigned)(32 * (warp & 3)) << 16);
     auto swz = [mfull, logU](int c) { return c < mfull ? c ^ ((c >> logU) & 7) : c; };
 
     // ---- A: face fluxes and lam*g, coalesced (lane t: chunks v*P + t), last round first
@@ -317,6 +315,12 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? (D3 ? 3 : 4) : 2) line4_
         if constexpr (D3 && !IMPL) {
             eBU = rbu[p1];
             eBD = rbd[p1];
+        }
+        if constexpr (TM) {  // the block's TMEM address, the first loads in flight
+            __syncthreads();
+            tm_fence_after();
+            tm_base = s_tmem;
+            tm_lane = tm_base + ((unsigned)(32 * (warp & 3)) << 16);
         }
         for (int v = V - 1; v >= 0; --v) {
             const int c = (v << logP) + t;
