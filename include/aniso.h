@@ -105,10 +105,10 @@ enum {
     ANISO_OPT_TMEM = 14,       /* FP32: 1 (default) keeps part of the line state in the SM's tensor
                                   memory (TMEM) instead of shared memory, so more blocks fit an SM:
                                   in batched calls the warp-per-line kernel's (four-warp blocks,
-                                  when every line of a sweep fits: at most 15 chunks of 4 cells a
-                                  lane; taken from the batch's first handle), and the cluster
-                                  kernel's for the plain state.  0 keeps it all in shared memory.
-                                  Results are the same bit for bit. */
+                                  lines of at most 8 chunks of 4 cells a lane; chosen grid by grid
+                                  where it keeps more blocks resident; taken from the batch's first
+                                  handle), and the cluster kernel's for the plain state.  0 keeps
+                                  it all in shared memory.  Results are the same bit for bit. */
     ANISO_OPT_CLUSTER_LINES = 15 /* FP32 fast path, lines cut across the blocks of one thread-block
                                   cluster (pieces of 2048 or 1024 cells), so that lines too long for
                                   one block need no transpose pass.  2 (default): lines of 4096,

@@ -164,7 +164,7 @@ cudaError_t launch_source(int prec, void *T, const void *Q, double dt, size_t n,
 // warps: warps per block (0 = default of 4); seg_chunks: target 16-byte
 // chunks per lane (0 = default of 4), which sets the team size and so the
 // PCR depth.
-// tmem: the tensor-memory form (FP32, four-warp blocks, at most 15 chunks a
+// tmem: the tensor-memory form (FP32, four-warp blocks, at most 8 chunks a
 // lane); false when the line does not fit it.
 bool line4_config(int prec, int n, bool transposed, int warps, int seg_chunks, int *team, int *lines_per_block,
                   int *nthreads, size_t *smem, bool tmem = false);

@@ -73,7 +73,7 @@ template <typename K> static int occ4(K kern, int nthreads, size_t smem)
 int line4_tm_cols(int n, int team)
 {
     const int m = n / 4, U = m / team, V = U + (m % team ? 1 : 0);
-    return 4 * V + 4 <= 32 ? 32 : 64;
+    return 8 * V <= 32 ? 32 : 64;
 }
 
 int line4_blocks_per_sm(int prec, int coef_fp16, int limiter, int nthreads, size_t smem, bool tmem, int tm_cols)

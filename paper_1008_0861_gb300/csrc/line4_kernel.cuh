@@ -187,9 +187,11 @@ __device__ __forceinline__ void tm_wait_st() { asm volatile("tcgen05.wait::st.sy
 // IMPL: a purely implicit update (no transverse term, mu = mu2 = 0: the second
 // half-update of each axis in the 4-step scheme); neighbouring lines and
 // transverse coefficients are then neither loaded nor limited.
-// TM (FP32, 2-D, four-warp blocks, at most 15 chunks a lane): each lane's
+// TM (FP32, 2-D, four-warp blocks, at most 8 chunks a lane): each lane's
 // gamma lives in its TMEM lane instead of shared memory, so the line state in
-// shared memory is 8 bytes a cell instead of 12 and more blocks fit an SM.
+// shared memory is 8 bytes a cell instead of 12 and more blocks fit an SM; the
+// lane's chunks of T_old wait there too, from the flux phase to phase C
+// (4 V + 4 V columns of the block's 32 or 64).
 template <typename R, typename C, bool VL, bool D3 = false, bool NL = false, bool IMPL = false, bool TM = false>
 __global__ void __launch_bounds__(256, sizeof(R) == 4 ? (D3 ? 3 : 4) : 2) line4_kernel(Line2Args args)
 {
@@ -281,7 +283,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? (D3 ? 3 : 4) : 2) line4_
     // follows the first round's loads, so the allocation overlaps them)
     __shared__ unsigned s_tmem;
     unsigned tm_base = 0, tm_lane = 0;
-    const unsigned tm_cols = 4 * V + 4 <= 32 ? 32u : 64u;
+    const unsigned tm_cols = 8 * V <= 32 ? 32u : 64u;
     if constexpr (TM) {
         if (warp == 0) tm_alloc(&s_tmem, tm_cols);
         tm_fence_before();
@@ -334,6 +336,9 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? (D3 ? 3 : 4) : 2) line4_
             const int c = (v << logP) + t;
             R Td[N], Tc[N], Tu[N], Gv[N], Ev[N], Tbd[N], Tbu[N], E2v[N];
             V16<R>::unpack(xc, Tc);
+            // TMEM form: this chunk of T_old waits in the lane's columns 4 (V + v)
+            // for phase C, which takes the same chunks by the same lanes
+            if constexpr (TM) tm_st4(tm_lane + 4u * (unsigned)(V + v), Tc[0], Tc[1], Tc[2], Tc[3]);
             unpack_raw(xg, Gv);
             if constexpr (!IMPL) {
                 V16<R>::unpack(xd, Td);
@@ -489,7 +494,9 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? (D3 ? 3 : 4) : 2) line4_
                 go[j] = cgo[j];
             }
             }
-            if constexpr (TM) tm_st4(tm_lane + 4u * (unsigned)(u + 1), gs[0], gs[1], gs[2], gs[3]);
+            // (chunk u + 1's gamma at columns 4 (u + 1); in the first round there is none)
+            if constexpr (TM)
+                if (u + 1 < V) tm_st4(tm_lane + 4u * (unsigned)(u + 1), gs[0], gs[1], gs[2], gs[3]);
         }
         // row s needs the face below the segment: the previous lane's last face
         const int tp = (t - 1) & (P - 1);
@@ -507,9 +514,13 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? (D3 ? 3 : 4) : 2) line4_
 
     // Phase C's first two chunks of T_old start loading now, so that their
     // latency hides behind R and B2 (-3 to -4 % measured on 1024-cell lines).
+    // (TMEM form: T_old is in tensor memory already)
     const VT *vcC = reinterpret_cast<const VT *>(rc);
-    VT pre0 = vcC[t], pre1 = pre0;  // t < P <= m
-    if (t + P < m) pre1 = vcC[t + P];
+    VT pre0{}, pre1{};
+    if constexpr (!TM) {
+        pre0 = pre1 = vcC[t];  // t < P <= m
+        if (t + P < m) pre1 = vcC[t + P];
+    }
 
     // ---- R: reduced system of the line in the segment-end unknowns
     R X, Xm;
@@ -552,11 +563,16 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? (D3 ? 3 : 4) : 2) line4_
         VT *vout = reinterpret_cast<VT *>(static_cast<R *>(J.Tout) + (size_t)lc * n);
         for (int v = 0; v < V; ++v) {
             const int c = (v << logP) + t;
-            if (c >= m) break;
             R to[N], d[N];
-            V16<R>::unpack(pre0, to);
-            pre0 = pre1;  // two chunks in flight
-            if (c + 2 * P < m) pre1 = vcC[c + 2 * P];
+            if constexpr (TM) {
+                tm_ld4(tm_lane + 4u * (unsigned)(V + v), to);  // warp-wide, before the lane's bound check
+                if (c >= m) continue;
+            } else {
+                if (c >= m) break;
+                V16<R>::unpack(pre0, to);
+                pre0 = pre1;  // two chunks in flight
+                if (c + 2 * P < m) pre1 = vcC[c + 2 * P];
+            }
             V16<R>::unpack(sA[swz(c)], d);
             R sum = R(0);
 #pragma unroll

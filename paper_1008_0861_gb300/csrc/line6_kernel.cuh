@@ -32,9 +32,17 @@ __global__ void __launch_bounds__(512, 1) line6_kernel(Line2Args args)
     constexpr int N = 4;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ Line2Job J;
-    if (threadIdx.x == 0)
-        J = args.jobs ? args.jobs[args.block_job ? args.block_job[blockIdx.x] : find_job(args.jobs, args.njobs)]
-                      : args.one;
+    if (args.jobs) {  // the block's job, copied by warp 0's lanes a word each
+        constexpr int W8 = (int)(sizeof(Line2Job) / 8);
+        static_assert(sizeof(Line2Job) % 8 == 0 && W8 <= 32, "job copy: one 8-byte word a lane");
+        if (threadIdx.x < W8) {
+            const int k = args.block_job ? args.block_job[blockIdx.x] : find_job(args.jobs, args.njobs);
+            reinterpret_cast<unsigned long long *>(&J)[threadIdx.x] =
+                reinterpret_cast<const unsigned long long *>(args.jobs + k)[threadIdx.x];
+        }
+    } else if (threadIdx.x == 0) {
+        J = args.one;
+    }
     __syncthreads();
 
     const int lim = args.limiter;

@@ -149,8 +149,9 @@ bool line4_config(int prec, int n, bool transposed, int warps, int seg_chunks, i
     const int L = 32 / P;
     while (transposed && (NW * L) % N != 0) NW *= 2;
     if (NW > 8) return false;
-    // the tensor-memory form: each lane keeps 4 V gamma columns of the block's 64
-    if (tmem && (prec != PREC_FP32 || NW != 4 || 4 * V + 4 > 64)) return false;
+    // the tensor-memory form: each lane keeps 4 V columns of gamma and 4 V of
+    // T_old, of the block's 64
+    if (tmem && (prec != PREC_FP32 || NW != 4 || 8 * V > 64)) return false;
     const size_t sm = (size_t)NW * (tmem ? 2 : 3) * L * m * 16;
     if (sm > SMEM_LIMIT - 1024) return false;
     *team = P;
