@@ -186,12 +186,16 @@ __global__ void __launch_bounds__(L7_THREADS, TM ? 3 : 2) line7_kernel(Line2Args
     VT *sA = reinterpret_cast<VT *>(smem_raw) + (size_t)lb * NARR * m;  // F -> rho -> delta -> T_new (hi)
     VT *sB = sA + m;                                                     // lam*g -> alpha -> (K) T_new lo
     VT *sC = sA + 2 * m;                                                 // gamma (shared-memory form)
-    // TMEM form: warp 0 allocates the block's columns now; the address is read
-    // after the barrier that ends phase A.  Warp w: lanes 32 (w % 4) .. + 31,
-    // columns 32 (w / 4) .. + 31 (chunk u of the lane's segment at 4 u).
+    // TMEM form: warp 0 allocates the block's 128 columns now; the address is
+    // read after the barrier that follows the first loads.  Warp w: lanes
+    // 32 (w % 4) .. + 31, columns 64 (w / 4) .. + 63: gamma of the lane's
+    // segment chunk u at 4 u, the lane's chunk of T_old of round v (from the
+    // flux phase, for phase C, which takes the same chunks) at 32 + 4 v.
+    constexpr unsigned TM7_COLS = 128;
     __shared__ unsigned s_tmem;
+    unsigned tm_lane = 0;
     if (TM) {
-        if (warp == 0) tm_alloc(&s_tmem);
+        if (warp == 0) tm_alloc(&s_tmem, TM7_COLS);
         tm_fence_before();
     }
     auto swz = [mfull, logU](int c) { return c < mfull ? c ^ ((c >> logU) & 7) : c; };
@@ -263,6 +267,7 @@ __global__ void __launch_bounds__(L7_THREADS, TM ? 3 : 2) line7_kernel(Line2Args
             const int c = v * P + t;
             R Tc[N], Td[N], Tu[N], Tcl[N], Tdl[N], Tul[N], Gv[N], Ev[N];
             V16<R>::unpack(x.c, Tc);
+            if (TM) tm_st4(tm_lane + 32u + 4u * (unsigned)v, Tc[0], Tc[1], Tc[2], Tc[3]);  // warp-wide
             V16<R>::unpack(x.d, Td);
             V16<R>::unpack(x.u, Tu);
             if (K) {
@@ -307,6 +312,11 @@ __global__ void __launch_bounds__(L7_THREADS, TM ? 3 : 2) line7_kernel(Line2Args
         } else {  // two rounds ahead
             In cur = load(V - 1);
             In nxt = V >= 2 ? load(V - 2) : cur;
+            if (TM) {  // the block's TMEM address, the first loads in flight
+                __syncthreads();
+                tm_fence_after();
+                tm_lane = s_tmem + ((unsigned)(32 * (warp & 3)) << 16) + 64u * (unsigned)(warp >> 2);
+            }
             for (int v = V - 1; v >= 0; --v) {
                 const In x = cur;
                 cur = nxt;
@@ -332,11 +342,6 @@ __global__ void __launch_bounds__(L7_THREADS, TM ? 3 : 2) line7_kernel(Line2Args
         }
     }
     __syncthreads();
-    unsigned tm_lane = 0;
-    if (TM) {
-        tm_fence_after();
-        tm_lane = s_tmem + ((unsigned)(32 * (warp & 3)) << 16) + 32u * (unsigned)(warp >> 2);
-    }
 
     // ---- B1: bottom-up elimination of lane t's segment (as line6)
     R rho1 = R(0), alp1 = R(0), gam1 = R(-1);
@@ -415,7 +420,11 @@ __global__ void __launch_bounds__(L7_THREADS, TM ? 3 : 2) line7_kernel(Line2Args
     // Phase C's first two chunks of T_old start loading now.
     const VT *vcC = reinterpret_cast<const VT *>(Lc);
     const VT *vcCl = K ? reinterpret_cast<const VT *>(Lcl) : nullptr;
-    VT pre0 = vcC[vi(q0 + t)], pre1 = V >= 2 ? vcC[vi(q0 + t + P)] : pre0;
+    VT pre0{}, pre1{};  // (TMEM form: T_old waits in tensor memory)
+    if (!TM) {
+        pre0 = vcC[vi(q0 + t)];
+        pre1 = V >= 2 ? vcC[vi(q0 + t + P)] : pre0;
+    }
     VT pre0l = make_float4(0.f, 0.f, 0.f, 0.f), pre1l = pre0l;
     if (K) {
         pre0l = vcCl[vi(q0 + t)];
@@ -600,13 +609,17 @@ __global__ void __launch_bounds__(L7_THREADS, TM ? 3 : 2) line7_kernel(Line2Args
     for (int v = 0; v < V; ++v) {
         const int c = v * P + t;
         R to[N], tol[N], d[N];
-        V16<R>::unpack(pre0, to);
-        if (K) V16<R>::unpack(pre0l, tol);
-        pre0 = pre1;
-        if (K) pre0l = pre1l;
-        if (v + 2 < V) {
-            pre1 = vcC[vi(q0 + c + 2 * P)];
-            if (K) pre1l = vcCl[vi(q0 + c + 2 * P)];
+        if (TM) {
+            tm_ld4(tm_lane + 32u + 4u * (unsigned)v, to);  // warp-wide
+        } else {
+            V16<R>::unpack(pre0, to);
+            if (K) V16<R>::unpack(pre0l, tol);
+            pre0 = pre1;
+            if (K) pre0l = pre1l;
+            if (v + 2 < V) {
+                pre1 = vcC[vi(q0 + c + 2 * P)];
+                if (K) pre1l = vcCl[vi(q0 + c + 2 * P)];
+            }
         }
         V16<R>::unpack(sA[swz(c)], d);
         R hi[N], lo[N];
@@ -687,7 +700,7 @@ __global__ void __launch_bounds__(L7_THREADS, TM ? 3 : 2) line7_kernel(Line2Args
         __syncthreads();
         if (warp == 0) {
             tm_fence_after();
-            tm_dealloc(s_tmem);
+            tm_dealloc(s_tmem, TM7_COLS);
         }
     }
     cl_wait();  // no block leaves while another may still read its shared memory
