@@ -403,14 +403,15 @@ static int enqueue_line2(aniso_ctx *h, const void *in, void *out, const void *g,
     const bool v6 = lk == 6 && line6_config(h->prec, h->field_fp16, n, &J.team, &J.lines_per_block, &nthreads,
                                             &smem, h->l4_warps == 8 ? 2 : 4);
     int cs = 0;
-    // (tensor memory for the plain state only: the compensated kernel would
-    // spill at three blocks an SM, and measured no faster)
-    const bool tm7 = h->tmem != 0 && !in_lo;
-    const bool v7 = lk == 7 && line7_config(h->prec, h->field_fp16, n, &cs, &nthreads, &smem, tm7);
+    // (the plain state's tensor-memory form moves gamma out of shared memory;
+    // the compensated one keeps it there, at two blocks an SM, and puts only
+    // T_old in tensor memory)
+    const bool v7 = lk == 7 && line7_config(h->prec, h->field_fp16, n, &cs, &nthreads, &smem,
+                                            h->tmem != 0 && !in_lo);
     if (v7) {
         J.team = 64;
         J.lines_per_block = 4;
-        a.tmem = tm7 ? 1 : 0;
+        a.tmem = h->tmem != 0 ? 1 : 0;
     }
     ok = ok || v6 || v7;
     if (!ok) return fail(ANISO_ERR_UNSUPPORTED, "vectorised line kernel cannot take n=%d", n);

@@ -47,15 +47,15 @@ static cudaError_t run7(Kern kern, const Line2Args &a, int cs, size_t smem, cuda
     return cudaLaunchKernelEx(&cfg, kern, a);
 }
 
-template <bool K, bool TM>
+template <bool K, bool TM, bool TO>
 static cudaError_t launch7k(int coef_fp16, const Line2Args &a, int cs, size_t smem, cudaStream_t s)
 {
     const bool vl = a.limiter == LIM_VANLEER;
     if (coef_fp16)
-        return vl ? run7(line7_kernel<__half, true, K, TM>, a, cs, smem, s)
-                  : run7(line7_kernel<__half, false, K, TM>, a, cs, smem, s);
-    return vl ? run7(line7_kernel<float, true, K, TM>, a, cs, smem, s)
-              : run7(line7_kernel<float, false, K, TM>, a, cs, smem, s);
+        return vl ? run7(line7_kernel<__half, true, K, TM, TO>, a, cs, smem, s)
+                  : run7(line7_kernel<__half, false, K, TM, TO>, a, cs, smem, s);
+    return vl ? run7(line7_kernel<float, true, K, TM, TO>, a, cs, smem, s)
+              : run7(line7_kernel<float, false, K, TM, TO>, a, cs, smem, s);
 }
 
 cudaError_t launch_line7(int coef_fp16, const Line2Args &a, int cs, size_t smem, cudaStream_t s)
@@ -63,8 +63,14 @@ cudaError_t launch_line7(int coef_fp16, const Line2Args &a, int cs, size_t smem,
     if (a.jobs || a.one.n % cs != 0) return cudaErrorInvalidValue;
     const bool k = a.one.TinLo != nullptr;
     if (k && (!a.one.ToutLo)) return cudaErrorInvalidValue;
-    if (k) return a.tmem ? cudaErrorInvalidValue : launch7k<true, false>(coef_fp16, a, cs, smem, s);
-    return a.tmem ? launch7k<false, true>(coef_fp16, a, cs, smem, s) : launch7k<false, false>(coef_fp16, a, cs, smem, s);
+    // with args.tmem: the plain state keeps gamma and T_old in tensor memory
+    // (two shared arrays, three blocks an SM); the compensated state keeps
+    // T_old's hi and lo there (three shared arrays, two blocks an SM)
+    if (k)
+        return a.tmem ? launch7k<true, false, true>(coef_fp16, a, cs, smem, s)
+                      : launch7k<true, false, false>(coef_fp16, a, cs, smem, s);
+    return a.tmem ? launch7k<false, true, true>(coef_fp16, a, cs, smem, s)
+                  : launch7k<false, false, false>(coef_fp16, a, cs, smem, s);
 }
 
 }  // namespace aniso

@@ -127,10 +127,12 @@ constexpr int L7_LPB = 4;    // lines a block holds
 constexpr int L7_THREADS = L7_P * L7_LPB;
 constexpr int L7_PUB = 16;   // numbers a warp publishes for the interface system
 
-// TM: each lane's gamma goes to its own tensor-memory lane (32 columns a
-// warp, 64 a block) instead of shared memory, so a block holds two arrays of
-// its lines' state in shared memory and three blocks fit an SM.
-template <typename C, bool VL, bool K, bool TM>
+// TM: each lane's gamma goes to its own tensor-memory lane instead of shared
+// memory, so a block holds two arrays of its lines' state in shared memory and
+// three blocks fit an SM.  TO: each lane's chunks of T_old (hi and lo with K)
+// wait in its TMEM lane from the flux phase to phase C instead of being read
+// again (TM implies it).
+template <typename C, bool VL, bool K, bool TM, bool TO = TM>
 __global__ void __launch_bounds__(L7_THREADS, TM ? 3 : 2) line7_kernel(Line2Args args)
 {
     typedef float R;
@@ -186,15 +188,19 @@ __global__ void __launch_bounds__(L7_THREADS, TM ? 3 : 2) line7_kernel(Line2Args
     VT *sA = reinterpret_cast<VT *>(smem_raw) + (size_t)lb * NARR * m;  // F -> rho -> delta -> T_new (hi)
     VT *sB = sA + m;                                                     // lam*g -> alpha -> (K) T_new lo
     VT *sC = sA + 2 * m;                                                 // gamma (shared-memory form)
-    // TMEM form: warp 0 allocates the block's 128 columns now; the address is
-    // read after the barrier that follows the first loads.  Warp w: lanes
-    // 32 (w % 4) .. + 31, columns 64 (w / 4) .. + 63: gamma of the lane's
-    // segment chunk u at 4 u, the lane's chunk of T_old of round v (from the
-    // flux phase, for phase C, which takes the same chunks) at 32 + 4 v.
+    // TMEM forms: warp 0 allocates the block's 128 columns now; the address
+    // is read after the barrier that follows the first loads.  Warp w: lanes
+    // 32 (w % 4) .. + 31, columns 64 (w / 4) .. + 63: with TM gamma of the
+    // lane's segment chunk u at 4 u and its chunk of T_old of round v (from the
+    // flux phase, for phase C, which takes the same chunks) at 32 + 4 v; with
+    // TO alone (the compensated state) T_old's hi at 4 v and lo at 32 + 4 v.
+    static_assert(!TM || TO, "the tensor-memory form keeps T_old there too");
+    static_assert(!(TM && K), "the compensated state keeps gamma in shared memory");
     constexpr unsigned TM7_COLS = 128;
+    constexpr unsigned COL_T = TM ? 32u : 0u, COL_TLO = 32u;
     __shared__ unsigned s_tmem;
     unsigned tm_lane = 0;
-    if (TM) {
+    if (TO) {
         if (warp == 0) tm_alloc(&s_tmem, TM7_COLS);
         tm_fence_before();
     }
@@ -267,7 +273,6 @@ __global__ void __launch_bounds__(L7_THREADS, TM ? 3 : 2) line7_kernel(Line2Args
             const int c = v * P + t;
             R Tc[N], Td[N], Tu[N], Tcl[N], Tdl[N], Tul[N], Gv[N], Ev[N];
             V16<R>::unpack(x.c, Tc);
-            if (TM) tm_st4(tm_lane + 32u + 4u * (unsigned)v, Tc[0], Tc[1], Tc[2], Tc[3]);  // warp-wide
             V16<R>::unpack(x.d, Td);
             V16<R>::unpack(x.u, Tu);
             if (K) {
@@ -277,6 +282,10 @@ __global__ void __launch_bounds__(L7_THREADS, TM ? 3 : 2) line7_kernel(Line2Args
             } else {
 #pragma unroll
                 for (int j = 0; j < N; ++j) Tcl[j] = Tdl[j] = Tul[j] = R(0);
+            }
+            if (TO) {  // warp-wide
+                tm_st4(tm_lane + COL_T + 4u * (unsigned)v, Tc[0], Tc[1], Tc[2], Tc[3]);
+                if (K) tm_st4(tm_lane + COL_TLO + 4u * (unsigned)v, Tcl[0], Tcl[1], Tcl[2], Tcl[3]);
             }
             unpack_raw(x.g, Gv);
             unpack_raw(x.e, Ev);
@@ -304,6 +313,11 @@ __global__ void __launch_bounds__(L7_THREADS, TM ? 3 : 2) line7_kernel(Line2Args
         };
         if (K) {  // one round ahead (twice the loads a round)
             In cur = load(V - 1);
+            if (TO) {  // the block's TMEM address, the first loads in flight
+                __syncthreads();
+                tm_fence_after();
+                tm_lane = s_tmem + ((unsigned)(32 * (warp & 3)) << 16) + 64u * (unsigned)(warp >> 2);
+            }
             for (int v = V - 1; v >= 0; --v) {
                 const In x = cur;
                 if (v >= 1) cur = load(v - 1);
@@ -312,7 +326,7 @@ __global__ void __launch_bounds__(L7_THREADS, TM ? 3 : 2) line7_kernel(Line2Args
         } else {  // two rounds ahead
             In cur = load(V - 1);
             In nxt = V >= 2 ? load(V - 2) : cur;
-            if (TM) {  // the block's TMEM address, the first loads in flight
+            if (TO) {  // the block's TMEM address, the first loads in flight
                 __syncthreads();
                 tm_fence_after();
                 tm_lane = s_tmem + ((unsigned)(32 * (warp & 3)) << 16) + 64u * (unsigned)(warp >> 2);
@@ -341,6 +355,9 @@ __global__ void __launch_bounds__(L7_THREADS, TM ? 3 : 2) line7_kernel(Line2Args
             s_fb[lb][1] = lgq;
         }
     }
+    // T_old's tensor-memory stores complete before phase C reads them back
+    // (the TM form's elimination waits again after its gamma stores)
+    if (TO) tm_wait_st();
     __syncthreads();
 
     // ---- B1: bottom-up elimination of lane t's segment (as line6)
@@ -420,15 +437,15 @@ __global__ void __launch_bounds__(L7_THREADS, TM ? 3 : 2) line7_kernel(Line2Args
     // Phase C's first two chunks of T_old start loading now.
     const VT *vcC = reinterpret_cast<const VT *>(Lc);
     const VT *vcCl = K ? reinterpret_cast<const VT *>(Lcl) : nullptr;
-    VT pre0{}, pre1{};  // (TMEM form: T_old waits in tensor memory)
-    if (!TM) {
+    VT pre0{}, pre1{};  // (TMEM forms: T_old waits in tensor memory)
+    VT pre0l = make_float4(0.f, 0.f, 0.f, 0.f), pre1l = pre0l;
+    if (!TO) {
         pre0 = vcC[vi(q0 + t)];
         pre1 = V >= 2 ? vcC[vi(q0 + t + P)] : pre0;
-    }
-    VT pre0l = make_float4(0.f, 0.f, 0.f, 0.f), pre1l = pre0l;
-    if (K) {
-        pre0l = vcCl[vi(q0 + t)];
-        pre1l = V >= 2 ? vcCl[vi(q0 + t + P)] : pre0l;
+        if (K) {
+            pre0l = vcCl[vi(q0 + t)];
+            pre1l = V >= 2 ? vcCl[vi(q0 + t + P)] : pre0l;
+        }
     }
 
     // ---- R1: the warp's unknowns through the interface unknowns around it
@@ -609,8 +626,9 @@ __global__ void __launch_bounds__(L7_THREADS, TM ? 3 : 2) line7_kernel(Line2Args
     for (int v = 0; v < V; ++v) {
         const int c = v * P + t;
         R to[N], tol[N], d[N];
-        if (TM) {
-            tm_ld4(tm_lane + 32u + 4u * (unsigned)v, to);  // warp-wide
+        if (TO) {  // warp-wide
+            tm_ld4(tm_lane + COL_T + 4u * (unsigned)v, to);
+            if (K) tm_ld4(tm_lane + COL_TLO + 4u * (unsigned)v, tol);
         } else {
             V16<R>::unpack(pre0, to);
             if (K) V16<R>::unpack(pre0l, tol);
@@ -695,7 +713,7 @@ __global__ void __launch_bounds__(L7_THREADS, TM ? 3 : 2) line7_kernel(Line2Args
         }
     }
     if (bad && active) atomicOr(args.err, 1u);
-    if (TM) {  // every warp is done with TMEM before the block frees it
+    if (TO) {  // every warp is done with TMEM before the block frees it
         tm_fence_before();
         __syncthreads();
         if (warp == 0) {
