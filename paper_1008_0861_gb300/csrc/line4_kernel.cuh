@@ -314,17 +314,16 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? (D3 ? 3 : 4) : 2) line4_
             xe2 = ld_raw(E2 + cl * N);
         }
         // the cell after the line (periodic wrap or mirrored ghost), issued
-        // with the first round's loads instead of inside that round
+        // with the first round's loads instead of inside that round (2-D; the
+        // 3-D form, short of registers, loads it where it is used)
         const int p1 = J.per_line ? 0 : n - 1;
-        const R eT = rc[p1];
-        R eU = eT, eD = eT, eBU = eT, eBD = eT;
-        if constexpr (!IMPL) {
-            eU = ru[p1];
-            eD = rd[p1];
-        }
-        if constexpr (D3 && !IMPL) {
-            eBU = rbu[p1];
-            eBD = rbd[p1];
+        R eT = R(0), eU = R(0), eD = R(0);
+        if constexpr (!D3) {
+            eT = rc[p1];
+            if constexpr (!IMPL) {
+                eU = ru[p1];
+                eD = rd[p1];
+            }
         }
         if constexpr (TM) {  // the block's TMEM address, the first loads in flight
             __syncthreads();
@@ -384,9 +383,16 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? (D3 ? 3 : 4) : 2) line4_
                 nw = wcar;
             }
             if (cur == m - 1) {  // the cell after the line
-                nT = eT;
-                if constexpr (!IMPL) nv = level<R, VL>(lim, eU - nT, nT - eD);
-                if constexpr (D3 && !IMPL) nw = level<R, VL>(lim, eBU - nT, nT - eBD);
+                if constexpr (D3) {
+                    nT = rc[p1];
+                    if constexpr (!IMPL) {
+                        nv = level<R, VL>(lim, ru[p1] - nT, nT - rd[p1]);
+                        nw = level<R, VL>(lim, rbu[p1] - nT, nT - rbd[p1]);
+                    }
+                } else {
+                    nT = eT;
+                    if constexpr (!IMPL) nv = level<R, VL>(lim, eU - nT, nT - eD);
+                }
             }
             Tcar = __shfl_sync(full, Tc[0], 0, P);
             if constexpr (!IMPL) vcar = __shfl_sync(full, vv[0], 0, P);
