@@ -1365,7 +1365,7 @@ def main():
                    "autotuned": tuned},
         "roofline": {"bound": "hbm", "kernel": names[dom], "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak if achieved else None,
-                     "peak_source": peak_note, "traffic": ncu_traffic(names[dom]),
+                     "peak_source": peak_note, "traffic": ncu_traffic(names[dom]) if args.instances == N_INST else None,
                      "algorithmic_bytes_per_launch": BYTES_PER_CELL_SWEEP * cells,
                      "avg_launch_ms": dom_ms / dom_n if dom_n else None,
                      "per_kernel_ms": {names[k]: kt[k][0] / max(1, kt[k][1]) for k in kt}},
