@@ -315,10 +315,12 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? (D3 ? 3 : 4) : 2) line4_
         }
         // the cell after the line (periodic wrap or mirrored ghost), issued
         // with the first round's loads instead of inside that round (2-D; the
-        // 3-D form, short of registers, loads it where it is used)
+        // 3-D and temperature-dependent forms, short of registers, load it
+        // where it is used)
+        constexpr bool EARLY = !D3 && !NL;
         const int p1 = J.per_line ? 0 : n - 1;
         R eT = R(0), eU = R(0), eD = R(0);
-        if constexpr (!D3) {
+        if constexpr (EARLY) {
             eT = rc[p1];
             if constexpr (!IMPL) {
                 eU = ru[p1];
@@ -383,12 +385,10 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? (D3 ? 3 : 4) : 2) line4_
                 nw = wcar;
             }
             if (cur == m - 1) {  // the cell after the line
-                if constexpr (D3) {
+                if constexpr (!EARLY) {
                     nT = rc[p1];
-                    if constexpr (!IMPL) {
-                        nv = level<R, VL>(lim, ru[p1] - nT, nT - rd[p1]);
-                        nw = level<R, VL>(lim, rbu[p1] - nT, nT - rbd[p1]);
-                    }
+                    if constexpr (!IMPL) nv = level<R, VL>(lim, ru[p1] - nT, nT - rd[p1]);
+                    if constexpr (D3 && !IMPL) nw = level<R, VL>(lim, rbu[p1] - nT, nT - rbd[p1]);
                 } else {
                     nT = eT;
                     if constexpr (!IMPL) nv = level<R, VL>(lim, eU - nT, nT - eD);
