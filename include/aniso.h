@@ -272,8 +272,10 @@ int aniso_step_batched_host(aniso_batch_t b, void *const *T_host, const double *
  * (min T0 - min T) / min T0).  The values are formed inside the y-update
  * kernel (each block's values in a fixed order, FP64 across blocks) and
  * finished by one small kernel per launch, so the call stays one graph.
- * Slots of steps a grid does not take, and of grids off the fast path, are
- * NaN.  *steps (may be NULL) receives the steps per grid (the call's largest
+ * Slots of steps a grid does not take, and of grids whose y-update does not
+ * run on the warp-per-line kernel (off the fast path, columns above 2048
+ * cells, or on the cluster kernel of ANISO_OPT_CLUSTER_LINES), are NaN.
+ * *steps (may be NULL) receives the steps per grid (the call's largest
  * nsteps); out may be NULL to query it.  capacity: doubles available at out.
  * Synchronises the batch's stream.  Errors: ANISO_ERR_ARG (capacity),
  * ANISO_ERR_STATE (no such call yet). */

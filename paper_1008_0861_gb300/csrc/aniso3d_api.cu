@@ -196,6 +196,7 @@ static int enqueue3(aniso3_ctx *h, int d, const void *in, void *out, double lam,
     size_t smem;
     if (!line4_config(h->prec, J.n, transposed, h->warps, h->seg, &J.team, &J.lines_per_block, &nthreads, &smem))
         return fail(ANISO_ERR_UNSUPPORTED, "3-D line kernel cannot take n=%d", J.n);
+    J.swz = line4_swizzle(h->prec, J.n, J.team);
     J.block0 = 0;
     J.nblocks = (J.nlines + J.lines_per_block - 1) / J.lines_per_block;
     CU(launch_line4_3d(h->prec, h->field_fp16, A, J.nblocks, nthreads, smem, h->stream));

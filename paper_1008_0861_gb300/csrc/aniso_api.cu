@@ -396,6 +396,7 @@ static int enqueue_line2(aniso_ctx *h, const void *in, void *out, const void *g,
                                 &nthreads, &smem)
                  : line2_config(h->prec, n, transposed, &J.team, &J.lines_per_block, &nthreads, &smem,
                                 h->seg_chunks);
+    if (v4 && ok) J.swz = line4_swizzle(h->prec, n, J.team);
     // lines above line4's limit: the long-line kernels (constant diffusivity
     // only); the compensated state runs on the cluster kernel alone
     if (v4 && in_lo) ok = false;
@@ -1214,6 +1215,7 @@ static int batch_build(aniso_batch *b, void *const *T, const double *dt, const i
             if (!line4_config(prec, J.n, true, nthreads / 32, seg, &J.team, &J.lines_per_block, &nt, &sm) ||
                 nt != nthreads)
                 shape_rc = fail(ANISO_ERR_UNSUPPORTED, "batch: line length %d does not fit the block shape", J.n);
+            J.swz = line4_swizzle(prec, J.n, J.team);
             int occ = line4_blocks_per_sm(prec, fp16, b->hs[0]->limiter, nthreads, sm, false);
             cls[k] = {occ > 0 ? occ : 0, sm, false};
             int t0, t1, t2;

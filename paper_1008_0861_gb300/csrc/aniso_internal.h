@@ -106,6 +106,10 @@ struct Line2Job {
     // per 4 cells 4 hi values then 4 lo values (32 bytes, 2 n floats a line);
     // the TinLo / ToutLo pointers then only mark the compensated state.
     int ilv_in, ilv_out;
+    // line4_kernel: shift of the shared-memory swizzle (chunk c of a line at
+    // c ^ ((c >> s) & 7) within its group of 8): 0 = log2 of the chunks per
+    // lane segment, 1 = none, 2..7 = s of 1..6 (line4_swizzle's choice).
+    int swz;
 };
 
 // One block's diagnostics partial: FP64 sum, min and max of its lines' output.
@@ -189,6 +193,10 @@ int line4_blocks_per_sm(int prec, int coef_fp16, int limiter, int nthreads, size
                         int tm_cols = 64);
 // TMEM columns a line4 block of lines of n cells (teams of `team` lanes) allocates.
 int line4_tm_cols(int n, int team);
+// Line2Job::swz for a line4 line of n cells in teams of `team` lanes: the
+// swizzle shift that spreads the segment phases' accesses over the shared
+// memory's bank groups (fewest quarter-warp wavefronts).
+int line4_swizzle(int prec, int n, int team);
 // Three-dimensional grids (kernels_3d.cu).  c[0..2] = x faces (normal, with
 // y, with z) in layout [nz][ny][nx]; c[3..5] = y faces (normal, with z, with
 // x) in [nx][nz][ny]; c[6..8] = z faces (normal, with x, with y) in

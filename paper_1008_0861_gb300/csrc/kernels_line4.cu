@@ -76,6 +76,50 @@ int line4_tm_cols(int n, int team)
     return 8 * V <= 32 ? 32 : 64;
 }
 
+// The kernel keeps 16-byte chunk c of a line at c ^ ((c >> s) & 7) inside
+// its group of 8 chunks (the last, incomplete group unswizzled).  The
+// coalesced phases have the 8 lanes of a quarter warp touch one whole group,
+// conflict-free under any such permutation.  The segment phases have lane t
+// walk chunks c_lo(t) + u of its segment (U + 1 chunks for the first m mod P
+// lanes, U for the rest), so a quarter warp's chunks lie a segment length
+// apart and their bank groups (chunk mod 8) repeat unless the shift spreads
+// them.  Each candidate (log2 U, none, 1..6) is scored by the wavefronts of
+// those walks, the largest number of a quarter's lanes on one bank group,
+// summed over the steps u and the quarters; the first lowest wins.
+int line4_swizzle(int prec, int n, int team)
+{
+    const int N = prec == PREC_FP64 ? 2 : 4;
+    const int m = n / N, P = team;
+    if (P < 8 || m < 8) return 0;  // a quarter warp spans several lines
+    const int U = m / P, rr = m % P, V = U + (rr ? 1 : 0);
+    const int mfull = m & ~7;
+    int logU = 0;
+    while ((2 << logU) <= U) ++logU;
+    int best = 0;
+    long best_w = -1;
+    for (int code = 0; code <= 7; ++code) {
+        const int sh = code >= 2 ? code - 1 : logU, msk = code == 1 ? 0 : 7;
+        long w = 0;
+        for (int u = 0; u < V; ++u)
+            for (int q0 = 0; q0 < P; q0 += 8) {
+                int cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+                for (int t = q0; t < q0 + 8; ++t) {
+                    if (u >= U + (t < rr ? 1 : 0)) continue;
+                    const int c = t * U + (t < rr ? t : rr) + u;
+                    ++cnt[(c < mfull ? c ^ ((c >> sh) & msk) : c) & 7];
+                }
+                int mx = 0;
+                for (int g = 0; g < 8; ++g) mx = cnt[g] > mx ? cnt[g] : mx;
+                w += mx;
+            }
+        if (best_w < 0 || w < best_w) {
+            best_w = w;
+            best = code;
+        }
+    }
+    return best;
+}
+
 int line4_blocks_per_sm(int prec, int coef_fp16, int limiter, int nthreads, size_t smem, bool tmem, int tm_cols)
 {
     const bool vl = limiter == LIM_VANLEER;

@@ -22,9 +22,11 @@
 //    staged in the same area, position-major (`nlines` wide) with the
 //    lines of a block packed into 16-byte stores: the x-update writes T*
 //    column-major and the y-update writes T^{n+1} back row-major.
-// Shared arrays hold whole 16-byte chunks at c ^ ((c >> log2 U) & 7) within
-// complete groups of 8 (U = chunks per segment), so that both the
-// chunk-parallel phases and the segment walks touch distinct bank groups.
+// Shared arrays hold whole 16-byte chunks at c ^ ((c >> s) & 7) within
+// complete groups of 8, so that both the chunk-parallel phases and the
+// segment walks touch distinct bank groups; the host picks s per line
+// (Line2Job::swz, line4_swizzle) for the segment lengths it has, the default
+// being log2 of the chunks per segment.
 // FP32 reciprocals use the hardware approximation (rcp.approx.ftz.f32,
 // within 1 ulp); FP64 divides exactly.  Each block first asks for its input
 // rows to be brought into L2 with bulk prefetches.
@@ -288,7 +290,9 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? (D3 ? 3 : 4) : 2) line4_
         if (warp == 0) tm_alloc(&s_tmem, tm_cols);
         tm_fence_before();
     }
-    auto swz = [mfull, logU](int c) { return c < mfull ? c ^ ((c >> logU) & 7) : c; };
+    const int swsh = J.swz >= 2 ? J.swz - 1 : logU;
+    const int swmk = J.swz == 1 ? 0 : 7;
+    auto swz = [mfull, swsh, swmk](int c) { return c < mfull ? c ^ ((c >> swsh) & swmk) : c; };
 
     // ---- A: face fluxes and lam*g, coalesced (lane t: chunks v*P + t), last round first
     {

@@ -98,3 +98,25 @@ def test_diagnostics_leave_the_state_unchanged(lib):
             lib.aniso_batch_destroy(b_)
             for g in gs:
                 g.close()
+
+
+def test_diagnostics_are_nan_where_the_y_update_is_not_the_warp_per_line_kernel(lib):
+    """A grid with columns above 2048 cells (long-line kernel) and one on the
+    cluster kernel (rows of 8192) record no diagnostics: their slots are NaN,
+    while the warp-per-line grids beside them in the batch record every step."""
+    shapes = [(256, 128), (64, 3000), (8192, 64), (96, 1024)]
+    insts = [W.random_instance(nx, ny, seed=300 + k, chi_par=0.05, dt_factor=40.0, nsteps=2)
+             for k, (nx, ny) in enumerate(shapes)]
+    grids, b = _batch(lib, insts)
+    try:
+        lib.aniso_step_batched(b, [g.T for g in grids], [i.dt for i in insts], [2] * len(insts))
+        ring = lib.aniso_batch_diagnostics(b, len(insts))
+        assert ring.shape == (len(insts), 2, 3)
+        for k in (0, 3):
+            assert np.isfinite(ring[k]).all()
+        for k in (1, 2):
+            assert np.isnan(ring[k]).all()
+    finally:
+        lib.aniso_batch_destroy(b)
+        for g in grids:
+            g.close()
