@@ -74,7 +74,10 @@ enum {
     ANISO_OPT_ORDER = 4,      /* ANISO_ORDER_* */
     ANISO_OPT_STREAM = 5,     /* cudaStream_t cast to integer; 0 = legacy default stream */
     ANISO_OPT_GRAPH = 6,      /* 1 (default): replay aniso_step loops from a captured CUDA graph */
-    ANISO_OPT_PROFILE = 7,    /* 1: time every sweep launch with CUDA events (aniso_kernel_times) */
+    ANISO_OPT_PROFILE = 7,    /* 1: time every sweep launch with CUDA events (aniso_kernel_times);
+                                 k > 1: batched calls time the sweeps of every k-th step of a
+                                 call (steps 0, k, 2k, ...), so that fewer event nodes sit in
+                                 the graph; single-handle calls time every sweep */
     ANISO_OPT_FAST_PATH = 8,  /* kernels of the x-then-y order with a transposed intermediate:
                                  3 (default): warp-autonomous line kernel (coalesced flux phase,
                                  per-lane segment elimination, shuffle-only line solve);

@@ -267,7 +267,8 @@ extern "C" int aniso_set_option(aniso_t h, int key, long long v)
         h->use_graph = v != 0;
         break;
     case ANISO_OPT_PROFILE:
-        h->profile = v != 0;
+        if (v < 0 || v > (1 << 20)) return fail(ANISO_ERR_ARG, "bad profile value %lld", v);
+        h->profile = (int)v;
         break;
     case ANISO_OPT_DIAGNOSTICS:
         h->diag = v != 0;
@@ -1102,6 +1103,7 @@ static int batch_build(aniso_batch *b, void *const *T, const double *dt, const i
         long long table = -1;  // line4: offset of the block -> job table, or -1
         int diag_region = -1;  // line4 y-update with diagnostics: its partials region
         int tmem = 0;          // line4: gamma in tensor memory
+        int step = 0;          // the call's step the launch belongs to
     };
     std::vector<unsigned char> blob;
     std::vector<Launch> launches;  // in enqueue order
@@ -1353,6 +1355,7 @@ static int batch_build(aniso_batch *b, void *const *T, const double *dt, const i
         }
     };
 
+    size_t step_begin = 0;
     for (int s = 0; s < max_steps; ++s) {
         for (int phase = 0; phase < 2; ++phase) {
             std::vector<LineJob> xl;
@@ -1506,6 +1509,8 @@ static int batch_build(aniso_batch *b, void *const *T, const double *dt, const i
             add_col(yl);
             launches.insert(launches.end(), solo.begin(), solo.end());
         }
+        for (size_t i = step_begin; i < launches.size(); ++i) launches[i].step = s;
+        step_begin = launches.size();
     }
     if (shape_rc) return shape_rc;
     // diagnostics buffers: the ring of the call and one partials region per
@@ -1640,7 +1645,9 @@ static int batch_build(aniso_batch *b, void *const *T, const double *dt, const i
                j - i < (size_t)(1 + aniso_batch::kSide))
             ++j;
         int pidx = -1;
-        if (b->profile) {
+        // (ANISO_OPT_PROFILE k: the sweeps of every k-th step carry events)
+        const bool prof = b->profile && L.step % b->profile == 0;
+        if (prof) {
             pidx = b->prof.take((L.kind == 0 || L.kind == 2 || L.kind == 7 || L.kind == 9 || L.kind == 11)
                                     ? ANISO_KERNEL_XSWEEP
                                     : ANISO_KERNEL_YSWEEP);
@@ -1675,7 +1682,7 @@ static int batch_build(aniso_batch *b, void *const *T, const double *dt, const i
             rc = fail(ANISO_ERR_CUDA, "batched launch: %s", cudaGetErrorString(ce));
             break;
         }
-        if (b->profile) {
+        if (prof) {
             if (cudaEventRecordWithFlags(b->prof.pool[pidx].b, b->cap_stream, cudaEventRecordExternal) !=
                 cudaSuccess) {
                 rc = fail(ANISO_ERR_CUDA, "profiling event failed");

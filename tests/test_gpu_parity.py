@@ -340,6 +340,38 @@ def test_kernel_timing_events(lib, graph):
         g.close()
 
 
+@pytest.mark.parametrize("every", [1, 3])
+def test_batch_kernel_timing_every_kth_step(lib, every):
+    """In batched calls ANISO_OPT_PROFILE = k times the sweeps of steps 0, k,
+    2k, ... of each call (7 steps: 7 or 3 sweeps of each kind a call), and the
+    results do not depend on it."""
+    insts = [_inst(128, 96, 1, seed=21), _inst(256, 64, 0, seed=22)]
+    grids = [GpuGrid(lib, i, FP32) for i in insts]
+    plain = [GpuGrid(lib, i, FP32) for i in insts]
+    try:
+        lib.aniso_set_option(grids[0].h, lib.ANISO_OPT_PROFILE, every)
+        b = lib.aniso_batch_create([g.h for g in grids])
+        pb = lib.aniso_batch_create([g.h for g in plain])
+        try:
+            for _ in range(2):
+                lib.aniso_step_batched(b, [g.T for g in grids], [i.dt for i in insts], [7, 7])
+                lib.aniso_step_batched(pb, [g.T for g in plain], [i.dt for i in insts], [7, 7])
+            per_call = 7 if every == 1 else 3
+            for kind in (lib.ANISO_KERNEL_XSWEEP, lib.ANISO_KERNEL_YSWEEP):
+                ms, n = lib.aniso_kernel_times(batch=b, kind=kind)
+                assert n == 2 * per_call and ms > 0.0
+            lib.aniso_sync(grids[0].h)
+            lib.aniso_sync(plain[0].h)
+            for g, p in zip(grids, plain):
+                assert np.array_equal(g.T.cpu().numpy(), p.T.cpu().numpy())
+        finally:
+            lib.aniso_batch_destroy(b)
+            lib.aniso_batch_destroy(pb)
+    finally:
+        for g in grids + plain:
+            g.close()
+
+
 @pytest.mark.parametrize("prec", [FP32, FP64])
 @pytest.mark.parametrize("nx,ny,bc", [(64, 96, 1), (128, 40, 0), (1024, 1024, 1), (36, 2048, 1),
                                       (512, 96, 1), (1000, 8, 0)])
