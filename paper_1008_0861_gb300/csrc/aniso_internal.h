@@ -193,6 +193,14 @@ int line4_blocks_per_sm(int prec, int coef_fp16, int limiter, int nthreads, size
                         int tm_cols = 64);
 // TMEM columns a line4 block of lines of n cells (teams of `team` lanes) allocates.
 int line4_tm_cols(int n, int team);
+// Chunks of padding after each warp's shared area in the FP32 line4 kernel
+// (narr arrays of 32/P lines of m chunks).  With teams of 16 or 8 lanes the
+// two half-warps of the transposed store read lines of different warp areas;
+// the pad puts those areas 16 banks apart (their offset 4 chunks mod 8).
+__host__ __device__ inline int line4_area_pad(int P, int narr, int m)
+{
+    return P == 16 ? ((2 - 2 * narr * m) & 3) : P == 8 ? ((4 - 4 * narr * m) & 7) : 0;
+}
 // Line2Job::swz for a line4 line of n cells in teams of `team` lanes: the
 // swizzle shift that spreads the segment phases' accesses over the shared
 // memory's bank groups (fewest quarter-warp wavefronts).

@@ -275,7 +275,8 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? (D3 ? 3 : 4) : 2) line4_
     const int WA = m << logL;        // chunks per array in one warp's area
     const int mfull = m & ~7, logU = 31 - __clz(U);
     constexpr int NARR = TM ? 2 : 3;  // shared arrays per warp area
-    VT *wbase = reinterpret_cast<VT *>(smem_raw) + (size_t)warp * NARR * WA;
+    const int AS = NARR * WA + (N == 4 ? line4_area_pad(P, NARR, m) : 0);  // chunks per warp area
+    VT *wbase = reinterpret_cast<VT *>(smem_raw) + (size_t)warp * AS;
     VT *sA = wbase + q * m;           // F -> rho -> delta -> T_new
     VT *sB = wbase + WA + q * m;      // lam*g -> alpha
     VT *sC = wbase + 2 * WA + q * m;  // gamma (shared-memory form only)
@@ -629,7 +630,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? (D3 ? 3 : 4) : 2) line4_
 #pragma unroll
                 for (int i = 0; i < N; ++i) {
                     const int lb = (grp << LOGN) + i;
-                    const VT *src = reinterpret_cast<const VT *>(smem_raw) + (size_t)(lb >> logL) * NARR * WA +
+                    const VT *src = reinterpret_cast<const VT *>(smem_raw) + (size_t)(lb >> logL) * AS +
                                     (lb & ((1 << logL) - 1)) * m + sc;
                     o[i] = reinterpret_cast<const R *>(src)[j];
                 }

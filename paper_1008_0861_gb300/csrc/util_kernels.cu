@@ -152,7 +152,8 @@ bool line4_config(int prec, int n, bool transposed, int warps, int seg_chunks, i
     // the tensor-memory form: each lane keeps 4 V columns of gamma and 4 V of
     // T_old, of the block's 64
     if (tmem && (prec != PREC_FP32 || NW != 4 || 8 * V > 64)) return false;
-    const size_t sm = (size_t)NW * (tmem ? 2 : 3) * L * m * 16;
+    const int narr = tmem ? 2 : 3;
+    const size_t sm = (size_t)NW * (narr * L * m + (N == 4 ? line4_area_pad(P, narr, m) : 0)) * 16;
     if (sm > SMEM_LIMIT - 1024) return false;
     *team = P;
     *lines_per_block = NW * L;
